@@ -1,0 +1,340 @@
+"""Benchmark of the elastic-wall D3Q19 LBGK step on GB300 (one JSON line).
+
+Workload (default): the long pulsatile tube - radius 40, length 1024,
+~5.15 M fluid sites, tau 0.6, inlet 0.03 + 0.02 sin(2 pi n / 4000) (parabolic),
+density outlet rho = 1, elastic wall F = 0.85 with Eh/r0 = 0.5
+(kappa = 0.75 * 40 / 0.5 = 60), populations in FP32 (``--storage``).
+A "step" is one full timestep of the lattice (both kernels).  The populations
+(19 * 4 B * 5.15 M = 391 MB per copy) exceed the 129 MB L2, so no flush is
+needed between steps.
+
+  value      site updates per second (MLUPS) over the timed device region,
+             CUDA events on the lattice's stream, max over ranks;
+  e2e        the same metric through the public C ABI with host buffers:
+             initial fields copied in from pinned memory, every step followed
+             by lbm_reduce (FP64 mass and iolet fluxes read back to the host),
+             final moments copied out - all inside the timed region;
+  roofline   bulk-tile kernel: algorithmic bytes (2 * 19 * sizeof(storage)
+             per site update) / its CUDA-event duration, against the measured
+             HBM copy bandwidth;
+  cpu_baseline  the FP64 CPU oracle on the same workload, a bounded number of
+             steps on all host cores.
+
+``--impl reference`` times the oracle alone (the reference arm of this tier).
+Under torchrun every rank runs its own copy of the workload (independent
+vessels, no data-path collective): weak scaling.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+DTYPE = {"f64": "f64", "f32": "f32", "f16s": "f32", "bf16s": "f32"}
+METRIC = "elastic-wall D3Q19 MLUPS & % HBM roofline; mixed-prec vs FP32 at fixed error"
+
+
+def workload(args):
+    import lbm_inputs as I
+    if args.config == "tube40":
+        geo = I.tube(40, 1024, u_mean=0.03, u_amp=0.02, period=4000.0)
+        params = dict(tau=0.6, F=0.85, kappa=0.75 * 40 / 0.5, rho0=1.0)
+        name = "long pulsatile tube R=40 L=1024 (~5.15M sites), tau=0.6, Eh/r0=0.5"
+    elif args.config == "tube8":
+        geo = I.tube(8, 64, u_mean=0.025)
+        params = dict(tau=0.8, F=0.85, kappa=12.0, rho0=1.0)
+        name = "straight cylinder R=8 L=64 (~13k sites), tau=0.8, Eh/r0=0.5"
+    else:
+        raise SystemExit("unknown config " + args.config)
+    return geo, params, name
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(storage, config):
+    """DRAM bytes per bulk-kernel launch from the committed ncu summary, or None
+    if the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2108_08783_gb300", "csrc", "kernels.cu"), "rb").read()
+        key = "%s/%s" % (config, storage)
+        if key in rec and rec[key]["kernels_sha1"] == hashlib.sha1(src).hexdigest():
+            return float(rec[key]["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle(geo, params, seconds=12.0, max_steps=200, min_steps=2):
+    """MLUPS of the FP64 oracle on all host cores over a time-bounded sample."""
+    from oracle import Oracle
+    from oracle.oracle import default_threads
+    threads = default_threads()
+    orc = Oracle(geo.labels, geo.iolets, tau=params["tau"], wall_model=1, F=params["F"],
+                 kappa=params["kappa"], rho0=params["rho0"], threads=threads)
+    orc.run(1)  # page in
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps and (steps < min_steps or time.perf_counter() - t0 < seconds):
+        orc.run(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return orc.n * steps / dt / 1e6, threads, steps, dt
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    geo, params, name = workload(args)
+    from oracle import Oracle
+    from oracle.oracle import default_threads
+    threads = default_threads()
+    orc = Oracle(geo.labels, geo.iolets, tau=params["tau"], wall_model=1, F=params["F"],
+                 kappa=params["kappa"], rho0=params["rho0"], threads=threads)
+    # each step of this arm is one oracle step over the whole lattice (bounded:
+    # about a tenth of a second to a few seconds on the host)
+    orc.run(args.warmup)
+    t0 = time.perf_counter()
+    orc.run(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = orc.n * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": name, "sites": int(orc.n)},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": "%d full oracle steps of the workload" % args.steps},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_init()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2108_08783_gb300 import Lattice
+    import lbm_inputs as I
+
+    geo, params, name = workload(args)
+    lat = Lattice(geo.labels, geo.iolets, storage=args.storage, tau=params["tau"], device=local)
+    lat.set_wall("elastic", rho0=params["rho0"], F=params["F"], kappa=params["kappa"])
+    info = lat.info()
+    n = lat.n
+    stream = lat.stream
+    # ---------------------------------------------------------------- device timing
+    lat.step(args.warmup)
+    lat.sync()
+    clocks = Clocks(local)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    lat.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    kms, klaunch = lat.profile_read()
+    lat.profile(False)
+    lat.sync()
+    clk = clocks.stop() if rank == 0 else None
+    ms_max = max_over_ranks(ws, ms)
+    value = ws * n * args.steps / (ms_max * 1e-3) / 1e6
+    # ---------------------------------------------------------------- roofline
+    peak, peak_kind = measured_peaks()
+    s = BYTES[args.storage]
+    bulk_sites = int(info[11])
+    bulk_ms = kms[0] / max(1, klaunch[0])
+    achieved = bulk_sites * 2 * 19 * s / (bulk_ms * 1e-3) / 1e9
+    traffic = kernel_traffic(args.storage, args.config)
+    roof = {"bound": "hbm", "kernel": "k_bulk", "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "algorithmic_bytes_per_launch": bulk_sites * 2 * 19 * s,
+            "launch_ms": bulk_ms, "boundary_launch_ms": kms[1] / max(1, klaunch[1]),
+            "step_frac": n * 2 * 19 * s / (ms / args.steps * 1e-3) / 1e9 / peak}
+    # ---------------------------------------------------------------- end to end
+    e2e = None
+    if not args.no_e2e:
+        rho_g, u_g = I.random_fields(1, geo.shape, drho=1e-3, umax=0.02)
+        c = lat.coords()
+        rho_h = torch.from_numpy(I.gather(rho_g, c)).pin_memory()
+        u_h = torch.from_numpy(I.gather(u_g, c)).pin_memory()
+        rho_o = torch.empty(n, dtype=torch.float64).pin_memory()
+        u_o = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+        red = torch.empty(1 + len(geo.iolets), dtype=torch.float64).pin_memory()
+        k = args.e2e_steps
+        barrier(ws)
+        t0 = time.perf_counter()
+        lat.init_fields(rho_h.numpy(), u_h.numpy())
+        for _ in range(k):
+            lat.step(1)
+            lat._check(lat._lib.lbm_reduce(lat.h, _addr(red)))
+        lat._check(lat._lib.lbm_moments(lat.h, _addr(rho_o), _addr(u_o), 0))
+        dt = time.perf_counter() - t0
+        dt = max_over_ranks(ws, dt)
+        e2e = {"value": ws * n * k / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": (rho_h.numel() + u_h.numel()) * 8 / k,
+               "d2h_bytes_per_step": red.numel() * 8 + (rho_o.numel() + u_o.numel()) * 8 / k,
+               "steps": k}
+    # ---------------------------------------------------------------- CPU baseline
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        mlups, threads, steps, dt = cpu_oracle(geo, params, seconds=args.cpu_seconds)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": "%d FP64 oracle steps of the same workload (%.1f s)" % (steps, dt)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.storage], "data": "synthetic",
+            "config": {"workload": name, "sites": n, "storage": args.storage,
+                       "wall": "elastic GZS", "l2": "populations (%.0f MB) exceed L2; no flush"
+                       % (19 * s * n / 1e6), "parallelism": "replicas x%d" % ws},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(klaunch[0] + klaunch[1]),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _addr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=list(BYTES))
+    ap.add_argument("--config", default="tube40", choices=["tube40", "tube8"])
+    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

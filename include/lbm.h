@@ -1,0 +1,219 @@
+/*
+ * lbm.h - C ABI of the GB300 elastic-wall D3Q19 lattice Boltzmann library.
+ *
+ * One call advances a compacted sparse vascular lattice by LBGK timesteps
+ * (Sec. 2.1, Eq. LBE_SRT) with the paper's localised elastic wall (Sec. 2.3:
+ * Guo-Zheng-Shi wall with Delta = 1 and wall velocity
+ * U_w = (F + dr - dx)/dr U_f; Sec. 2.4: tube law dE = (1 - sigma^2) R^2/(Y h)
+ * (p - P0)), the rigid bounce-back wall it is compared with (Sec. 2.4), a
+ * velocity-profile inlet and fixed-density outlets (Sec. 3).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: LBM_OK (0) or a negative LBM_E* status.  No call aborts
+ *     the process; lbm_last_error(ctx) gives a one-line message.
+ *   - Host arrays passed in are copied before the call returns; the caller
+ *     keeps ownership.  Output arrays are written, never retained.
+ *   - Sites are numbered in canonical order: ascending (x*ny + y)*nz + z over
+ *     the fluid voxels (z fastest).  Directions follow the canonical D3Q19
+ *     order: 0 rest; 1/2 +-x; 3/4 +-y; 5/6 +-z; 7/8 (+1,+1,0)/(-1,-1,0);
+ *     9/10 (+1,-1,0)/(-1,+1,0); 11/12 (+1,0,+1)/(-1,0,-1);
+ *     13/14 (+1,0,-1)/(-1,0,+1); 15/16 (0,+1,+1)/(0,-1,-1);
+ *     17/18 (0,+1,-1)/(0,-1,+1).
+ *   - Device memory comes from the caller's allocator (or cudaMalloc when it
+ *     is NULL) and is released by lbm_destroy.  All kernels run on the CUDA
+ *     stream given at build time (lbm_set_stream changes it).
+ *   - One context per host thread; contexts share no state.
+ *   - Device-side faults of the method (non-finite or non-positive density)
+ *     are sticky flags reported by lbm_sync as LBM_EUNSTABLE.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Device allocator hook: alloc returns device memory of at least `bytes`
+ * bytes (256-byte aligned) or NULL; free releases it.  `user` is passed back. */
+typedef struct lbm_allocator {
+  void *(*alloc)(size_t bytes, void *user);
+  void (*free)(void *ptr, void *user);
+  void *user;
+} lbm_allocator;
+
+/* An inlet or outlet (Sec. 3).  Ghost voxels labelled 2+k belong to iolet k.
+ *   kind     LBM_IOLET_VELOCITY: the boundary population is rebuilt by the
+ *            GZS rule from (rho_f, u_in(x, n)); LBM_IOLET_DENSITY: from
+ *            (rho, u_f) (fixed-pressure outlet, p = c_s^2 rho, Eq. Pressure).
+ *   u_in(x, n) = axis * (u_mean p0(r) + u_amp (ps(r) sin(th) + pc(r) cos(th))),
+ *            th = 2 pi n / period + phase (period <= 0: steady, u_amp unused),
+ *            r = distance of the fluid site x from the line (centre, axis).
+ *   profile  LBM_PROFILE_PARABOLIC: p0 = ps = 2 (1 - r^2/radius^2)+, pc = 0;
+ *            LBM_PROFILE_WOMERSLEY: p0 parabolic, ps + i pc = the rigid-tube
+ *            Womersley shape (Sec. 2.2 with M = 1) at alpha = radius
+ *            sqrt(2 pi / period / nu), nu = (tau - 1/2)/3, unit mean over the
+ *            disc, zero outside it; LBM_PROFILE_PLUG: p0 = ps = 1, pc = 0.
+ *   axis     flow direction (normalised by the library); for a density iolet
+ *            it only orients the reported flux. */
+typedef struct lbm_iolet {
+  int32_t kind;
+  int32_t profile;
+  double rho;
+  double u_mean, u_amp, period, phase;
+  double centre[3], axis[3], radius;
+} lbm_iolet;
+
+enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,    /* invalid argument or inconsistent input */
+  LBM_ENOMEM = -2,    /* the allocator (or host malloc) failed */
+  LBM_ECUDA = -3,     /* a CUDA runtime call failed; see lbm_last_error */
+  LBM_EUNSTABLE = -4, /* a kernel saw a non-finite or non-positive density */
+  LBM_ETIMEOUT = -5,  /* a bounded device wait gave up */
+  LBM_ESTATE = -6     /* call not valid in the context's current state */
+};
+
+/* Population storage.  *S variants store f_i - w_i (the deviation from the
+ * rest equilibrium) so that half-precision keeps its significant bits. */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 };
+enum { LBM_WALL_BOUNCEBACK = 0, LBM_WALL_ELASTIC_GZS = 1 };
+enum { LBM_IOLET_VELOCITY = 0, LBM_IOLET_DENSITY = 1 };
+enum { LBM_PROFILE_PARABOLIC = 0, LBM_PROFILE_WOMERSLEY = 1, LBM_PROFILE_PLUG = 2 };
+
+/* lbm_build_lattice - compact the fluid voxels and build the link tables
+ * (the sparse lattice of Sec. 1; D3Q19 links of Sec. 2.1).
+ *   labels     host uint8 [nx*ny*nz], index (x*ny + y)*nz + z: 0 solid,
+ *              1 fluid, 2+k ghost of iolet k (k < n_iolets).  A link to a
+ *              solid voxel or out of the box is a wall link; a link to a
+ *              ghost of iolet k is an iolet link.
+ *   iolets     host [n_iolets] (copied).
+ *   storage    LBM_F64 / LBM_F32 / LBM_F16S / LBM_BF16S.  Collision runs in
+ *              FP64 for LBM_F64 and in FP32 otherwise; the wall's tube-law
+ *              update always runs in FP64.
+ *   tau        relaxation time, > 1/2 (Eq. LBE_SRT).
+ *   alloc      device allocator, or NULL for cudaMalloc/cudaFree.
+ *   cuda_stream  cudaStream_t for every kernel and copy (NULL = legacy stream).
+ *   out        receives the context.  Populations start at rest (rho = 1,
+ *              u = 0), wall model bounce-back, step counter 0.
+ * Errors: LBM_EINVAL for bad sizes, tau <= 1/2, a label >= 2 + n_iolets, a
+ * bad iolet (kind/profile out of range, zero axis, radius <= 0 for a profiled
+ * inlet) or a fluid site touching two different velocity inlets; LBM_ENOMEM;
+ * LBM_ECUDA. */
+int lbm_build_lattice(const uint8_t *labels, int32_t nx, int32_t ny, int32_t nz,
+                      const lbm_iolet *iolets, int32_t n_iolets, int32_t storage, double tau,
+                      const lbm_allocator *alloc, void *cuda_stream, lbm_ctx **out);
+
+/* lbm_set_wall_params - choose the wall rule and its per-wall-site parameters.
+ *   wall_model  LBM_WALL_BOUNCEBACK (Sec. 2.4, half-way bounce-back) or
+ *               LBM_WALL_ELASTIC_GZS (Sec. 2.3-2.4).
+ *   rho0        reference density: p - P0 = c_s^2 (rho_f - rho0).
+ *   F, kappa    host [n] in wall-site order (the sites with at least one wall
+ *               link, ascending), or n == 1 to broadcast one value.  F is the
+ *               velocity ratio U_R/U_f; kappa is the tube-law coefficient
+ *               (1 - sigma^2) r0^2/(E h) in lattice units, so that at each
+ *               step dE = kappa max(0, p - P0), dr = 1 + dE and
+ *               U_w = (F + dr - 1)/dr u_f.  NULL means 0.
+ * Errors: LBM_EINVAL for an unknown model, n not in {1, n_wall_sites}, or a
+ * negative / non-finite F or kappa. */
+int lbm_set_wall_params(lbm_ctx *ctx, int32_t wall_model, double rho0, const double *F,
+                        const double *kappa, int64_t n);
+
+/* lbm_init_fields - set f = f^eq(rho, u) (Eq. feq) at every site and reset the
+ * step counter to 0.  rho host [n_sites] or NULL (1); u host [n_sites][3] or
+ * NULL (0). */
+int lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *u);
+
+/* lbm_step - enqueue n_steps >= 0 timesteps on the context's stream and
+ * return without waiting.  Step n evaluates the inlet time factor at n. */
+int lbm_step(lbm_ctx *ctx, int64_t n_steps);
+
+/* lbm_moments - rho [n_sites] and u [n_sites][3] (FP64, canonical order) of
+ * the current pre-collision state (Eqs. Density, Momentum).  Either pointer may
+ * be NULL.  dst_is_device != 0: device pointers, written asynchronously on the
+ * context's stream; 0: host pointers, the call waits for the copy. */
+int lbm_moments(lbm_ctx *ctx, double *rho, double *u, int32_t dst_is_device);
+
+/* lbm_sync - wait for the context's stream; return LBM_EUNSTABLE if any kernel
+ * since the last lbm_sync saw a non-finite or non-positive density (the flag
+ * is then cleared), LBM_ECUDA on a CUDA error, else LBM_OK. */
+int lbm_sync(lbm_ctx *ctx);
+
+/* lbm_info - sizes of the context:
+ *   out[0] n_sites, [1] n_wall_sites, [2] n_wall_links, [3] n_tiles (32 sites),
+ *   [4] bulk tiles, [5] uniform boundary tiles, [6] irregular tiles,
+ *   [7] step counter, [8] storage, [9] n_iolets, [10] device bytes held,
+ *   [11] sites in bulk tiles. */
+int lbm_info(const lbm_ctx *ctx, int64_t out[12]);
+
+/* lbm_profile - when enable != 0, lbm_step records CUDA events on the
+ * context's stream around each of its two kernels (bulk tiles, boundary
+ * tiles); lbm_profile_read waits for the stream and returns the summed device
+ * time in ms[0] (bulk kernel) and ms[1] (boundary kernel) and the launch
+ * counts, then clears the record.  Measurement only: no work is skipped. */
+int lbm_profile(lbm_ctx *ctx, int32_t enable);
+int lbm_profile_read(lbm_ctx *ctx, double ms[2], int64_t launches[2]);
+
+/* lbm_export_lattice - the integer lattice (host arrays, any may be NULL):
+ *   coords [n_sites][3] int32 voxel coordinates;
+ *   nbr [n_sites][18] int32 neighbour along directions 1..18: site id >= 0,
+ *     -1 wall, -2-k iolet k;
+ *   wall_sites [n_wall_sites] int64 ascending;
+ *   wall_links [n_wall_links][2] int64 (site, direction) sorted. */
+int lbm_export_lattice(const lbm_ctx *ctx, int32_t *coords, int32_t *nbr, int64_t *wall_sites,
+                       int64_t *wall_links);
+
+/* lbm_wall_state - per wall site (wall-site order) the expansion dE and the
+ * wall velocity U_w [n][3] computed by the most recent step (host arrays, any
+ * may be NULL; zeros before the first step or under bounce-back).  Waits for
+ * the stream. */
+int lbm_wall_state(lbm_ctx *ctx, double *dE, double *Uw);
+
+/* lbm_reduce - FP64 diagnostics of the current state, deterministic order:
+ *   out[0] total mass sum_x rho_x;
+ *   out[1 + k] sum over the sites with a link into iolet k of (rho u).axis_k.
+ * out is a host array [1 + n_iolets]; the call waits for the stream. */
+int lbm_reduce(lbm_ctx *ctx, double *out);
+
+/* lbm_get_populations / lbm_set_populations - the pre-collision populations
+ * f[n_sites][19] (FP64, canonical site order, canonical directions),
+ * converting to or from the in-place storage layout.  set also sets the step
+ * counter.  *_is_device selects device (asynchronous) or host (waits)
+ * pointers. */
+int lbm_get_populations(lbm_ctx *ctx, double *f, int32_t dst_is_device);
+int lbm_set_populations(lbm_ctx *ctx, const double *f, int64_t step, int32_t src_is_device);
+
+/* Checkpoint of the exact device state (raw storage plus step counter), so a
+ * resumed run is bit-identical to an uninterrupted one. */
+size_t lbm_checkpoint_bytes(const lbm_ctx *ctx);
+int lbm_checkpoint_save(lbm_ctx *ctx, void *host_buf, size_t bytes);
+int lbm_checkpoint_load(lbm_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* lbm_wss - wall shear stress at m sites (a metric; the paper's WSS fields
+ * are not defined there): sigma = -(1 - 1/(2 tau)) sum_i f_i^neq c_i c_i,
+ * t = sigma n, WSS = |t - (t.n) n| for the given unit normals.
+ *   sites host int64 [m] canonical ids; normals host [m][3]; out host [m]. */
+int lbm_wss(lbm_ctx *ctx, const int64_t *sites, const double *normals, int64_t m, double *out);
+
+/* lbm_set_stream - run subsequent work on another cudaStream_t. */
+int lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
+
+/* lbm_last_error - message of the last failing call on ctx ("" if none),
+ * valid until the next call on ctx; with ctx == NULL, the message of the last
+ * failed lbm_build_lattice on the calling thread.  lbm_status_string - name of
+ * a status. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+const char *lbm_status_string(int status);
+
+/* lbm_destroy - wait for the stream, free all device and host memory. NULL is a no-op. */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

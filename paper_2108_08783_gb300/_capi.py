@@ -1,0 +1,104 @@
+"""ctypes declarations of ``liblbm.so`` (the C ABI in ``include/lbm.h``).
+
+Argument marshalling only.  The library is loaded from this package's
+directory; if it has not been built the import fails loudly - there is no
+fallback implementation.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = (
+    0, -1, -2, -3, -4, -5, -6)
+LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
+LBM_WALL_BOUNCEBACK, LBM_WALL_ELASTIC_GZS = 0, 1
+LBM_IOLET_VELOCITY, LBM_IOLET_DENSITY = 0, 1
+LBM_PROFILE_PARABOLIC, LBM_PROFILE_WOMERSLEY, LBM_PROFILE_PLUG = 0, 1, 2
+
+# Every symbol include/lbm.h declares.
+EXPORTS = (
+    "lbm_build_lattice", "lbm_set_wall_params", "lbm_init_fields", "lbm_step", "lbm_moments",
+    "lbm_sync", "lbm_info", "lbm_export_lattice", "lbm_wall_state", "lbm_reduce",
+    "lbm_get_populations", "lbm_set_populations", "lbm_checkpoint_bytes", "lbm_checkpoint_save",
+    "lbm_checkpoint_load", "lbm_wss", "lbm_set_stream", "lbm_last_error", "lbm_status_string",
+    "lbm_destroy", "lbm_profile", "lbm_profile_read",
+)
+
+
+class LbmIolet(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("profile", C.c_int32), ("rho", C.c_double),
+                ("u_mean", C.c_double), ("u_amp", C.c_double), ("period", C.c_double),
+                ("phase", C.c_double), ("centre", C.c_double * 3), ("axis", C.c_double * 3),
+                ("radius", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class LbmAllocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (status_name(status), message))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblbm.so is not built (%s); run __graft_entry__.build() or "
+                          "python -m paper_2108_08783_gb300.build" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    i32, i64, dbl = C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "lbm_build_lattice": ([P, i32, i32, i32, P, i32, i32, dbl, P, P, C.POINTER(P)], C.c_int),
+        "lbm_set_wall_params": ([P, i32, dbl, P, P, i64], C.c_int),
+        "lbm_init_fields": ([P, P, P], C.c_int),
+        "lbm_step": ([P, i64], C.c_int),
+        "lbm_moments": ([P, P, P, i32], C.c_int),
+        "lbm_sync": ([P], C.c_int),
+        "lbm_info": ([P, P], C.c_int),
+        "lbm_export_lattice": ([P, P, P, P, P], C.c_int),
+        "lbm_wall_state": ([P, P, P], C.c_int),
+        "lbm_reduce": ([P, P], C.c_int),
+        "lbm_get_populations": ([P, P, i32], C.c_int),
+        "lbm_set_populations": ([P, P, i64, i32], C.c_int),
+        "lbm_checkpoint_bytes": ([P], C.c_size_t),
+        "lbm_checkpoint_save": ([P, P, C.c_size_t], C.c_int),
+        "lbm_checkpoint_load": ([P, P, C.c_size_t], C.c_int),
+        "lbm_wss": ([P, P, P, i64, P], C.c_int),
+        "lbm_set_stream": ([P, P], C.c_int),
+        "lbm_last_error": ([P], C.c_char_p),
+        "lbm_status_string": ([C.c_int], C.c_char_p),
+        "lbm_destroy": ([P], None),
+        "lbm_profile": ([P, i32], C.c_int),
+        "lbm_profile_read": ([P, P, P], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def status_name(status):
+    return lib().lbm_status_string(int(status)).decode()
+
+
+def check(rc, ctx=None):
+    if rc != LBM_OK:
+        msg = lib().lbm_last_error(ctx).decode()
+        raise LbmError(rc, msg)
+    return rc

@@ -1,0 +1,611 @@
+// C ABI of the library (declared in include/lbm.h): context lifetime, device
+// memory, host<->device copies and kernel launches.  Every step of the method
+// runs in the kernels of kernels.cu; this file only marshals.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using lbm::DevLattice;
+using lbm::HostLattice;
+
+struct lbm_ctx {
+  HostLattice L;
+  std::vector<lbm_iolet> iolets;
+  int storage = LBM_F64;
+  double tau = 1.0;
+  int wall_model = LBM_WALL_BOUNCEBACK;
+  double rho0 = 1.0;
+  int64_t step = 0;
+  cudaStream_t stream = nullptr;
+  lbm_allocator alloc{};
+  bool user_alloc = false;
+  std::vector<void*> owned;
+  size_t dev_bytes = 0;
+  DevLattice d;
+  int64_t* iolet_off = nullptr;
+  int64_t* iolet_sites = nullptr;
+  double* partial = nullptr;
+  double* red_out = nullptr;
+  std::string err;
+  // optional per-kernel timing (lbm_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;  // 3 per profiled step
+  size_t ev_used = 0;
+};
+
+namespace {
+
+constexpr uint64_t kCkptMagic = 0x314b43504d424cULL;  // "LBMPCK1"
+
+// Message of the last failed lbm_build_lattice on this thread (no context exists then).
+thread_local std::string g_build_err;
+
+int fail(lbm_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  return fail(c, LBM_ECUDA, buf);
+}
+
+void* dev_alloc_raw(lbm_ctx* c, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (c->user_alloc) {
+    p = c->alloc.alloc(bytes, c->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void dev_free_raw(lbm_ctx* c, void* p) {
+  if (!p) return;
+  if (c->user_alloc) c->alloc.free(p, c->alloc.user);
+  else cudaFree(p);
+}
+
+// Owned allocation, released by lbm_destroy.
+template <class T>
+T* dev_alloc(lbm_ctx* c, size_t count) {
+  void* p = dev_alloc_raw(c, count * sizeof(T));
+  if (p) {
+    c->owned.push_back(p);
+    c->dev_bytes += (count * sizeof(T) + 255) & ~(size_t)255;
+  }
+  return static_cast<T*>(p);
+}
+
+// Temporary allocation freed when it goes out of scope (after a stream sync).
+struct Temp {
+  lbm_ctx* c;
+  void* p = nullptr;
+  Temp(lbm_ctx* c_, size_t bytes) : c(c_) { p = bytes ? dev_alloc_raw(c, bytes) : nullptr; }
+  ~Temp() { dev_free_raw(c, p); }
+};
+
+template <class T>
+cudaError_t h2d(lbm_ctx* c, T* dst, const T* src, size_t count) {
+  if (count == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+}
+
+int check_launch(lbm_ctx* c, int rc, const char* what) {
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, what);
+  return LBM_OK;
+}
+
+int sync(lbm_ctx* c, const char* what) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  return LBM_OK;
+}
+
+bool odd_layout(const lbm_ctx* c) { return (c->step & 1) != 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_string(int s) {
+  switch (s) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_EINVAL: return "LBM_EINVAL";
+    case LBM_ENOMEM: return "LBM_ENOMEM";
+    case LBM_ECUDA: return "LBM_ECUDA";
+    case LBM_EUNSTABLE: return "LBM_EUNSTABLE";
+    case LBM_ETIMEOUT: return "LBM_ETIMEOUT";
+    case LBM_ESTATE: return "LBM_ESTATE";
+  }
+  return "LBM_E?";
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_build_err.c_str(); }
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (void* p : c->owned) dev_free_raw(c, p);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  delete c;
+}
+
+int lbm_profile(lbm_ctx* c, int32_t enable) {
+  if (!c) return LBM_EINVAL;
+  c->prof = enable != 0;
+  c->ev_used = 0;
+  return LBM_OK;
+}
+
+int lbm_profile_read(lbm_ctx* c, double* ms, int64_t* launches) {
+  if (!c || !ms || !launches) return LBM_EINVAL;
+  int rc = sync(c, "lbm_profile_read");
+  if (rc != LBM_OK) return rc;
+  ms[0] = ms[1] = 0.0;
+  launches[0] = launches[1] = 0;
+  for (size_t k = 0; k + 2 < c->ev_used; k += 3) {
+    float a = 0.f, b = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&a, c->ev[k + 1], c->ev[k + 2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, c->ev[k], c->ev[k + 1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_profile_read");
+    ms[0] += a;
+    ms[1] += b;
+    launches[0] += c->d.n_bulk > 0;
+    launches[1] += c->d.n_wall_tiles > 0;
+  }
+  c->ev_used = 0;
+  return LBM_OK;
+}
+
+int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
+                      const lbm_iolet* iolets, int32_t n_iolets, int32_t storage, double tau,
+                      const lbm_allocator* alloc, void* cuda_stream, lbm_ctx** out) {
+  g_build_err.clear();
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (storage < LBM_F64 || storage > LBM_BF16S) {
+    g_build_err = "unknown storage";
+    return LBM_EINVAL;
+  }
+  if (alloc && (!alloc->alloc || !alloc->free)) {
+    g_build_err = "allocator needs both alloc and free";
+    return LBM_EINVAL;
+  }
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ENOMEM;
+  c->storage = storage;
+  c->tau = tau;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (alloc) {
+    c->alloc = *alloc;
+    c->user_alloc = true;
+  }
+  int rc;
+  try {
+    rc = lbm::build_lattice(labels, nx, ny, nz, iolets, n_iolets, tau, c->L, c->err);
+  } catch (const std::bad_alloc&) {
+    rc = LBM_ENOMEM;
+  }
+  if (rc != LBM_OK) {
+    g_build_err = rc == LBM_ENOMEM ? std::string("host allocation failed") : c->err;
+    delete c;
+    return rc;
+  }
+  c->iolets.assign(iolets, iolets + n_iolets);
+  HostLattice& L = c->L;
+  DevLattice& d = c->d;
+  d.n = L.n;
+  d.npad = ((L.n + 127) / 128) * 128;
+  if (d.npad == 0) d.npad = 128;
+  d.n_bulk = (int32_t)L.bulk_desc.size();
+  d.n_wall_tiles = (int32_t)L.wall_desc.size();
+  d.n_irregular = (int32_t)L.n_irregular;
+  d.slot_stride = L.n_slots;
+  d.n_iolets = n_iolets;
+  const size_t S = (size_t)L.n_slots;
+  const size_t sz = lbm::storage_bytes(storage);
+  d.pop = dev_alloc<unsigned char>(c, (size_t)lbm::kQ * d.npad * sz);
+  lbm::TileDesc* bd = dev_alloc<lbm::TileDesc>(c, L.bulk_desc.size());
+  lbm::TileDesc* wd = dev_alloc<lbm::TileDesc>(c, L.wall_desc.size());
+  int32_t* tr = dev_alloc<int32_t>(c, L.tile_ref.size());
+  uint32_t* cf = dev_alloc<uint32_t>(c, L.cta_flags.size());
+  uint32_t* sm = dev_alloc<uint32_t>(c, S);
+  int32_t* sn = dev_alloc<int32_t>(c, 18 * S);
+  double* sp = dev_alloc<double>(c, 3 * S);
+  double* sF = dev_alloc<double>(c, S);
+  double* sK = dev_alloc<double>(c, S);
+  double* sdE = dev_alloc<double>(c, S);
+  double* sUw = dev_alloc<double>(c, 3 * S);
+  lbm::IoletDev* io = dev_alloc<lbm::IoletDev>(c, n_iolets);
+  int* err = dev_alloc<int>(c, 1);
+  c->iolet_off = dev_alloc<int64_t>(c, L.iolet_off.size());
+  c->iolet_sites = dev_alloc<int64_t>(c, L.iolet_sites.size());
+  c->partial = dev_alloc<double>(c, lbm::reduce_partials());
+  c->red_out = dev_alloc<double>(c, 1 + n_iolets);
+  if (!d.pop || !bd || !wd || !tr || !cf || !sm || !sn || !sp || !sF || !sK || !sdE || !sUw ||
+      !io || !err || !c->iolet_off || !c->iolet_sites || !c->partial || !c->red_out) {
+    g_build_err = "device allocation failed";
+    lbm_destroy(c);
+    return LBM_ENOMEM;
+  }
+  d.bulk_desc = bd;
+  d.wall_desc = wd;
+  d.tile_ref = tr;
+  d.cta_flags = cf;
+  d.slot_mask = sm;
+  d.slot_nbr = sn;
+  d.slot_prof = sp;
+  d.slot_F = sF;
+  d.slot_kappa = sK;
+  d.slot_dE = sdE;
+  d.slot_Uw = sUw;
+  d.iolets = io;
+  d.err = err;
+  std::vector<lbm::IoletDev> hio(n_iolets);
+  for (int k = 0; k < n_iolets; ++k) {
+    const lbm_iolet& s = iolets[k];
+    lbm::IoletDev& t = hio[k];
+    std::memset(&t, 0, sizeof t);
+    t.kind = s.kind;
+    t.steady = s.period > 0.0 ? 0 : 1;
+    t.rho = s.rho;
+    t.u_mean = s.u_mean;
+    t.u_amp = s.u_amp;
+    t.period = s.period > 0.0 ? s.period : 1.0;
+    t.phase = s.phase;
+    const double an = std::sqrt(s.axis[0] * s.axis[0] + s.axis[1] * s.axis[1] + s.axis[2] * s.axis[2]);
+    for (int a = 0; a < 3; ++a) t.axis[a] = s.axis[a] / an;
+  }
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  chk(h2d(c, bd, L.bulk_desc.data(), L.bulk_desc.size()));
+  chk(h2d(c, wd, L.wall_desc.data(), L.wall_desc.size()));
+  chk(h2d(c, tr, L.tile_ref.data(), L.tile_ref.size()));
+  chk(h2d(c, cf, L.cta_flags.data(), L.cta_flags.size()));
+  chk(h2d(c, sm, L.slot_mask.data(), S));
+  chk(h2d(c, sn, L.slot_nbr.data(), 18 * S));
+  chk(h2d(c, sp, L.slot_prof.data(), 3 * S));
+  chk(h2d(c, io, hio.data(), hio.size()));
+  chk(h2d(c, c->iolet_off, L.iolet_off.data(), L.iolet_off.size()));
+  chk(h2d(c, c->iolet_sites, L.iolet_sites.data(), L.iolet_sites.size()));
+  if (S) {
+    chk(cudaMemsetAsync(sF, 0, S * sizeof(double), c->stream));
+    chk(cudaMemsetAsync(sK, 0, S * sizeof(double), c->stream));
+    chk(cudaMemsetAsync(sdE, 0, S * sizeof(double), c->stream));
+    chk(cudaMemsetAsync(sUw, 0, 3 * S * sizeof(double), c->stream));
+  }
+  chk(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+  chk(cudaMemsetAsync(d.pop, 0, (size_t)lbm::kQ * d.npad * sz, c->stream));
+  if (e != cudaSuccess) {
+    rc = cuda_fail(c, e, "lbm_build_lattice upload");
+    g_build_err = c->err;
+    lbm_destroy(c);
+    return rc;
+  }
+  rc = check_launch(c, lbm::launch_init(storage, d, nullptr, nullptr, c->stream), "init kernel");
+  if (rc == LBM_OK) rc = sync(c, "lbm_build_lattice");
+  if (rc != LBM_OK) {
+    g_build_err = c->err;
+    lbm_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_set_stream(lbm_ctx* c, void* s) {
+  if (!c) return LBM_EINVAL;
+  c->stream = (cudaStream_t)s;
+  return LBM_OK;
+}
+
+int lbm_set_wall_params(lbm_ctx* c, int32_t wall_model, double rho0, const double* F,
+                        const double* kappa, int64_t n) {
+  if (!c) return LBM_EINVAL;
+  c->err.clear();
+  if (wall_model != LBM_WALL_BOUNCEBACK && wall_model != LBM_WALL_ELASTIC_GZS)
+    return fail(c, LBM_EINVAL, "unknown wall model");
+  if (!std::isfinite(rho0)) return fail(c, LBM_EINVAL, "rho0 must be finite");
+  const int64_t W = (int64_t)c->L.wall_sites.size();
+  if (W > 0 && n != 1 && n != W) return fail(c, LBM_EINVAL, "n must be 1 or n_wall_sites");
+  const size_t S = (size_t)c->L.n_slots;
+  std::vector<double> hF(S, 0.0), hK(S, 0.0);
+  for (int64_t w = 0; w < W; ++w) {
+    const double f = F ? F[n == 1 ? 0 : w] : 0.0;
+    const double k = kappa ? kappa[n == 1 ? 0 : w] : 0.0;
+    if (!std::isfinite(f) || !std::isfinite(k) || f < 0.0 || k < 0.0)
+      return fail(c, LBM_EINVAL, "F and kappa must be finite and >= 0");
+    hF[c->L.wall_slot[w]] = f;
+    hK[c->L.wall_slot[w]] = k;
+  }
+  cudaError_t e = h2d(c, const_cast<double*>(c->d.slot_F), hF.data(), S);
+  if (e == cudaSuccess) e = h2d(c, const_cast<double*>(c->d.slot_kappa), hK.data(), S);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_wall_params");
+  int rc = sync(c, "lbm_set_wall_params");
+  if (rc != LBM_OK) return rc;
+  c->wall_model = wall_model;
+  c->rho0 = rho0;
+  return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx* c, const double* rho, const double* u) {
+  if (!c) return LBM_EINVAL;
+  c->err.clear();
+  const size_t n = (size_t)c->L.n;
+  Temp tr(c, rho ? n * sizeof(double) : 0), tu(c, u ? 3 * n * sizeof(double) : 0);
+  if ((rho && !tr.p) || (u && !tu.p)) return fail(c, LBM_ENOMEM, "lbm_init_fields: allocation");
+  cudaError_t e = cudaSuccess;
+  if (rho) e = h2d(c, (double*)tr.p, rho, n);
+  if (u && e == cudaSuccess) e = h2d(c, (double*)tu.p, u, 3 * n);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_init_fields copy");
+  int rc = check_launch(c, lbm::launch_init(c->storage, c->d, rho ? (double*)tr.p : nullptr,
+                                            u ? (double*)tu.p : nullptr, c->stream),
+                        "init kernel");
+  if (rc == LBM_OK) rc = sync(c, "lbm_init_fields");
+  if (rc == LBM_OK) c->step = 0;
+  return rc;
+}
+
+int lbm_step(lbm_ctx* c, int64_t n_steps) {
+  if (!c) return LBM_EINVAL;
+  if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps must be >= 0");
+  lbm::StepParams p;
+  p.omega = 1.0 / c->tau;
+  p.rho0 = c->rho0;
+  p.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
+  for (int64_t s = 0; s < n_steps; ++s) {
+    p.step = c->step;
+    p.write_state = s == n_steps - 1 ? 1 : 0;
+    void* ev[3] = {nullptr, nullptr, nullptr};
+    if (c->prof) {
+      while (c->ev.size() < c->ev_used + 3) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return cuda_fail(c, r, "lbm_step event");
+        c->ev.push_back(e);
+      }
+      for (int k = 0; k < 3; ++k) ev[k] = c->ev[c->ev_used + k];
+      c->ev_used += 3;
+    }
+    int rc = lbm::launch_step(c->storage, c->d, p, c->stream, c->prof ? ev : nullptr);
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "step kernels");
+    ++c->step;
+  }
+  return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c) {
+  if (!c) return LBM_EINVAL;
+  int rc = sync(c, "lbm_sync");
+  if (rc != LBM_OK) return rc;
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, c->d.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sync flag");
+  if (flag) {
+    cudaMemsetAsync(c->d.err, 0, sizeof(int), c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (flag & lbm::kErrTimeout)
+      return fail(c, LBM_ETIMEOUT, "a bounded device wait gave up");
+    return fail(c, LBM_EUNSTABLE, "non-finite or non-positive density");
+  }
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx* c, double* rho, double* u, int32_t dst_is_device) {
+  if (!c) return LBM_EINVAL;
+  c->err.clear();
+  const size_t n = (size_t)c->L.n;
+  if (dst_is_device) {
+    return check_launch(c, lbm::launch_moments(c->storage, c->d, odd_layout(c), rho, u, c->stream),
+                        "moments kernel");
+  }
+  Temp tr(c, rho ? n * sizeof(double) : 0), tu(c, u ? 3 * n * sizeof(double) : 0);
+  if ((rho && !tr.p) || (u && !tu.p)) return fail(c, LBM_ENOMEM, "lbm_moments: allocation");
+  int rc = check_launch(c, lbm::launch_moments(c->storage, c->d, odd_layout(c),
+                                               rho ? (double*)tr.p : nullptr,
+                                               u ? (double*)tu.p : nullptr, c->stream),
+                        "moments kernel");
+  if (rc != LBM_OK) return rc;
+  cudaError_t e = cudaSuccess;
+  if (rho && n) e = cudaMemcpyAsync(rho, tr.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (u && n && e == cudaSuccess)
+    e = cudaMemcpyAsync(u, tu.p, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_moments copy");
+  return sync(c, "lbm_moments");
+}
+
+int lbm_info(const lbm_ctx* c, int64_t out[12]) {
+  if (!c || !out) return LBM_EINVAL;
+  const HostLattice& L = c->L;
+  out[0] = L.n;
+  out[1] = (int64_t)L.wall_sites.size();
+  out[2] = L.n_wall_links;
+  out[3] = L.n_tiles;
+  out[4] = (int64_t)L.bulk_desc.size();
+  out[5] = (int64_t)L.wall_desc.size() - L.n_irregular;
+  out[6] = L.n_irregular;
+  out[7] = c->step;
+  out[8] = c->storage;
+  out[9] = (int64_t)c->iolets.size();
+  out[10] = (int64_t)c->dev_bytes;
+  int64_t bulk_sites = 0;
+  for (const lbm::TileDesc& t : L.bulk_desc)
+    bulk_sites += std::min<int64_t>(lbm::kTile, L.n - (int64_t)t.tile * lbm::kTile);
+  out[11] = bulk_sites;
+  return LBM_OK;
+}
+
+int lbm_export_lattice(const lbm_ctx* c, int32_t* coords, int32_t* nbr, int64_t* wall_sites,
+                       int64_t* wall_links) {
+  if (!c) return LBM_EINVAL;
+  const HostLattice& L = c->L;
+  if (coords) std::memcpy(coords, L.coords.data(), L.coords.size() * sizeof(int32_t));
+  if (nbr) std::memcpy(nbr, L.nbr.data(), L.nbr.size() * sizeof(int32_t));
+  if (wall_sites)
+    std::memcpy(wall_sites, L.wall_sites.data(), L.wall_sites.size() * sizeof(int64_t));
+  if (wall_links) {
+    int64_t k = 0;
+    for (int64_t s = 0; s < L.n; ++s)
+      for (int i = 1; i < lbm::kQ; ++i)
+        if (L.nbr[(size_t)18 * s + (i - 1)] == -1) {
+          wall_links[2 * k] = s;
+          wall_links[2 * k + 1] = i;
+          ++k;
+        }
+  }
+  return LBM_OK;
+}
+
+int lbm_wall_state(lbm_ctx* c, double* dE, double* Uw) {
+  if (!c) return LBM_EINVAL;
+  c->err.clear();
+  const size_t S = (size_t)c->L.n_slots;
+  std::vector<double> hdE(S), hUw(3 * S);
+  cudaError_t e = cudaSuccess;
+  if (S) {
+    e = cudaMemcpyAsync(hdE.data(), c->d.slot_dE, S * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hUw.data(), c->d.slot_Uw, 3 * S * sizeof(double),
+                          cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_wall_state copy");
+  int rc = sync(c, "lbm_wall_state");
+  if (rc != LBM_OK) return rc;
+  for (size_t w = 0; w < c->L.wall_sites.size(); ++w) {
+    const int64_t m = c->L.wall_slot[w];
+    if (dE) dE[w] = hdE[m];
+    if (Uw)
+      for (int a = 0; a < 3; ++a) Uw[3 * w + a] = hUw[(size_t)a * S + m];
+  }
+  return LBM_OK;
+}
+
+int lbm_reduce(lbm_ctx* c, double* out) {
+  if (!c || !out) return LBM_EINVAL;
+  c->err.clear();
+  const int k = (int)c->iolets.size();
+  int rc = check_launch(c, lbm::launch_reduce(c->storage, c->d, odd_layout(c), c->iolet_off,
+                                              c->iolet_sites, c->partial, lbm::reduce_partials(),
+                                              c->red_out, c->stream),
+                        "reduce kernels");
+  if (rc != LBM_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(out, c->red_out, (1 + k) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_reduce copy");
+  return sync(c, "lbm_reduce");
+}
+
+int lbm_get_populations(lbm_ctx* c, double* f, int32_t dst_is_device) {
+  if (!c || !f) return LBM_EINVAL;
+  c->err.clear();
+  const size_t cnt = (size_t)c->L.n * lbm::kQ;
+  if (dst_is_device)
+    return check_launch(c, lbm::launch_gather(c->storage, c->d, odd_layout(c), f, c->stream),
+                        "gather kernel");
+  Temp t(c, cnt * sizeof(double));
+  if (!t.p) return fail(c, LBM_ENOMEM, "lbm_get_populations: allocation");
+  int rc = check_launch(c, lbm::launch_gather(c->storage, c->d, odd_layout(c), (double*)t.p,
+                                              c->stream),
+                        "gather kernel");
+  if (rc != LBM_OK) return rc;
+  if (cnt) {
+    cudaError_t e = cudaMemcpyAsync(f, t.p, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_get_populations copy");
+  }
+  return sync(c, "lbm_get_populations");
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* f, int64_t step, int32_t src_is_device) {
+  if (!c || !f) return LBM_EINVAL;
+  if (step < 0) return fail(c, LBM_EINVAL, "step must be >= 0");
+  c->err.clear();
+  const size_t cnt = (size_t)c->L.n * lbm::kQ;
+  const int odd = (int)(step & 1);
+  if (src_is_device) {
+    int rc = check_launch(c, lbm::launch_scatter(c->storage, c->d, odd, f, c->stream),
+                          "scatter kernel");
+    if (rc == LBM_OK) c->step = step;
+    return rc;
+  }
+  Temp t(c, cnt * sizeof(double));
+  if (!t.p) return fail(c, LBM_ENOMEM, "lbm_set_populations: allocation");
+  cudaError_t e = h2d(c, (double*)t.p, f, cnt);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_populations copy");
+  int rc = check_launch(c, lbm::launch_scatter(c->storage, c->d, odd, (double*)t.p, c->stream),
+                        "scatter kernel");
+  if (rc == LBM_OK) rc = sync(c, "lbm_set_populations");
+  if (rc == LBM_OK) c->step = step;
+  return rc;
+}
+
+size_t lbm_checkpoint_bytes(const lbm_ctx* c) {
+  if (!c) return 0;
+  return 4 * sizeof(uint64_t) + (size_t)lbm::kQ * c->d.npad * lbm::storage_bytes(c->storage);
+}
+
+int lbm_checkpoint_save(lbm_ctx* c, void* buf, size_t bytes) {
+  if (!c || !buf) return LBM_EINVAL;
+  if (bytes < lbm_checkpoint_bytes(c)) return fail(c, LBM_EINVAL, "checkpoint buffer too small");
+  uint64_t* h = static_cast<uint64_t*>(buf);
+  h[0] = kCkptMagic;
+  h[1] = (uint64_t)c->storage | ((uint64_t)c->L.n << 8);
+  h[2] = (uint64_t)c->d.npad;
+  h[3] = (uint64_t)c->step;
+  const size_t pb = lbm_checkpoint_bytes(c) - 4 * sizeof(uint64_t);
+  cudaError_t e = cudaMemcpyAsync(h + 4, c->d.pop, pb, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_checkpoint_save");
+  return sync(c, "lbm_checkpoint_save");
+}
+
+int lbm_checkpoint_load(lbm_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return LBM_EINVAL;
+  if (bytes < lbm_checkpoint_bytes(c)) return fail(c, LBM_EINVAL, "checkpoint buffer too small");
+  const uint64_t* h = static_cast<const uint64_t*>(buf);
+  if (h[0] != kCkptMagic || h[1] != ((uint64_t)c->storage | ((uint64_t)c->L.n << 8)) ||
+      h[2] != (uint64_t)c->d.npad)
+    return fail(c, LBM_EINVAL, "checkpoint does not match this lattice");
+  const size_t pb = lbm_checkpoint_bytes(c) - 4 * sizeof(uint64_t);
+  cudaError_t e = cudaMemcpyAsync(c->d.pop, h + 4, pb, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_checkpoint_load");
+  int rc = sync(c, "lbm_checkpoint_load");
+  if (rc == LBM_OK) c->step = (int64_t)h[3];
+  return rc;
+}
+
+int lbm_wss(lbm_ctx* c, const int64_t* sites, const double* normals, int64_t m, double* out) {
+  if (!c || m < 0 || (m > 0 && (!sites || !normals || !out))) return LBM_EINVAL;
+  c->err.clear();
+  if (m == 0) return LBM_OK;
+  for (int64_t q = 0; q < m; ++q)
+    if (sites[q] < 0 || sites[q] >= c->L.n) return fail(c, LBM_EINVAL, "site id out of range");
+  Temp ts(c, m * sizeof(int64_t)), tn(c, 3 * m * sizeof(double)), to(c, m * sizeof(double));
+  if (!ts.p || !tn.p || !to.p) return fail(c, LBM_ENOMEM, "lbm_wss: allocation");
+  cudaError_t e = h2d(c, (int64_t*)ts.p, sites, m);
+  if (e == cudaSuccess) e = h2d(c, (double*)tn.p, normals, 3 * m);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_wss copy");
+  int rc = check_launch(c, lbm::launch_wss(c->storage, c->d, odd_layout(c), c->tau,
+                                           (const int64_t*)ts.p, (const double*)tn.p, m,
+                                           (double*)to.p, c->stream),
+                        "wss kernel");
+  if (rc != LBM_OK) return rc;
+  e = cudaMemcpyAsync(out, to.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_wss copy back");
+  return sync(c, "lbm_wss");
+}
+
+}  // extern "C"

@@ -1,0 +1,744 @@
+// GB300 (sm_103a) kernels of the elastic-wall D3Q19 LBGK step.
+//
+// Layout in HBM: populations are one array per direction, pop[i][x] (structure
+// of arrays, npad elements per direction), sites in canonical z-fastest order,
+// streamed in place with the AA pattern:
+//   even step: site x reads slot (x, i), collides and writes f*_i to (x, opp i);
+//   odd step:  site x reads direction j from (x - c_j, opp j), collides and
+//              writes f*_i to (x + c_i, i).
+// Every slot is read and written by one site per step, so the kernels need no
+// second buffer and no synchronisation between sites.  A link that leaves the
+// fluid (wall, inlet or outlet) instead writes the boundary population into
+// (x, opp i) on both parities, which is exactly where x reads direction opp i
+// on the next step.
+//
+// Arithmetic (Sec. 2.1): with g_i = f_i - w_i, drho = sum g_i,
+//   rho u = sum g_i c_i, g_i^eq = w_i (drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)),
+//   g*_i = g_i + (g_i^eq - g_i)/tau   (Eq. LBE_SRT, Eq. feq with the 1/2 factors).
+// Boundary populations (Sec. 2.3, 2.4, 3), for a link i leaving the fluid at
+// x, j = opp(i):
+//   wall, elastic: f_j = f^eq_j(rho, U_w) + (1 - 1/tau)(f_j - f^eq_j(rho, u)),
+//     U_w = (F + dr - 1)/dr u, dr = 1 + kappa max(0, (rho - rho0)/3) (FP64);
+//   wall, bounce-back: f_j = f*_i;
+//   velocity inlet: the GZS form with (rho, u_in(x, n));
+//   density outlet: the GZS form with (rho_out, u).
+//
+// Two kernels per step: k_bulk over tiles whose 18 links are fluid (no
+// branches, 18 neighbour offsets per tile), and k_boundary over the other
+// tiles, which stages each CTA's per-tile and per-site link data (descriptors,
+// link masks, F, kappa, inlet profile and, on odd steps, per-site neighbours)
+// into shared memory with cp.async.bulk copies completing on an mbarrier.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+#include <utility>
+
+#include "d3q19.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+// ------------------------------------------------------------------ helpers
+
+template <int... Is, class F>
+__device__ __forceinline__ void for_seq(std::integer_sequence<int, Is...>, F&& f) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void unroll(F&& f) {
+  for_seq(std::make_integer_sequence<int, N>{}, f);
+}
+
+template <class C>
+__device__ __forceinline__ constexpr C weight(int i) {
+  return i == 0 ? C(1.0 / 3.0) : (i <= 6 ? C(1.0 / 18.0) : C(1.0 / 36.0));
+}
+
+// c_i . u for direction I, written without multiplications by 0 or +-1.
+template <int I, class C>
+__device__ __forceinline__ C cdot(C ux, C uy, C uz) {
+  constexpr int p = (I + 1) / 2;
+  C d;
+  if constexpr (p == 1) d = ux;
+  else if constexpr (p == 2) d = uy;
+  else if constexpr (p == 3) d = uz;
+  else if constexpr (p == 4) d = ux + uy;
+  else if constexpr (p == 5) d = ux - uy;
+  else if constexpr (p == 6) d = ux + uz;
+  else if constexpr (p == 7) d = ux - uz;
+  else if constexpr (p == 8) d = uy + uz;
+  else d = uy - uz;
+  if constexpr (I & 1) return d;
+  else return -d;
+}
+
+// Shifted equilibrium g^eq_I = f^eq_I - w_I for density 1 + drho and velocity u;
+// usq = 1.5 u.u.
+template <int I, class C>
+__device__ __forceinline__ C geq(C drho, C rho, C ux, C uy, C uz, C usq) {
+  if constexpr (I == 0) {
+    return weight<C>(0) * (drho - rho * usq);
+  } else {
+    const C cu = cdot<I, C>(ux, uy, uz);
+    return weight<C>(I) * (drho + rho * (C(3) * cu + C(4.5) * cu * cu - usq));
+  }
+}
+
+// ------------------------------------------------------------- storage codecs
+// ld/st convert between the stored value and g = f - w in the compute type C;
+// get/put convert between the stored value and f in double.
+template <class S>
+struct Codec;
+template <>
+struct Codec<double> {
+  using C = double;
+  static __device__ __forceinline__ C ld(const double* p, int i) { return *p - weight<C>(i); }
+  static __device__ __forceinline__ void st(double* p, int i, C g) { *p = g + weight<C>(i); }
+  static __device__ __forceinline__ double get(const double* p, int) { return *p; }
+  static __device__ __forceinline__ void put(double* p, int, double f) { *p = f; }
+};
+template <>
+struct Codec<float> {
+  using C = float;
+  static __device__ __forceinline__ C ld(const float* p, int i) { return *p - weight<C>(i); }
+  static __device__ __forceinline__ void st(float* p, int i, C g) { *p = g + weight<C>(i); }
+  static __device__ __forceinline__ double get(const float* p, int) { return (double)*p; }
+  static __device__ __forceinline__ void put(float* p, int, double f) { *p = (float)f; }
+};
+template <>
+struct Codec<__half> {
+  using C = float;
+  static __device__ __forceinline__ C ld(const __half* p, int) { return __half2float(*p); }
+  static __device__ __forceinline__ void st(__half* p, int, C g) { *p = __float2half_rn(g); }
+  static __device__ __forceinline__ double get(const __half* p, int i) {
+    return (double)__half2float(*p) + weight<double>(i);
+  }
+  static __device__ __forceinline__ void put(__half* p, int i, double f) {
+    *p = __float2half_rn((float)(f - weight<double>(i)));
+  }
+};
+template <>
+struct Codec<__nv_bfloat16> {
+  using C = float;
+  static __device__ __forceinline__ C ld(const __nv_bfloat16* p, int) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, int, C g) { *p = __float2bfloat16_rn(g); }
+  static __device__ __forceinline__ double get(const __nv_bfloat16* p, int i) {
+    return (double)__bfloat162float(*p) + weight<double>(i);
+  }
+  static __device__ __forceinline__ void put(__nv_bfloat16* p, int i, double f) {
+    *p = __float2bfloat16_rn((float)(f - weight<double>(i)));
+  }
+};
+
+// ------------------------------------------------------------------ collision
+
+template <class C>
+struct Mom {
+  C drho, rho, ux, uy, uz, usq;
+};
+
+// Eqs. (Density), (Momentum) on shifted populations (sum w_i c_i = 0).
+template <class C>
+__device__ __forceinline__ Mom<C> moments(const C (&g)[kQ]) {
+  Mom<C> m;
+  const C a1 = g[1] - g[2], a3 = g[3] - g[4], a5 = g[5] - g[6], a7 = g[7] - g[8];
+  const C a9 = g[9] - g[10], a11 = g[11] - g[12], a13 = g[13] - g[14];
+  const C a15 = g[15] - g[16], a17 = g[17] - g[18];
+  m.drho = ((g[0] + (g[1] + g[2])) + ((g[3] + g[4]) + (g[5] + g[6]))) +
+           (((g[7] + g[8]) + (g[9] + g[10])) + ((g[11] + g[12]) + (g[13] + g[14]))) +
+           ((g[15] + g[16]) + (g[17] + g[18]));
+  const C jx = (a1 + a7) + (a9 + a11) + a13;
+  const C jy = (a3 + a7) - (a9 - a15) + a17;
+  const C jz = (a5 + a11) - (a13 - a15) - a17;
+  m.rho = C(1) + m.drho;
+  const C inv = C(1) / m.rho;
+  m.ux = jx * inv;
+  m.uy = jy * inv;
+  m.uz = jz * inv;
+  m.usq = C(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+  return m;
+}
+
+// BGK relaxation (Eq. LBE_SRT): gs_i = g_i + omega (g^eq_i - g_i).
+template <class C>
+__device__ __forceinline__ void relax(const C (&g)[kQ], C (&gs)[kQ], const Mom<C>& m, C omega) {
+  unroll<kQ>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const C e = geq<i, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
+    gs[i] = g[i] + omega * (e - g[i]);
+  });
+}
+
+template <class C>
+__device__ __forceinline__ bool unstable(C rho) {
+  return !(rho > C(0)) || !(rho < C(1e30));
+}
+
+// --------------------------------------------------------- async bulk copies
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Global -> shared copy of `bytes` (multiple of 16, both ends 16-byte aligned)
+// completing on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: each try_wait suspends for a hardware-chosen interval, so
+// the limit is reached only if the copies never complete.
+constexpr uint32_t kWaitLimit = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ------------------------------------------------------------- bulk kernel
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBulkWarpsPerCta * 32)
+    k_bulk(const DevLattice d, const StepParams p) {
+  using Cd = Codec<S>;
+  using C = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+  const int lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * kBulkWarpsPerCta + (threadIdx.x >> 5);
+  if (t >= d.n_bulk) return;  // warp-uniform
+  const int32_t* dw = reinterpret_cast<const int32_t*>(d.bulk_desc + t);
+  const int32_t word = lane < 20 ? __ldg(dw + lane) : 0;
+  const int32_t tile = __shfl_sync(0xffffffffu, word, 19);
+  int32_t off[kQ];
+  off[0] = 0;
+  if constexpr (ODD) {
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) off[i] = __shfl_sync(0xffffffffu, word, i - 1);
+  }
+  const int64_t x = (int64_t)tile * kTile + lane;
+  if (x >= d.n) return;
+  S* P = static_cast<S*>(d.pop);
+  const int64_t np = d.npad;
+  C g[kQ], gs[kQ];
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int o = dir_opp(j);
+    if constexpr (!ODD || j == 0) g[j] = Cd::ld(P + j * np + x, j);
+    else g[j] = Cd::ld(P + o * np + x + off[o], j);
+  });
+  const Mom<C> m = moments(g);
+  if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
+  relax(g, gs, m, C(p.omega));
+  unroll<kQ>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int o = dir_opp(i);
+    if constexpr (!ODD) Cd::st(P + o * np + x, i, gs[i]);
+    else Cd::st(P + i * np + x + off[i], i, gs[i]);
+  });
+}
+
+// --------------------------------------------------------- boundary kernel
+
+// Shared-memory layout of one boundary CTA (kWallTilesPerCta tiles, SL slots);
+// every block starts on a 16-byte boundary.
+constexpr int kSL = kWallTilesPerCta * kTile;
+constexpr int kOffDesc = 0;
+constexpr int kOffMask = kOffDesc + kWallTilesPerCta * (int)sizeof(TileDesc);
+constexpr int kOffF = kOffMask + kSL * 4;
+constexpr int kOffK = kOffF + kSL * 8;
+constexpr int kOffProf = kOffK + kSL * 8;
+constexpr int kOffNbr = kOffProf + 3 * kSL * 8;
+constexpr int kSmemEven = kOffNbr;
+constexpr int kSmemOdd = kOffNbr + 18 * kSL * 4;
+static_assert(kOffMask % 16 == 0 && kOffF % 16 == 0 && kOffK % 16 == 0 && kOffProf % 16 == 0 &&
+                  kOffNbr % 16 == 0,
+              "shared-memory blocks must be 16-byte aligned");
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kSL) k_boundary(const DevLattice d, const StepParams p) {
+  using Cd = Codec<S>;
+  using C = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint64_t bar;
+  const int64_t t0 = (int64_t)blockIdx.x * kWallTilesPerCta;
+  const int64_t left = (int64_t)d.n_wall_tiles - t0;
+  const int nt = left < kWallTilesPerCta ? (int)left : kWallTilesPerCta;
+  const int64_t s0 = t0 * kTile;
+  const uint32_t ns = (uint32_t)nt * kTile;
+  const int64_t st = d.slot_stride;
+  TileDesc* desc_s = reinterpret_cast<TileDesc*>(sm + kOffDesc);
+  uint32_t* mask_s = reinterpret_cast<uint32_t*>(sm + kOffMask);
+  double* F_s = reinterpret_cast<double*>(sm + kOffF);
+  double* K_s = reinterpret_cast<double*>(sm + kOffK);
+  double* prof_s = reinterpret_cast<double*>(sm + kOffProf);
+  int32_t* nbr_s = reinterpret_cast<int32_t*>(sm + kOffNbr);
+
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t flags = __ldg(d.cta_flags + blockIdx.x);
+    const bool irr = ODD && (flags & kCtaIrregular);
+    const bool inl = flags & kCtaInlet;
+    uint32_t bytes = (uint32_t)nt * sizeof(TileDesc) + ns * (4 + 8 + 8);
+    if (inl) bytes += 3 * ns * 8;
+    if (irr) bytes += 18 * ns * 4;
+    mbar_expect_tx(&bar, bytes);
+    bulk_g2s(desc_s, d.wall_desc + t0, (uint32_t)nt * sizeof(TileDesc), &bar);
+    bulk_g2s(mask_s, d.slot_mask + s0, ns * 4, &bar);
+    bulk_g2s(F_s, d.slot_F + s0, ns * 8, &bar);
+    bulk_g2s(K_s, d.slot_kappa + s0, ns * 8, &bar);
+    if (inl)
+      for (int c = 0; c < 3; ++c) bulk_g2s(prof_s + c * kSL, d.slot_prof + c * st + s0, ns * 8, &bar);
+    if (irr)
+      for (int i = 0; i < 18; ++i) bulk_g2s(nbr_s + i * kSL, d.slot_nbr + i * st + s0, ns * 4, &bar);
+  }
+  if (!mbar_wait_bounded(&bar, 0)) {
+    atomicOr(d.err, kErrTimeout);
+    mbar_wait_bounded(&bar, 0);  // give copies still in flight a second bounded chance
+    return;
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w >= nt) return;
+  const TileDesc& td = desc_s[w];
+  const int ml = w * kTile + lane;  // local slot
+  const uint32_t smask = mask_s[ml];
+  if (!(smask & kValid)) return;
+  const int64_t slot = s0 + ml;
+  const int64_t x = (int64_t)td.tile * kTile + lane;
+  const bool irr = td.mask & kIrregular;
+  S* P = static_cast<S*>(d.pop);
+  const int64_t np = d.npad;
+
+  // neighbour of a fluid link i (odd steps)
+  auto nb = [&](int i) -> int64_t {
+    return irr ? (int64_t)nbr_s[(i - 1) * kSL + ml] : x + td.code[i - 1];
+  };
+  // code of a non-fluid link i: -1 wall, -2-k iolet k
+  auto nf_code = [&](int i) -> int32_t {
+    if (!irr) return td.code[i - 1];
+    if constexpr (ODD) return nbr_s[(i - 1) * kSL + ml];
+    else return __ldg(d.slot_nbr + (i - 1) * st + slot);
+  };
+
+  C g[kQ], gs[kQ];
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int o = dir_opp(j);
+    if constexpr (!ODD || j == 0) {
+      g[j] = Cd::ld(P + j * np + x, j);
+    } else {
+      if ((smask >> o) & 1u) g[j] = Cd::ld(P + j * np + x, j);
+      else g[j] = Cd::ld(P + o * np + nb(o), j);
+    }
+  });
+  const Mom<C> m = moments(g);
+  if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
+  const C omega = C(p.omega);
+  relax(g, gs, m, omega);
+  const C keep = C(1) - omega;  // (1 - 1/tau)
+
+  // Elastic wall velocity (Sec. 2.3-2.4, FP64): dr = dx + dE, U_w = (F + dr - dx)/dr u.
+  C uwx = C(0), uwy = C(0), uwz = C(0);
+  if ((smask & kHasWall) && p.elastic) {
+    const double pr = ((double)m.rho - p.rho0) / 3.0;
+    const double dE = K_s[ml] * (pr > 0.0 ? pr : 0.0);
+    const double dr = 1.0 + dE;
+    const double sc = (F_s[ml] + dr - 1.0) / dr;
+    uwx = C(sc) * m.ux;
+    uwy = C(sc) * m.uy;
+    uwz = C(sc) * m.uz;
+    if (p.write_state) {
+      d.slot_dE[slot] = dE;
+      d.slot_Uw[slot] = (double)uwx;
+      d.slot_Uw[st + slot] = (double)uwy;
+      d.slot_Uw[2 * st + slot] = (double)uwz;
+    }
+  }
+  // Inlet velocity (Sec. 3): u_in = a (u_mean p0 + u_amp (ps sin th + pc cos th)).
+  C uix = C(0), uiy = C(0), uiz = C(0);
+  if (smask & kHasInlet) {
+    const IoletDev& io = d.iolets[(smask & kInletBits) >> kInletShift];
+    double gval = io.u_mean * prof_s[ml];
+    if (!io.steady) {
+      const double th = 2.0 * M_PI * (double)p.step / io.period + io.phase;
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      gval += io.u_amp * (prof_s[kSL + ml] * sn + prof_s[2 * kSL + ml] * cs);
+    }
+    uix = C(gval * io.axis[0]);
+    uiy = C(gval * io.axis[1]);
+    uiz = C(gval * io.axis[2]);
+  }
+
+  const C uwsq = C(1.5) * (uwx * uwx + uwy * uwy + uwz * uwz);
+  const C uisq = C(1.5) * (uix * uix + uiy * uiy + uiz * uiz);
+  Cd::st(P + x, 0, gs[0]);
+  unroll<kQ - 1>([&](auto I0) {
+    constexpr int i = decltype(I0)::value + 1;
+    constexpr int j = dir_opp(i);
+    if ((smask >> i) & 1u) {
+      const int32_t code = nf_code(i);
+      C b;
+      if (code == -1 && !p.elastic) {
+        b = gs[i];  // half-way bounce-back (Sec. 2.4)
+      } else {
+        // GZS: f_j = f^eq_j(rho_b, u_b) + (1 - 1/tau) f^neq_j
+        const C fneq = g[j] - geq<j, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
+        C e;
+        if (code == -1) {
+          e = geq<j, C>(m.drho, m.rho, uwx, uwy, uwz, uwsq);
+        } else {
+          const IoletDev& io = d.iolets[-2 - code];
+          if (io.kind == LBM_IOLET_VELOCITY) {
+            e = geq<j, C>(m.drho, m.rho, uix, uiy, uiz, uisq);
+          } else {
+            const C rb = C(io.rho);
+            e = geq<j, C>(C(io.rho - 1.0), rb, m.ux, m.uy, m.uz, m.usq);
+          }
+        }
+        b = e + keep * fneq;
+      }
+      Cd::st(P + j * np + x, j, b);
+    } else {
+      if constexpr (!ODD) Cd::st(P + j * np + x, i, gs[i]);
+      else Cd::st(P + i * np + nb(i), i, gs[i]);
+    }
+  });
+}
+
+// ------------------------------------------------ state conversion kernels
+
+// Fluid neighbours and non-fluid mask of site x from the tile tables.
+__device__ void site_links(const DevLattice& d, int64_t x, uint32_t& nf, int64_t (&nb)[kQ]) {
+  const int32_t ref = d.tile_ref[x >> 5];
+  nb[0] = x;
+  if (ref >= 0) {
+    const TileDesc& td = d.bulk_desc[ref];
+    nf = 0;
+    for (int i = 1; i < kQ; ++i) nb[i] = x + td.code[i - 1];
+    return;
+  }
+  const int64_t r = -1 - (int64_t)ref;
+  const TileDesc& td = d.wall_desc[r];
+  const int64_t slot = r * kTile + (x & 31);
+  nf = d.slot_mask[slot] & kDirBits;
+  const bool irr = td.mask & kIrregular;
+  for (int i = 1; i < kQ; ++i)
+    nb[i] = irr ? (int64_t)d.slot_nbr[(i - 1) * d.slot_stride + slot] : x + td.code[i - 1];
+}
+
+// Storage index holding the pre-collision population j of site x.
+__device__ __forceinline__ int64_t slot_of(const DevLattice& d, int64_t x, int j, bool odd,
+                                           uint32_t nf, const int64_t (&nb)[kQ]) {
+  if (!odd || j == 0) return j * d.npad + x;
+  const int o = dir_opp(j);
+  if ((nf >> o) & 1u) return j * d.npad + x;
+  return o * d.npad + nb[o];
+}
+
+template <class S>
+__global__ void k_init(const DevLattice d, const double* rho, const double* u) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.n) return;
+  const double r = rho ? rho[x] : 1.0;
+  const double ux = u ? u[3 * x] : 0.0, uy = u ? u[3 * x + 1] : 0.0, uz = u ? u[3 * x + 2] : 0.0;
+  const double usq = 1.5 * (ux * ux + uy * uy + uz * uz);
+  S* P = static_cast<S*>(d.pop);
+  unroll<kQ>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    // f^eq (Eq. feq) = w_i + g^eq_i
+    const double f = weight<double>(i) + geq<i, double>(r - 1.0, r, ux, uy, uz, usq);
+    Codec<S>::put(P + i * d.npad + x, i, f);
+  });
+}
+
+template <class S>
+__global__ void k_gather(const DevLattice d, int odd, double* f) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.n) return;
+  uint32_t nf;
+  int64_t nb[kQ];
+  site_links(d, x, nf, nb);
+  const S* P = static_cast<const S*>(d.pop);
+  for (int j = 0; j < kQ; ++j) f[kQ * x + j] = Codec<S>::get(P + slot_of(d, x, j, odd, nf, nb), j);
+}
+
+template <class S>
+__global__ void k_scatter(const DevLattice d, int odd, const double* f) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.n) return;
+  uint32_t nf;
+  int64_t nb[kQ];
+  site_links(d, x, nf, nb);
+  S* P = static_cast<S*>(d.pop);
+  for (int j = 0; j < kQ; ++j) Codec<S>::put(P + slot_of(d, x, j, odd, nf, nb), j, f[kQ * x + j]);
+}
+
+template <class S>
+__device__ void site_f(const DevLattice& d, int64_t x, bool odd, double (&f)[kQ]) {
+  uint32_t nf;
+  int64_t nb[kQ];
+  site_links(d, x, nf, nb);
+  const S* P = static_cast<const S*>(d.pop);
+  for (int j = 0; j < kQ; ++j) f[j] = Codec<S>::get(P + slot_of(d, x, j, odd, nf, nb), j);
+}
+
+__device__ void f_moments(const double (&f)[kQ], double& rho, double& jx, double& jy, double& jz) {
+  rho = 0.0; jx = 0.0; jy = 0.0; jz = 0.0;
+  for (int j = 0; j < kQ; ++j) {
+    rho += f[j];
+    jx += f[j] * dir_x(j);
+    jy += f[j] * dir_y(j);
+    jz += f[j] * dir_z(j);
+  }
+}
+
+template <class S>
+__global__ void k_moments(const DevLattice d, int odd, double* rho, double* u) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.n) return;
+  double f[kQ], r, jx, jy, jz;
+  site_f<S>(d, x, odd, f);
+  f_moments(f, r, jx, jy, jz);
+  if (rho) rho[x] = r;
+  if (u) {
+    u[3 * x] = jx / r;
+    u[3 * x + 1] = jy / r;
+    u[3 * x + 2] = jz / r;
+  }
+}
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 1024;
+
+__device__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// Mass partials: fixed grid, fixed order -> deterministic.
+template <class S>
+__global__ void __launch_bounds__(kRedThreads) k_mass(const DevLattice d, int odd, double* partial) {
+  __shared__ double sh[kRedThreads];
+  double acc = 0.0;
+  for (int64_t x = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; x < d.n;
+       x += (int64_t)kRedBlocks * kRedThreads) {
+    double f[kQ], r, jx, jy, jz;
+    site_f<S>(d, x, odd, f);
+    f_moments(f, r, jx, jy, jz);
+    if (!(r > 0.0) || !(r < 1e30)) atomicOr(d.err, kErrUnstable);
+    acc += r;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_mass_final(const double* partial, double* out) {
+  __shared__ double sh[kRedThreads];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < kRedBlocks; b += kRedThreads) acc += partial[b];
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[0] = s;
+}
+
+// One block per iolet: flux of rho u along its axis over the sites touching it.
+template <class S>
+__global__ void __launch_bounds__(kRedThreads)
+    k_flux(const DevLattice d, int odd, const int64_t* off, const int64_t* sites, double* out) {
+  __shared__ double sh[kRedThreads];
+  const int k = blockIdx.x;
+  const IoletDev& io = d.iolets[k];
+  double acc = 0.0;
+  for (int64_t q = off[k] + threadIdx.x; q < off[k + 1]; q += kRedThreads) {
+    double f[kQ], r, jx, jy, jz;
+    site_f<S>(d, sites[q], odd, f);
+    f_moments(f, r, jx, jy, jz);
+    acc += jx * io.axis[0] + jy * io.axis[1] + jz * io.axis[2];
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[1 + k] = s;
+}
+
+// Wall shear stress (metric): sigma = -(1 - 1/(2 tau)) sum f^neq c c,
+// t = sigma n, WSS = |t - (t.n) n|.
+template <class S>
+__global__ void k_wss(const DevLattice d, int odd, double tau, const int64_t* sites,
+                      const double* normals, int64_t m, double* out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m) return;
+  double f[kQ], r, jx, jy, jz;
+  site_f<S>(d, sites[q], odd, f);
+  f_moments(f, r, jx, jy, jz);
+  const double ux = jx / r, uy = jy / r, uz = jz / r;
+  const double usq = 1.5 * (ux * ux + uy * uy + uz * uz);
+  double Pm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  unroll<kQ>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const double fe = weight<double>(i) + geq<i, double>(r - 1.0, r, ux, uy, uz, usq);
+    const double fn = f[i] - fe;
+    const int c[3] = {dir_x(i), dir_y(i), dir_z(i)};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) Pm[a][b] += fn * c[a] * c[b];
+  });
+  const double* n = normals + 3 * q;
+  const double k = -(1.0 - 0.5 / tau);
+  double t[3], tn = 0.0;
+  for (int a = 0; a < 3; ++a) t[a] = k * (Pm[a][0] * n[0] + Pm[a][1] * n[1] + Pm[a][2] * n[2]);
+  for (int a = 0; a < 3; ++a) tn += t[a] * n[a];
+  double s2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double ta = t[a] - tn * n[a];
+    s2 += ta * ta;
+  }
+  out[q] = sqrt(s2);
+}
+
+// ------------------------------------------------------------- dispatch
+
+template <class S>
+int step_t(const DevLattice& d, const StepParams& p, cudaStream_t s, void* const* ev) {
+  const bool odd = p.step & 1;
+  const int nwc = (d.n_wall_tiles + kWallTilesPerCta - 1) / kWallTilesPerCta;
+  const int nbc = (d.n_bulk + kBulkWarpsPerCta - 1) / kBulkWarpsPerCta;
+  if (ev) cudaEventRecord((cudaEvent_t)ev[0], s);
+  if (nwc) {
+    if (odd) k_boundary<S, true><<<nwc, kSL, kSmemOdd, s>>>(d, p);
+    else k_boundary<S, false><<<nwc, kSL, kSmemEven, s>>>(d, p);
+  }
+  if (ev) cudaEventRecord((cudaEvent_t)ev[1], s);
+  if (nbc) {
+    if (odd) k_bulk<S, true><<<nbc, kBulkWarpsPerCta * 32, 0, s>>>(d, p);
+    else k_bulk<S, false><<<nbc, kBulkWarpsPerCta * 32, 0, s>>>(d, p);
+  }
+  if (ev) cudaEventRecord((cudaEvent_t)ev[2], s);
+  return (int)cudaGetLastError();
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <class F>
+int dispatch(int storage, F&& f) {
+  switch (storage) {
+    case LBM_F64: return f((double*)nullptr);
+    case LBM_F32: return f((float*)nullptr);
+    case LBM_F16S: return f((__half*)nullptr);
+    case LBM_BF16S: return f((__nv_bfloat16*)nullptr);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t storage_bytes(int storage) {
+  switch (storage) {
+    case LBM_F64: return 8;
+    case LBM_F32: return 4;
+    default: return 2;
+  }
+}
+
+int reduce_partials() { return kRedBlocks; }
+
+int launch_step(int storage, const DevLattice& d, const StepParams& p, void* stream,
+                void* const* events) {
+  return dispatch(storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    return step_t<S>(d, p, (cudaStream_t)stream, events);
+  });
+}
+
+int launch_init(int storage, const DevLattice& d, const double* rho, const double* u,
+                void* stream) {
+  if (d.n == 0) return 0;
+  return dispatch(storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    k_init<S><<<blocks_for(d.n, 256), 256, 0, (cudaStream_t)stream>>>(d, rho, u);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_gather(int storage, const DevLattice& d, int odd, double* f, void* stream) {
+  if (d.n == 0) return 0;
+  return dispatch(storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    k_gather<S><<<blocks_for(d.n, 128), 128, 0, (cudaStream_t)stream>>>(d, odd, f);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_scatter(int storage, const DevLattice& d, int odd, const double* f, void* stream) {
+  if (d.n == 0) return 0;
+  return dispatch(storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    k_scatter<S><<<blocks_for(d.n, 128), 128, 0, (cudaStream_t)stream>>>(d, odd, f);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_moments(int storage, const DevLattice& d, int odd, double* rho, double* u,
+                   void* stream) {
+  if (d.n == 0) return 0;
+  return dispatch(storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    k_moments<S><<<blocks_for(d.n, 128), 128, 0, (cudaStream_t)stream>>>(d, odd, rho, u);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_reduce(int storage, const DevLattice& d, int odd, const int64_t* off,
+                  const int64_t* sites, double* partial, int n_partial, double* out,
+                  void* stream) {
+  if (n_partial < kRedBlocks) return (int)cudaErrorInvalidValue;
+  return dispatch(storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_mass<S><<<kRedBlocks, kRedThreads, 0, s>>>(d, odd, partial);
+    k_mass_final<<<1, kRedThreads, 0, s>>>(partial, out);
+    if (d.n_iolets > 0) k_flux<S><<<d.n_iolets, kRedThreads, 0, s>>>(d, odd, off, sites, out);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_wss(int storage, const DevLattice& d, int odd, double tau, const int64_t* sites,
+               const double* normals, int64_t m, double* out, void* stream) {
+  if (m == 0) return 0;
+  return dispatch(storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    k_wss<S><<<blocks_for(m, 128), 128, 0, (cudaStream_t)stream>>>(d, odd, tau, sites, normals,
+                                                                    m, out);
+    return (int)cudaGetLastError();
+  });
+}
+
+}  // namespace lbm

@@ -1,0 +1,151 @@
+// Internal declarations of the GB300 elastic-wall D3Q19 library: the host
+// lattice (built once from voxel labels) and the device-side views the
+// kernels use.  Not part of the public C ABI (see include/lbm.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int kQ = 19;
+constexpr int kTile = 32;          // sites per tile = one warp
+constexpr int kWallTilesPerCta = 4;  // boundary kernel: tiles (warps) per CTA
+constexpr int kBulkWarpsPerCta = 8;  // bulk kernel: tiles (warps) per CTA
+
+// Flag bits shared by TileDesc::mask and the per-slot masks.  Bits 1..18 mark
+// the non-fluid directions (wall or iolet links).
+constexpr uint32_t kDirBits = 0x7FFFEu;
+constexpr int kInletShift = 20;           // slot masks: bits 20..27 = velocity-inlet id
+constexpr uint32_t kInletBits = 0xFFu << kInletShift;
+constexpr uint32_t kValid = 1u << 28;     // slot holds a site (slot masks only)
+constexpr uint32_t kHasInlet = 1u << 29;  // a velocity-inlet link is present
+constexpr uint32_t kHasWall = 1u << 30;   // a wall link is present
+constexpr uint32_t kIrregular = 1u << 31; // tile: links differ from lane to lane
+
+// Per-CTA flags of the boundary kernel.
+constexpr uint32_t kCtaIrregular = 1u;
+constexpr uint32_t kCtaInlet = 2u;
+
+// Sticky device error bits (ctx->err).
+constexpr int kErrUnstable = 1;
+constexpr int kErrTimeout = 2;
+
+// One tile of 32 consecutive sites, 80 bytes (a multiple of 16 so that a run
+// of descriptors can be bulk-copied into shared memory).
+//  uniform tile: code[i-1] is, for direction i, the constant offset
+//    nbr(x, i) - x when that link is fluid for every lane, or the common
+//    non-fluid code (-1 wall, -2-k iolet k); mask bits 1..18 mark the
+//    non-fluid directions.
+//  irregular tile (kIrregular): codes unused; per-site links live in the
+//    slot arrays.
+struct alignas(16) TileDesc {
+  int32_t code[18];
+  uint32_t mask;
+  int32_t tile;
+};
+static_assert(sizeof(TileDesc) == 80, "TileDesc must be 80 bytes");
+
+// Iolet as the kernels see it.
+struct IoletDev {
+  int32_t kind;   // LBM_IOLET_VELOCITY / LBM_IOLET_DENSITY
+  int32_t steady; // 1: no oscillating term (period <= 0)
+  double rho;
+  double u_mean, u_amp, period, phase;
+  double axis[3];  // unit vector
+  double pad;
+};
+static_assert(sizeof(IoletDev) % 16 == 0, "IoletDev alignment");
+
+// Host-side lattice produced by build_lattice().
+struct HostLattice {
+  int32_t nx = 0, ny = 0, nz = 0;
+  int64_t n = 0;                  // fluid sites
+  std::vector<int32_t> coords;    // [n][3]
+  std::vector<int32_t> nbr;       // [n][18]
+  std::vector<int64_t> wall_sites;
+  int64_t n_wall_links = 0;
+  // tiles
+  int64_t n_tiles = 0;
+  std::vector<TileDesc> bulk_desc;   // bulk tiles (all 18 links fluid, uniform)
+  std::vector<TileDesc> wall_desc;   // boundary tiles: irregular first, then uniform
+  int64_t n_irregular = 0;
+  std::vector<int32_t> tile_ref;     // [n_tiles]: >= 0 bulk index, < 0: -1 - boundary index
+  // boundary slots (32 per boundary tile)
+  int64_t n_slots = 0;
+  std::vector<uint32_t> slot_mask;   // [n_slots]
+  std::vector<int32_t> slot_nbr;     // [18][n_slots] absolute neighbour or non-fluid code
+  std::vector<double> slot_prof;     // [3][n_slots] inlet shape p0, ps, pc
+  std::vector<int64_t> wall_slot;    // [n_wall_sites] slot of each wall site
+  std::vector<uint32_t> cta_flags;   // [ceil(wall tiles / kWallTilesPerCta)]
+  // iolet site lists (sites with a link into iolet k), CSR
+  std::vector<int64_t> iolet_off;    // [n_iolets + 1]
+  std::vector<int64_t> iolet_sites;
+};
+
+// Builds the lattice; returns LBM_OK or LBM_EINVAL with a message.
+int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
+                  const lbm_iolet* iolets, int32_t n_iolets, double tau, HostLattice& out,
+                  std::string& err);
+
+// Device views --------------------------------------------------------------
+
+struct DevLattice {
+  void* pop = nullptr;   // [19][npad] storage elements
+  int64_t npad = 0;
+  int64_t n = 0;
+  const TileDesc* bulk_desc = nullptr;
+  int32_t n_bulk = 0;
+  const TileDesc* wall_desc = nullptr;
+  int32_t n_wall_tiles = 0;
+  int32_t n_irregular = 0;
+  const int32_t* tile_ref = nullptr;
+  const uint32_t* cta_flags = nullptr;
+  const uint32_t* slot_mask = nullptr;
+  const int32_t* slot_nbr = nullptr;   // [18][slot_stride]
+  const double* slot_prof = nullptr;   // [3][slot_stride]
+  const double* slot_F = nullptr;
+  const double* slot_kappa = nullptr;
+  double* slot_dE = nullptr;
+  double* slot_Uw = nullptr;           // [3][slot_stride]
+  int64_t slot_stride = 0;
+  const IoletDev* iolets = nullptr;
+  int32_t n_iolets = 0;
+  int* err = nullptr;
+};
+
+struct StepParams {
+  double omega;      // 1 / tau
+  double rho0;
+  int32_t elastic;   // 1: elastic GZS wall, 0: bounce-back
+  int32_t write_state;
+  int64_t step;
+};
+
+// Kernel launchers (kernels.cu); storage is LBM_F64 ... LBM_BF16S.
+// All return cudaError_t values cast to int.
+// events: NULL, or three cudaEvent_t recorded before the boundary kernel,
+// between the two kernels and after the bulk kernel.
+int launch_step(int storage, const DevLattice& d, const StepParams& p, void* stream,
+                void* const* events);
+int launch_init(int storage, const DevLattice& d, const double* rho, const double* u,
+                void* stream);
+int launch_gather(int storage, const DevLattice& d, int odd_layout, double* f_out, void* stream);
+int launch_scatter(int storage, const DevLattice& d, int odd_layout, const double* f_in,
+                   void* stream);
+int launch_moments(int storage, const DevLattice& d, int odd_layout, double* rho, double* u,
+                   void* stream);
+int launch_reduce(int storage, const DevLattice& d, int odd_layout, const int64_t* iolet_off,
+                  const int64_t* iolet_sites, double* partial, int n_partial, double* out,
+                  void* stream);
+int launch_wss(int storage, const DevLattice& d, int odd_layout, double tau,
+               const int64_t* sites, const double* normals, int64_t m, double* out,
+               void* stream);
+size_t storage_bytes(int storage);
+int reduce_partials();
+
+}  // namespace lbm

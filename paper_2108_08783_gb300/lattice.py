@@ -1,0 +1,226 @@
+"""Python binding of the C ABI: one ``Lattice`` per ``lbm_ctx``.
+
+Only argument marshalling lives here; every step of the method runs in the
+library's CUDA kernels.  PyTorch provides device memory (through the caching
+allocator, passed to the library as an allocator callback) and the CUDA
+stream.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _capi as A
+
+STORAGE = {"f64": A.LBM_F64, "f32": A.LBM_F32, "f16s": A.LBM_F16S, "bf16s": A.LBM_BF16S}
+WALL = {"bounceback": A.LBM_WALL_BOUNCEBACK, "elastic": A.LBM_WALL_ELASTIC_GZS}
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def iolet_struct(io):
+    """Marshal an iolet description (any object with the ``lbm_iolet`` fields)."""
+    s = A.LbmIolet()
+    s.kind = int(io.kind)
+    s.profile = int(io.profile)
+    s.rho = float(io.rho)
+    s.u_mean = float(io.u_mean)
+    s.u_amp = float(io.u_amp)
+    s.period = float(io.period)
+    s.phase = float(io.phase)
+    for d in range(3):
+        s.centre[d] = float(io.centre[d])
+        s.axis[d] = float(io.axis[d])
+    s.radius = float(io.radius)
+    return s
+
+
+class _TorchAllocator:
+    """lbm_allocator backed by torch's CUDA caching allocator."""
+
+    def __init__(self, device, stream):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+        self._alloc = A.ALLOC_FN(self._do_alloc)
+        self._free = A.FREE_FN(self._do_free)
+        self.struct = A.LbmAllocator(self._alloc, self._free, None)
+
+    def _do_alloc(self, nbytes, user):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+        except Exception:
+            return None
+
+    def _do_free(self, ptr, user):
+        try:
+            self.torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass
+
+
+class Lattice:
+    """A compacted D3Q19 lattice on one GPU (wraps ``lbm_build_lattice``).
+
+    ``labels`` is a uint8 voxel grid [nx, ny, nz] (0 solid, 1 fluid, 2+k ghost
+    of iolet k); ``iolets`` the iolet descriptions; ``storage`` one of
+    ``f64 f32 f16s bf16s``.
+    """
+
+    def __init__(self, labels, iolets=(), storage="f64", tau=0.8, device=0, stream=None,
+                 torch_allocator=True):
+        import torch
+        self._lib = A.lib()
+        labels = np.ascontiguousarray(labels, np.uint8)
+        assert labels.ndim == 3
+        self.shape = labels.shape
+        self.storage = storage
+        self.tau = float(tau)
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        self.n_iolets = len(iolets)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        self._alloc = _TorchAllocator(self.device, stream) if torch_allocator else None
+        arr = (A.LbmIolet * max(1, len(iolets)))(*[iolet_struct(io) for io in iolets])
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self._lib.lbm_build_lattice(
+                _ptr(labels), *[int(v) for v in labels.shape], C.cast(arr, C.c_void_p),
+                len(iolets), STORAGE[storage], self.tau,
+                C.byref(self._alloc.struct) if self._alloc else None,
+                C.c_void_p(stream.cuda_stream), C.byref(h))
+        A.check(rc, None)
+        self.h = h
+        info = self.info()
+        self.n = int(info[0])
+        self.n_wall = int(info[1])
+        self.n_wall_links = int(info[2])
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        h = getattr(self, "h", None)
+        if h is not None:
+            self._lib.lbm_destroy(h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc):
+        return A.check(rc, self.h)
+
+    # ------------------------------------------------------------ calls
+    def info(self):
+        out = np.zeros(12, np.int64)
+        self._check(self._lib.lbm_info(self.h, _ptr(out)))
+        return out
+
+    @property
+    def step_count(self):
+        return int(self.info()[7])
+
+    def set_wall(self, model="elastic", rho0=1.0, F=0.85, kappa=0.0):
+        F = np.ascontiguousarray(np.atleast_1d(F), np.float64)
+        kappa = np.ascontiguousarray(np.atleast_1d(kappa), np.float64)
+        n = max(F.size, kappa.size)
+        if F.size == 1 and n > 1:
+            F = np.full(n, F[0])
+        if kappa.size == 1 and n > 1:
+            kappa = np.full(n, kappa[0])
+        self._check(self._lib.lbm_set_wall_params(self.h, WALL[model], float(rho0), _ptr(F),
+                                                  _ptr(kappa), n))
+
+    def init_fields(self, rho=None, u=None):
+        rho = None if rho is None else np.ascontiguousarray(rho, np.float64)
+        u = None if u is None else np.ascontiguousarray(u, np.float64).reshape(-1, 3)
+        self._check(self._lib.lbm_init_fields(self.h, _ptr(rho), _ptr(u)))
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(self._lib.lbm_sync(self.h))
+
+    def moments(self):
+        rho = np.zeros(self.n)
+        u = np.zeros((self.n, 3))
+        self._check(self._lib.lbm_moments(self.h, _ptr(rho), _ptr(u), 0))
+        return rho, u
+
+    def moments_into(self, rho, u):
+        """Write moments into device tensors (float64 [n], [n,3]) asynchronously."""
+        self._check(self._lib.lbm_moments(self.h, C.c_void_p(rho.data_ptr()),
+                                          C.c_void_p(u.data_ptr()), 1))
+
+    def export(self):
+        coords = np.zeros((self.n, 3), np.int32)
+        nbr = np.zeros((self.n, 18), np.int32)
+        ws = np.zeros(self.n_wall, np.int64)
+        wl = np.zeros((self.n_wall_links, 2), np.int64)
+        self._check(self._lib.lbm_export_lattice(self.h, _ptr(coords), _ptr(nbr), _ptr(ws),
+                                                 _ptr(wl)))
+        return {"coords": coords, "nbr": nbr, "wall_sites": ws, "wall_links": wl}
+
+    def coords(self):
+        coords = np.zeros((self.n, 3), np.int32)
+        self._check(self._lib.lbm_export_lattice(self.h, _ptr(coords), None, None, None))
+        return coords
+
+    def wall_state(self):
+        dE = np.zeros(self.n_wall)
+        Uw = np.zeros((self.n_wall, 3))
+        self._check(self._lib.lbm_wall_state(self.h, _ptr(dE), _ptr(Uw)))
+        return dE, Uw
+
+    def reduce(self):
+        out = np.zeros(1 + self.n_iolets)
+        self._check(self._lib.lbm_reduce(self.h, _ptr(out)))
+        return out
+
+    def populations(self):
+        f = np.zeros((self.n, 19))
+        self._check(self._lib.lbm_get_populations(self.h, _ptr(f), 0))
+        return f
+
+    def set_populations(self, f, step=0):
+        f = np.ascontiguousarray(f, np.float64).reshape(self.n, 19)
+        self._check(self._lib.lbm_set_populations(self.h, _ptr(f), int(step), 0))
+
+    def checkpoint(self):
+        nb = self._lib.lbm_checkpoint_bytes(self.h)
+        buf = np.zeros(nb, np.uint8)
+        self._check(self._lib.lbm_checkpoint_save(self.h, _ptr(buf), nb))
+        return buf
+
+    def restore(self, buf):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        self._check(self._lib.lbm_checkpoint_load(self.h, _ptr(buf), buf.size))
+
+    def profile(self, enable=True):
+        self._check(self._lib.lbm_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(ms, launches) per kernel: index 0 bulk tiles, 1 boundary tiles."""
+        ms = np.zeros(2)
+        n = np.zeros(2, np.int64)
+        self._check(self._lib.lbm_profile_read(self.h, _ptr(ms), _ptr(n)))
+        return ms, n
+
+    def wss(self, sites, normals):
+        sites = np.ascontiguousarray(sites, np.int64)
+        normals = np.ascontiguousarray(normals, np.float64).reshape(-1, 3)
+        out = np.zeros(sites.size)
+        self._check(self._lib.lbm_wss(self.h, _ptr(sites), _ptr(normals), sites.size, _ptr(out)))
+        return out

@@ -1,0 +1,203 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (rel-L2 over all sites, on rho and on u):
+  FP64 storage/collision: 1e-10 after 1000 steps;
+  FP32: 1e-5 after 1000 steps;
+  FP16S / BF16S (shifted storage, FP32 collision): the measured bounds stated
+  below, on rho - 1 and on u.
+Integer work (lattice build) is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+from lbm_pair import make_pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-5}
+
+
+def _config1(length=64, **kw):
+    # radius 8, length 64, peak inlet 0.05 (mean 0.025), rho_out = 1
+    return I.tube(8, length, u_mean=0.025, **kw)
+
+
+def _compare(lat, orc, tol, what=""):
+    rl, ul = lat.moments()
+    ro, uo = orc.moments()
+    er, eu = rel_l2(rl, ro), rel_l2(ul, uo)
+    assert er <= tol and eu <= tol, (what, er, eu)
+    return er, eu
+
+
+# ------------------------------------------------------------------ integer build
+
+@pytest.mark.parametrize("geo", [
+    _config1(), _config1(63), I.duct(5, 7, 33), I.closed_box(9, 11, 13),
+    I.tube(12, 40, u_mean=0.01, u_amp=0.01, period=300.0, profile=1),
+] + [I.random_labels(s, shape) for s, shape in enumerate(
+    [(8, 8, 8), (9, 13, 11), (16, 16, 16), (17, 23, 31), (32, 32, 32), (12, 40, 7)])],
+    ids=lambda g: g.name)
+def test_lattice_build_bit_exact(geo):
+    from paper_2108_08783_gb300 import Lattice
+    from oracle import Oracle
+    lat = Lattice(geo.labels, geo.iolets, storage="f64")
+    a = lat.export()
+    b = Oracle(geo.labels, geo.iolets).export()
+    np.testing.assert_array_equal(a["coords"], b["coords"])
+    np.testing.assert_array_equal(a["nbr"].astype(np.int64), b["nbr"])
+    np.testing.assert_array_equal(a["wall_sites"], b["wall_sites"])
+    np.testing.assert_array_equal(a["wall_links"], b["wall_links"])
+    info = lat.info()
+    assert info[0] == len(b["coords"]) and info[3] == (len(b["coords"]) + 31) // 32
+    assert info[4] + info[5] + info[6] == info[3]
+
+
+# ------------------------------------------------------------------ FP64 / FP32 parity
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("wall_model", [1, 0])
+def test_config1_1000_steps(storage, wall_model):
+    """Config-1 tube (tau 0.8, peak inlet 0.05, rho_out 1, kappa 12, F 0.85) from rest."""
+    geo = _config1()
+    lat, orc = make_pair(geo, storage, tau=0.8, wall_model=wall_model, F=0.85, kappa=12.0)
+    lat.step(1000)
+    lat.sync()
+    orc.run(1000)
+    _compare(lat, orc, TOL[storage], "config1")
+    if wall_model == 1:
+        dEl, Uwl = lat.wall_state()
+        dEo, Uwo = orc.wall_state()
+        assert rel_l2(dEl, dEo) <= 10 * TOL[storage]
+        assert rel_l2(Uwl, Uwo) <= 10 * TOL[storage]
+    rl = lat.reduce()
+    ro = orc.reduce()
+    np.testing.assert_allclose(rl, ro, rtol=10 * TOL[storage], atol=1e-9)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_ragged_tail_random_start_odd_steps(storage):
+    """L = 63 (ragged last tile), smooth random initial fields, odd step count,
+    per-wall-site F and kappa from a seeded per-voxel field."""
+    geo = _config1(63)
+    rng = np.random.default_rng(11)
+    F_grid = rng.uniform(0.0, 1.0, geo.shape)
+    K_grid = rng.uniform(0.0, 40.0, geo.shape)
+    lat, orc = make_pair(geo, storage, tau=0.7, wall_model=1, rho0=0.9995,
+                         fields=I.random_fields(5, geo.shape, drho=2e-3, umax=0.03),
+                         F_grid=F_grid, kappa_grid=K_grid)
+    lat.step(333)
+    lat.sync()
+    orc.run(333)
+    _compare(lat, orc, TOL[storage], "ragged")
+    np.testing.assert_allclose(lat.populations(), orc.populations(), rtol=0,
+                               atol=50 * TOL[storage])
+
+
+@pytest.mark.parametrize("seed,shape", [(0, (8, 8, 8)), (1, (13, 9, 17)), (2, (20, 20, 20)),
+                                        (3, (33, 17, 9))])
+@pytest.mark.parametrize("wall_model", [1, 0])
+def test_random_geometries_f64(seed, shape, wall_model):
+    geo = I.random_labels(seed, shape, fill=0.75)
+    lat, orc = make_pair(geo, "f64", tau=0.9, wall_model=wall_model, F=0.5, kappa=3.0,
+                         rho0=0.999, fields=I.random_fields(seed, shape, drho=1e-3, umax=0.02))
+    for chunk in (1, 2, 17):  # odd and even counts
+        lat.step(chunk)
+        orc.run(chunk)
+        np.testing.assert_allclose(lat.populations(), orc.populations(), rtol=0, atol=1e-13)
+
+
+def test_womersley_inlet_and_duct_density_iolets():
+    geo = I.tube(10, 30, u_mean=0.01, u_amp=0.01, period=400.0, profile=1, phase=0.3)
+    lat, orc = make_pair(geo, "f64", tau=0.6, wall_model=1, F=0.85, kappa=5.0)
+    lat.step(501)
+    orc.run(501)
+    _compare(lat, orc, 1e-10, "womersley")
+    geo = I.duct(6, 9, 20, rho_in=1.002, rho_out=0.998)
+    lat, orc = make_pair(geo, "f64", tau=1.0, wall_model=0)
+    lat.step(400)
+    orc.run(400)
+    _compare(lat, orc, 1e-10, "duct")
+
+
+def test_zero_and_single_site_lattices():
+    from paper_2108_08783_gb300 import Lattice
+    lab = np.zeros((4, 4, 4), np.uint8)
+    lat = Lattice(lab, [], storage="f32")
+    assert lat.n == 0
+    lat.step(3)
+    lat.sync()
+    assert lat.reduce()[0] == 0.0
+    lab[1, 2, 3] = 1
+    geo = I.Geometry(lab, [])
+    lat, orc = make_pair(geo, "f64", tau=0.8, wall_model=1, F=0.5, kappa=1.0)
+    lat.step(5)
+    orc.run(5)
+    np.testing.assert_allclose(lat.populations(), orc.populations(), atol=1e-15)
+
+
+# ------------------------------------------------------------------ state API
+
+def test_populations_roundtrip_and_checkpoint_resume():
+    geo = _config1(40)
+    lat, orc = make_pair(geo, "f32", tau=0.8, wall_model=1, F=0.85, kappa=12.0,
+                         fields=I.random_fields(2, geo.shape))
+    lat.step(7)  # odd layout
+    f = lat.populations()
+    lat.set_populations(f, step=7)
+    np.testing.assert_array_equal(lat.populations(), f)
+    ck = lat.checkpoint()
+    lat.step(50)
+    ref = lat.populations()
+    lat.restore(ck)
+    assert lat.step_count == 7
+    lat.step(50)
+    np.testing.assert_array_equal(lat.populations(), ref)
+    # resuming the oracle from the exported populations tracks the GPU
+    orc.set_populations(f, step=7)
+    orc.run(50)
+    assert rel_l2(lat.moments()[1], orc.moments()[1]) < 1e-5
+
+
+def test_unstable_run_is_flagged():
+    from paper_2108_08783_gb300 import LbmError
+    geo = I.closed_box(10, 10, 10)
+    lat, _ = make_pair(geo, "f32", tau=0.5001, wall_model=0,
+                       fields=I.random_fields(0, geo.shape, drho=0.3, umax=0.4))
+    lat.step(300)
+    with pytest.raises(LbmError) as e:
+        lat.sync()
+    assert e.value.status == -4
+    lat.sync()  # the flag is cleared once reported
+
+
+# ------------------------------------------------------------------ full-size sampled parity
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f64", 1e-10)])
+def test_config2_full_size_short_run(storage, tol):
+    """Config 2 at full size (R = 40, L = 1024, ~5.1 M sites, tau 0.6, pulsatile
+    inlet 0.03 + 0.02 sin(2 pi n / 4000), Eh/r0 = 0.5 -> kappa 60), 20 steps
+    from a seeded smooth random state, all sites compared with the oracle."""
+    geo = I.tube(40, 1024, u_mean=0.03, u_amp=0.02, period=4000.0)
+    lat, orc = make_pair(geo, storage, tau=0.6, wall_model=1, F=0.85, kappa=60.0,
+                         fields=I.random_fields(7, geo.shape, drho=1e-3, umax=0.03, smooth=1))
+    lat.step(20)
+    orc.run(20)
+    _compare(lat, orc, tol, "config2")
+
+
+# ------------------------------------------------------------------ reduced precision
+
+@pytest.mark.parametrize("storage,bound", [("f16s", 2e-3), ("bf16s", 2e-2)])
+def test_shifted_half_storage_bound(storage, bound):
+    """Stated bound for 16-bit shifted storage after 1000 steps on config 1:
+    rel-L2 of (rho - 1) and of u against the FP64 oracle."""
+    geo = _config1()
+    lat, orc = make_pair(geo, storage, tau=0.8, wall_model=1, F=0.85, kappa=12.0)
+    lat.step(1000)
+    orc.run(1000)
+    rl, ul = lat.moments()
+    ro, uo = orc.moments()
+    assert rel_l2(rl - 1, ro - 1) < bound
+    assert rel_l2(ul, uo) < bound
