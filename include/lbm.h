@@ -150,13 +150,13 @@ int lbm_sync(lbm_ctx *ctx);
  *   [11] sites in bulk tiles. */
 int lbm_info(const lbm_ctx *ctx, int64_t out[12]);
 
-/* lbm_profile - when enable != 0, lbm_step records CUDA events on the
- * context's stream around each of its two kernels (bulk tiles, boundary
- * tiles); lbm_profile_read waits for the stream and returns the summed device
- * time in ms[0] (bulk kernel) and ms[1] (boundary kernel) and the launch
- * counts, then clears the record.  Measurement only: no work is skipped. */
+/* lbm_profile - when enable != 0, lbm_step records a CUDA event on the
+ * context's stream before and after each launch of its step kernel;
+ * lbm_profile_read waits for the stream, returns the summed device time of
+ * those launches (*ms) and their count (*launches), then clears the record.
+ * Measurement only: no work is skipped. */
 int lbm_profile(lbm_ctx *ctx, int32_t enable);
-int lbm_profile_read(lbm_ctx *ctx, double ms[2], int64_t launches[2]);
+int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches);
 
 /* lbm_export_lattice - the integer lattice (host arrays, any may be NULL):
  *   coords [n_sites][3] int32 voxel coordinates;

@@ -33,8 +33,8 @@ def _stale():
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, src + ".o")
+def _compile(src, extra, bdir):
+    obj = os.path.join(bdir, src + ".o")
     path = os.path.join(CSRC, src)
     if src.endswith(".cu"):
         cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
@@ -48,24 +48,30 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compile and link ``liblbm.so`` if any source is newer; return its path."""
-    if not force and not _stale():
+def build(force=False, verbose=False, extra=(), out=None):
+    """Compile and link ``liblbm.so`` if any source is newer; return its path.
+
+    ``extra`` adds nvcc flags (e.g. ``-DLBM_MINB_F32=4``); ``out`` writes the
+    shared object elsewhere (with its own object directory) instead of the
+    package's ``liblbm.so``."""
+    lib = LIB if out is None else os.path.abspath(out)
+    if out is None and not force and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = BUILD if out is None else lib + ".objs"
+    os.makedirs(bdir, exist_ok=True)
     with ThreadPoolExecutor(len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
+        results = list(ex.map(lambda s: _compile(s, list(extra), bdir), SOURCES))
     if verbose:
         for _, log in results:
             if log:
                 sys.stderr.write(log)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [NVCC, "-shared", *ARCH, "-o", tmp, *[o for o, _ in results], "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

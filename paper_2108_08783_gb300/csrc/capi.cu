@@ -37,7 +37,7 @@ struct lbm_ctx {
   std::string err;
   // optional per-kernel timing (lbm_profile)
   bool prof = false;
-  std::vector<cudaEvent_t> ev;  // 3 per profiled step
+  std::vector<cudaEvent_t> ev;  // 2 per profiled step
   size_t ev_used = 0;
 };
 
@@ -154,17 +154,14 @@ int lbm_profile_read(lbm_ctx* c, double* ms, int64_t* launches) {
   if (!c || !ms || !launches) return LBM_EINVAL;
   int rc = sync(c, "lbm_profile_read");
   if (rc != LBM_OK) return rc;
-  ms[0] = ms[1] = 0.0;
-  launches[0] = launches[1] = 0;
-  for (size_t k = 0; k + 2 < c->ev_used; k += 3) {
-    float a = 0.f, b = 0.f;
-    cudaError_t e = cudaEventElapsedTime(&a, c->ev[k + 1], c->ev[k + 2]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, c->ev[k], c->ev[k + 1]);
+  *ms = 0.0;
+  *launches = 0;
+  for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+    float a = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&a, c->ev[k], c->ev[k + 1]);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_profile_read");
-    ms[0] += a;
-    ms[1] += b;
-    launches[0] += c->d.n_bulk > 0;
-    launches[1] += c->d.n_wall_tiles > 0;
+    *ms += a;
+    *launches += c->d.n_tiles > 0;
   }
   c->ev_used = 0;
   return LBM_OK;
@@ -210,18 +207,13 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   d.n = L.n;
   d.npad = ((L.n + 127) / 128) * 128;
   if (d.npad == 0) d.npad = 128;
-  d.n_bulk = (int32_t)L.bulk_desc.size();
-  d.n_wall_tiles = (int32_t)L.wall_desc.size();
-  d.n_irregular = (int32_t)L.n_irregular;
+  d.n_tiles = L.n_tiles;
   d.slot_stride = L.n_slots;
   d.n_iolets = n_iolets;
   const size_t S = (size_t)L.n_slots;
   const size_t sz = lbm::storage_bytes(storage);
   d.pop = dev_alloc<unsigned char>(c, (size_t)lbm::kQ * d.npad * sz);
-  lbm::TileDesc* bd = dev_alloc<lbm::TileDesc>(c, L.bulk_desc.size());
-  lbm::TileDesc* wd = dev_alloc<lbm::TileDesc>(c, L.wall_desc.size());
-  int32_t* tr = dev_alloc<int32_t>(c, L.tile_ref.size());
-  uint32_t* cf = dev_alloc<uint32_t>(c, L.cta_flags.size());
+  lbm::TileDesc* td = dev_alloc<lbm::TileDesc>(c, L.tiles.size());
   uint32_t* sm = dev_alloc<uint32_t>(c, S);
   int32_t* sn = dev_alloc<int32_t>(c, 18 * S);
   double* sp = dev_alloc<double>(c, 3 * S);
@@ -235,16 +227,13 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   c->iolet_sites = dev_alloc<int64_t>(c, L.iolet_sites.size());
   c->partial = dev_alloc<double>(c, lbm::reduce_partials());
   c->red_out = dev_alloc<double>(c, 1 + n_iolets);
-  if (!d.pop || !bd || !wd || !tr || !cf || !sm || !sn || !sp || !sF || !sK || !sdE || !sUw ||
+  if (!d.pop || !td || !sm || !sn || !sp || !sF || !sK || !sdE || !sUw ||
       !io || !err || !c->iolet_off || !c->iolet_sites || !c->partial || !c->red_out) {
     g_build_err = "device allocation failed";
     lbm_destroy(c);
     return LBM_ENOMEM;
   }
-  d.bulk_desc = bd;
-  d.wall_desc = wd;
-  d.tile_ref = tr;
-  d.cta_flags = cf;
+  d.tiles = td;
   d.slot_mask = sm;
   d.slot_nbr = sn;
   d.slot_prof = sp;
@@ -271,10 +260,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   }
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-  chk(h2d(c, bd, L.bulk_desc.data(), L.bulk_desc.size()));
-  chk(h2d(c, wd, L.wall_desc.data(), L.wall_desc.size()));
-  chk(h2d(c, tr, L.tile_ref.data(), L.tile_ref.size()));
-  chk(h2d(c, cf, L.cta_flags.data(), L.cta_flags.size()));
+  chk(h2d(c, td, L.tiles.data(), L.tiles.size()));
   chk(h2d(c, sm, L.slot_mask.data(), S));
   chk(h2d(c, sn, L.slot_nbr.data(), 18 * S));
   chk(h2d(c, sp, L.slot_prof.data(), 3 * S));
@@ -369,16 +355,16 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
   for (int64_t s = 0; s < n_steps; ++s) {
     p.step = c->step;
     p.write_state = s == n_steps - 1 ? 1 : 0;
-    void* ev[3] = {nullptr, nullptr, nullptr};
+    void* ev[2] = {nullptr, nullptr};
     if (c->prof) {
-      while (c->ev.size() < c->ev_used + 3) {
+      while (c->ev.size() < c->ev_used + 2) {
         cudaEvent_t e;
         cudaError_t r = cudaEventCreate(&e);
         if (r != cudaSuccess) return cuda_fail(c, r, "lbm_step event");
         c->ev.push_back(e);
       }
-      for (int k = 0; k < 3; ++k) ev[k] = c->ev[c->ev_used + k];
-      c->ev_used += 3;
+      for (int k = 0; k < 2; ++k) ev[k] = c->ev[c->ev_used + k];
+      c->ev_used += 2;
     }
     int rc = lbm::launch_step(c->storage, c->d, p, c->stream, c->prof ? ev : nullptr);
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "step kernels");
@@ -435,17 +421,14 @@ int lbm_info(const lbm_ctx* c, int64_t out[12]) {
   out[1] = (int64_t)L.wall_sites.size();
   out[2] = L.n_wall_links;
   out[3] = L.n_tiles;
-  out[4] = (int64_t)L.bulk_desc.size();
-  out[5] = (int64_t)L.wall_desc.size() - L.n_irregular;
+  out[4] = L.n_bulk;
+  out[5] = L.n_uniform;
   out[6] = L.n_irregular;
   out[7] = c->step;
   out[8] = c->storage;
   out[9] = (int64_t)c->iolets.size();
   out[10] = (int64_t)c->dev_bytes;
-  int64_t bulk_sites = 0;
-  for (const lbm::TileDesc& t : L.bulk_desc)
-    bulk_sites += std::min<int64_t>(lbm::kTile, L.n - (int64_t)t.tile * lbm::kTile);
-  out[11] = bulk_sites;
+  out[11] = L.bulk_sites;
   return LBM_OK;
 }
 

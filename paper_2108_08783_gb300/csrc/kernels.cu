@@ -23,11 +23,11 @@
 //   velocity inlet: the GZS form with (rho, u_in(x, n));
 //   density outlet: the GZS form with (rho_out, u).
 //
-// Two kernels per step: k_bulk over tiles whose 18 links are fluid (no
-// branches, 18 neighbour offsets per tile), and k_boundary over the other
-// tiles, which stages each CTA's per-tile and per-site link data (descriptors,
-// link masks, F, kappa, inlet profile and, on odd steps, per-site neighbours)
-// into shared memory with cp.async.bulk copies completing on an mbarrier.
+// One kernel per step (k_step), one warp per tile of 32 sites: bulk tiles
+// (all 18 links fluid) take a branch-free path with 18 neighbour offsets per
+// tile; boundary tiles first stage their per-site link data (link masks, F,
+// kappa, inlet profile and, on odd steps, per-site neighbours) into shared
+// memory with cp.async.bulk copies completing on an mbarrier.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -95,7 +95,7 @@ template <class S>
 struct Codec;
 template <>
 struct Codec<double> {
-  using C = double;
+  using C = double;  // compute type
   static __device__ __forceinline__ C ld(const double* p, int i) { return *p - weight<C>(i); }
   static __device__ __forceinline__ void st(double* p, int i, C g) { *p = g + weight<C>(i); }
   static __device__ __forceinline__ double get(const double* p, int) { return *p; }
@@ -222,30 +222,37 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-// ------------------------------------------------------------- bulk kernel
+// --------------------------------------------------------------- step kernel
+//
+// One warp per tile of 32 consecutive sites, kWarpsPerCta tiles per CTA, in
+// tile order (neighbouring warps touch neighbouring memory).  The tile
+// descriptor (80 bytes) is read by lanes 0..19 and broadcast with shuffles.
+//   bulk tile (mask == 0): branch-free update, 18 neighbour offsets per tile;
+//   boundary tile: lane 0 stages the tile's per-site link data (link masks;
+//     F and kappa if a wall link is present; the inlet profile if an inlet
+//     link is present; on odd steps of an irregular tile the per-site
+//     neighbour table) into the warp's shared-memory area with cp.async.bulk
+//     copies that complete on the warp's mbarrier, then every lane applies
+//     the collision and, for each link leaving the fluid, the boundary rule.
 
+// Per-warp staging area, every block 16-byte aligned.
+constexpr int kStMask = 0;               // 32 x u32
+constexpr int kStF = kStMask + 128;      // 32 x f64
+constexpr int kStK = kStF + 256;         // 32 x f64
+constexpr int kStProf = kStK + 256;      // 3 x 32 x f64
+constexpr int kStNbr = kStProf + 768;    // 18 x 32 x i32
+constexpr int kStBytes = kStNbr + 2304;  // 3712
+static_assert(kStBytes % 16 == 0, "staging blocks must stay 16-byte aligned");
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Branch-free update of a site whose 18 links are fluid.
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kBulkWarpsPerCta * 32)
-    k_bulk(const DevLattice d, const StepParams p) {
+__device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t (&off)[kQ],
+                                            const StepParams& p, int* err) {
   using Cd = Codec<S>;
-  using C = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
-  const int lane = threadIdx.x & 31;
-  const int64_t t = (int64_t)blockIdx.x * kBulkWarpsPerCta + (threadIdx.x >> 5);
-  if (t >= d.n_bulk) return;  // warp-uniform
-  const int32_t* dw = reinterpret_cast<const int32_t*>(d.bulk_desc + t);
-  const int32_t word = lane < 20 ? __ldg(dw + lane) : 0;
-  const int32_t tile = __shfl_sync(0xffffffffu, word, 19);
-  int32_t off[kQ];
-  off[0] = 0;
-  if constexpr (ODD) {
-#pragma unroll
-    for (int i = 1; i < kQ; ++i) off[i] = __shfl_sync(0xffffffffu, word, i - 1);
-  }
-  const int64_t x = (int64_t)tile * kTile + lane;
-  if (x >= d.n) return;
-  S* P = static_cast<S*>(d.pop);
-  const int64_t np = d.npad;
-  C g[kQ], gs[kQ];
+  using C = typename Cd::C;
+  C g[kQ];
   unroll<kQ>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int o = dir_opp(j);
@@ -253,100 +260,45 @@ __global__ void __launch_bounds__(kBulkWarpsPerCta * 32)
     else g[j] = Cd::ld(P + o * np + x + off[o], j);
   });
   const Mom<C> m = moments(g);
-  if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
-  relax(g, gs, m, C(p.omega));
-  unroll<kQ>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    constexpr int o = dir_opp(i);
-    if constexpr (!ODD) Cd::st(P + o * np + x, i, gs[i]);
-    else Cd::st(P + i * np + x + off[i], i, gs[i]);
+  if (unstable(m.rho)) atomicOr(err, kErrUnstable);
+  const C omega = C(p.omega);
+  Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
+  unroll<9>([&](auto Pi) {
+    constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
+    const C sa = g[a] + omega * (geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[a]);
+    const C sb = g[b] + omega * (geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[b]);
+    if constexpr (ODD) {
+      Cd::st(P + a * np + x + off[a], a, sa);
+      Cd::st(P + b * np + x + off[b], b, sb);
+    } else {
+      Cd::st(P + b * np + x, a, sa);
+      Cd::st(P + a * np + x, b, sb);
+    }
   });
 }
 
-// --------------------------------------------------------- boundary kernel
-
-// Shared-memory layout of one boundary CTA (kWallTilesPerCta tiles, SL slots);
-// every block starts on a 16-byte boundary.
-constexpr int kSL = kWallTilesPerCta * kTile;
-constexpr int kOffDesc = 0;
-constexpr int kOffMask = kOffDesc + kWallTilesPerCta * (int)sizeof(TileDesc);
-constexpr int kOffF = kOffMask + kSL * 4;
-constexpr int kOffK = kOffF + kSL * 8;
-constexpr int kOffProf = kOffK + kSL * 8;
-constexpr int kOffNbr = kOffProf + 3 * kSL * 8;
-constexpr int kSmemEven = kOffNbr;
-constexpr int kSmemOdd = kOffNbr + 18 * kSL * 4;
-static_assert(kOffMask % 16 == 0 && kOffF % 16 == 0 && kOffK % 16 == 0 && kOffProf % 16 == 0 &&
-                  kOffNbr % 16 == 0,
-              "shared-memory blocks must be 16-byte aligned");
-
+// Update of a site of a boundary tile.  `code[i]` holds the tile's uniform
+// offsets / non-fluid codes; irregular tiles use the staged per-site table.
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kSL) k_boundary(const DevLattice d, const StepParams p) {
+__device__ __forceinline__ void boundary_update(const DevLattice& d, const StepParams& p, S* P,
+                                                int64_t x, const int32_t (&code)[kQ], bool irr,
+                                                uint32_t smask, const unsigned char* st, int lane,
+                                                int64_t slot) {
   using Cd = Codec<S>;
-  using C = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint64_t bar;
-  const int64_t t0 = (int64_t)blockIdx.x * kWallTilesPerCta;
-  const int64_t left = (int64_t)d.n_wall_tiles - t0;
-  const int nt = left < kWallTilesPerCta ? (int)left : kWallTilesPerCta;
-  const int64_t s0 = t0 * kTile;
-  const uint32_t ns = (uint32_t)nt * kTile;
-  const int64_t st = d.slot_stride;
-  TileDesc* desc_s = reinterpret_cast<TileDesc*>(sm + kOffDesc);
-  uint32_t* mask_s = reinterpret_cast<uint32_t*>(sm + kOffMask);
-  double* F_s = reinterpret_cast<double*>(sm + kOffF);
-  double* K_s = reinterpret_cast<double*>(sm + kOffK);
-  double* prof_s = reinterpret_cast<double*>(sm + kOffProf);
-  int32_t* nbr_s = reinterpret_cast<int32_t*>(sm + kOffNbr);
-
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const uint32_t flags = __ldg(d.cta_flags + blockIdx.x);
-    const bool irr = ODD && (flags & kCtaIrregular);
-    const bool inl = flags & kCtaInlet;
-    uint32_t bytes = (uint32_t)nt * sizeof(TileDesc) + ns * (4 + 8 + 8);
-    if (inl) bytes += 3 * ns * 8;
-    if (irr) bytes += 18 * ns * 4;
-    mbar_expect_tx(&bar, bytes);
-    bulk_g2s(desc_s, d.wall_desc + t0, (uint32_t)nt * sizeof(TileDesc), &bar);
-    bulk_g2s(mask_s, d.slot_mask + s0, ns * 4, &bar);
-    bulk_g2s(F_s, d.slot_F + s0, ns * 8, &bar);
-    bulk_g2s(K_s, d.slot_kappa + s0, ns * 8, &bar);
-    if (inl)
-      for (int c = 0; c < 3; ++c) bulk_g2s(prof_s + c * kSL, d.slot_prof + c * st + s0, ns * 8, &bar);
-    if (irr)
-      for (int i = 0; i < 18; ++i) bulk_g2s(nbr_s + i * kSL, d.slot_nbr + i * st + s0, ns * 4, &bar);
-  }
-  if (!mbar_wait_bounded(&bar, 0)) {
-    atomicOr(d.err, kErrTimeout);
-    mbar_wait_bounded(&bar, 0);  // give copies still in flight a second bounded chance
-    return;
-  }
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (w >= nt) return;
-  const TileDesc& td = desc_s[w];
-  const int ml = w * kTile + lane;  // local slot
-  const uint32_t smask = mask_s[ml];
-  if (!(smask & kValid)) return;
-  const int64_t slot = s0 + ml;
-  const int64_t x = (int64_t)td.tile * kTile + lane;
-  const bool irr = td.mask & kIrregular;
-  S* P = static_cast<S*>(d.pop);
+  using C = typename Cd::C;
   const int64_t np = d.npad;
-
-  // neighbour of a fluid link i (odd steps)
+  const int32_t* nbr_s = reinterpret_cast<const int32_t*>(st + kStNbr);
+  // neighbour index of a fluid link i (odd steps)
   auto nb = [&](int i) -> int64_t {
-    return irr ? (int64_t)nbr_s[(i - 1) * kSL + ml] : x + td.code[i - 1];
+    return irr ? (int64_t)nbr_s[(i - 1) * kTile + lane] : x + code[i];
   };
   // code of a non-fluid link i: -1 wall, -2-k iolet k
-  auto nf_code = [&](int i) -> int32_t {
-    if (!irr) return td.code[i - 1];
-    if constexpr (ODD) return nbr_s[(i - 1) * kSL + ml];
-    else return __ldg(d.slot_nbr + (i - 1) * st + slot);
+  auto nfc = [&](int i) -> int32_t {
+    if (!irr) return code[i];
+    if constexpr (ODD) return nbr_s[(i - 1) * kTile + lane];
+    else return __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
   };
-
-  C g[kQ], gs[kQ];
+  C g[kQ];
   unroll<kQ>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int o = dir_opp(j);
@@ -360,93 +312,161 @@ __global__ void __launch_bounds__(kSL) k_boundary(const DevLattice d, const Step
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
   const C omega = C(p.omega);
-  relax(g, gs, m, omega);
   const C keep = C(1) - omega;  // (1 - 1/tau)
 
   // Elastic wall velocity (Sec. 2.3-2.4, FP64): dr = dx + dE, U_w = (F + dr - dx)/dr u.
   C uwx = C(0), uwy = C(0), uwz = C(0);
   if ((smask & kHasWall) && p.elastic) {
+    const double* F_s = reinterpret_cast<const double*>(st + kStF);
+    const double* K_s = reinterpret_cast<const double*>(st + kStK);
     const double pr = ((double)m.rho - p.rho0) / 3.0;
-    const double dE = K_s[ml] * (pr > 0.0 ? pr : 0.0);
+    const double dE = K_s[lane] * (pr > 0.0 ? pr : 0.0);
     const double dr = 1.0 + dE;
-    const double sc = (F_s[ml] + dr - 1.0) / dr;
+    const double sc = (F_s[lane] + dr - 1.0) / dr;
     uwx = C(sc) * m.ux;
     uwy = C(sc) * m.uy;
     uwz = C(sc) * m.uz;
     if (p.write_state) {
+      const int64_t ss = d.slot_stride;
       d.slot_dE[slot] = dE;
       d.slot_Uw[slot] = (double)uwx;
-      d.slot_Uw[st + slot] = (double)uwy;
-      d.slot_Uw[2 * st + slot] = (double)uwz;
+      d.slot_Uw[ss + slot] = (double)uwy;
+      d.slot_Uw[2 * ss + slot] = (double)uwz;
     }
   }
   // Inlet velocity (Sec. 3): u_in = a (u_mean p0 + u_amp (ps sin th + pc cos th)).
   C uix = C(0), uiy = C(0), uiz = C(0);
   if (smask & kHasInlet) {
+    const double* prof = reinterpret_cast<const double*>(st + kStProf);
     const IoletDev& io = d.iolets[(smask & kInletBits) >> kInletShift];
-    double gval = io.u_mean * prof_s[ml];
+    double gval = io.u_mean * prof[lane];
     if (!io.steady) {
       const double th = 2.0 * M_PI * (double)p.step / io.period + io.phase;
       double sn, cs;
       sincos(th, &sn, &cs);
-      gval += io.u_amp * (prof_s[kSL + ml] * sn + prof_s[2 * kSL + ml] * cs);
+      gval += io.u_amp * (prof[kTile + lane] * sn + prof[2 * kTile + lane] * cs);
     }
     uix = C(gval * io.axis[0]);
     uiy = C(gval * io.axis[1]);
     uiz = C(gval * io.axis[2]);
   }
-
   const C uwsq = C(1.5) * (uwx * uwx + uwy * uwy + uwz * uwz);
   const C uisq = C(1.5) * (uix * uix + uiy * uiy + uiz * uiz);
-  Cd::st(P + x, 0, gs[0]);
-  unroll<kQ - 1>([&](auto I0) {
-    constexpr int i = decltype(I0)::value + 1;
-    constexpr int j = dir_opp(i);
-    if ((smask >> i) & 1u) {
-      const int32_t code = nf_code(i);
-      C b;
-      if (code == -1 && !p.elastic) {
-        b = gs[i];  // half-way bounce-back (Sec. 2.4)
-      } else {
-        // GZS: f_j = f^eq_j(rho_b, u_b) + (1 - 1/tau) f^neq_j
-        const C fneq = g[j] - geq<j, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
-        C e;
-        if (code == -1) {
-          e = geq<j, C>(m.drho, m.rho, uwx, uwy, uwz, uwsq);
-        } else {
-          const IoletDev& io = d.iolets[-2 - code];
-          if (io.kind == LBM_IOLET_VELOCITY) {
-            e = geq<j, C>(m.drho, m.rho, uix, uiy, uiz, uisq);
-          } else {
-            const C rb = C(io.rho);
-            e = geq<j, C>(C(io.rho - 1.0), rb, m.ux, m.uy, m.uz, m.usq);
-          }
-        }
-        b = e + keep * fneq;
-      }
-      Cd::st(P + j * np + x, j, b);
+
+  // Boundary population for direction J when the opposite link leaves the
+  // fluid through `c`: bounce-back (sopp = f*_opp(J)) or the GZS form
+  // f^eq_J(rho_b, u_b) + (1 - 1/tau) f^neq_J.
+  auto bc = [&](auto Jc, int32_t c, C sopp, C fneqJ) -> C {
+    constexpr int J = decltype(Jc)::value;
+    if (c == -1) {
+      if (!p.elastic) return sopp;
+      return geq<J, C>(m.drho, m.rho, uwx, uwy, uwz, uwsq) + keep * fneqJ;
+    }
+    const IoletDev& io = d.iolets[-2 - c];
+    if (io.kind == LBM_IOLET_VELOCITY)
+      return geq<J, C>(m.drho, m.rho, uix, uiy, uiz, uisq) + keep * fneqJ;
+    return geq<J, C>(C(io.rho - 1.0), C(io.rho), m.ux, m.uy, m.uz, m.usq) + keep * fneqJ;
+  };
+
+  Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
+  unroll<9>([&](auto Pi) {
+    constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
+    const C na = g[a] - geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
+    const C nbq = g[b] - geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
+    const C sa = g[a] - omega * na;
+    const C sb = g[b] - omega * nbq;
+    if (!((smask >> a) & 1u)) {
+      if constexpr (ODD) Cd::st(P + a * np + nb(a), a, sa);
+      else Cd::st(P + b * np + x, a, sa);
     } else {
-      if constexpr (!ODD) Cd::st(P + j * np + x, i, gs[i]);
-      else Cd::st(P + i * np + nb(i), i, gs[i]);
+      Cd::st(P + b * np + x, b, bc(std::integral_constant<int, b>{}, nfc(a), sa, nbq));
+    }
+    if (!((smask >> b) & 1u)) {
+      if constexpr (ODD) Cd::st(P + b * np + nb(b), b, sb);
+      else Cd::st(P + a * np + x, b, sb);
+    } else {
+      Cd::st(P + a * np + x, a, bc(std::integral_constant<int, a>{}, nfc(b), sb, na));
     }
   });
+}
+
+// Resident CTAs per SM the register allocation is sized for: FP64 needs more
+// registers per thread (ALU-bound anyway); the 32/16-bit paths trade a few
+// boundary-path spills for occupancy of the HBM-bound bulk path.
+#ifndef LBM_MINB_F64
+#define LBM_MINB_F64 2
+#endif
+#ifndef LBM_MINB_F32
+#define LBM_MINB_F32 3
+#endif
+template <class S>
+struct MinBlocks {
+  static constexpr int value = std::is_same<S, double>::value ? LBM_MINB_F64 : LBM_MINB_F32;
+};
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<S>::value)
+    k_step(const DevLattice d, const StepParams p) {
+  __shared__ __align__(128) unsigned char stage[kWarpsPerCta][kStBytes];
+  __shared__ uint64_t bars[kWarpsPerCta];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * kWarpsPerCta + w;
+  if (t >= d.n_tiles) return;  // warp-uniform
+  const int32_t* dw = reinterpret_cast<const int32_t*>(d.tiles + t);
+  const int32_t word = lane < 20 ? __ldg(dw + lane) : 0;
+  const uint32_t tmask = (uint32_t)__shfl_sync(kFull, word, 18);
+  const int32_t slot0 = __shfl_sync(kFull, word, 19);
+  int32_t code[kQ];
+  code[0] = 0;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) code[i] = __shfl_sync(kFull, word, i - 1);
+  const int64_t x = t * kTile + lane;
+  S* P = static_cast<S*>(d.pop);
+  if (tmask == 0) {
+    if (x < d.n) bulk_update<S, ODD>(P, d.npad, x, code, p, d.err);
+    return;
+  }
+  unsigned char* st = stage[w];
+  uint64_t* bar = &bars[w];
+  const bool irr = tmask & kIrregular;
+  if (lane == 0) mbar_init(bar, 1);
+  __syncwarp();
+  if (lane == 0) {
+    const int64_t ss = d.slot_stride;
+    const bool wall = tmask & kHasWall, inl = tmask & kHasInlet, nbr = ODD && irr;
+    mbar_expect_tx(bar, 128u + (wall ? 512u : 0u) + (inl ? 768u : 0u) + (nbr ? 2304u : 0u));
+    bulk_g2s(st + kStMask, d.slot_mask + slot0, 128, bar);
+    if (wall) {
+      bulk_g2s(st + kStF, d.slot_F + slot0, 256, bar);
+      bulk_g2s(st + kStK, d.slot_kappa + slot0, 256, bar);
+    }
+    if (inl)
+      for (int c = 0; c < 3; ++c) bulk_g2s(st + kStProf + 256 * c, d.slot_prof + c * ss + slot0, 256, bar);
+    if (nbr)
+      for (int i = 0; i < 18; ++i) bulk_g2s(st + kStNbr + 128 * i, d.slot_nbr + i * ss + slot0, 128, bar);
+  }
+  if (!mbar_wait_bounded(bar, 0)) {
+    if (lane == 0) atomicOr(d.err, kErrTimeout);
+    mbar_wait_bounded(bar, 0);  // a second bounded chance for copies still in flight
+    return;
+  }
+  const uint32_t smask = reinterpret_cast<const uint32_t*>(st + kStMask)[lane];
+  if (!(smask & kValid)) return;
+  boundary_update<S, ODD>(d, p, P, x, code, irr, smask, st, lane, (int64_t)slot0 + lane);
 }
 
 // ------------------------------------------------ state conversion kernels
 
 // Fluid neighbours and non-fluid mask of site x from the tile tables.
 __device__ void site_links(const DevLattice& d, int64_t x, uint32_t& nf, int64_t (&nb)[kQ]) {
-  const int32_t ref = d.tile_ref[x >> 5];
+  const TileDesc& td = d.tiles[x >> 5];
   nb[0] = x;
-  if (ref >= 0) {
-    const TileDesc& td = d.bulk_desc[ref];
+  if (td.mask == 0) {
     nf = 0;
     for (int i = 1; i < kQ; ++i) nb[i] = x + td.code[i - 1];
     return;
   }
-  const int64_t r = -1 - (int64_t)ref;
-  const TileDesc& td = d.wall_desc[r];
-  const int64_t slot = r * kTile + (x & 31);
+  const int64_t slot = (int64_t)td.slot + (x & 31);
   nf = d.slot_mask[slot] & kDirBits;
   const bool irr = td.mask & kIrregular;
   for (int i = 1; i < kQ; ++i)
@@ -628,20 +648,13 @@ __global__ void k_wss(const DevLattice d, int odd, double tau, const int64_t* si
 
 template <class S>
 int step_t(const DevLattice& d, const StepParams& p, cudaStream_t s, void* const* ev) {
-  const bool odd = p.step & 1;
-  const int nwc = (d.n_wall_tiles + kWallTilesPerCta - 1) / kWallTilesPerCta;
-  const int nbc = (d.n_bulk + kBulkWarpsPerCta - 1) / kBulkWarpsPerCta;
+  const unsigned nb = (unsigned)((d.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta);
   if (ev) cudaEventRecord((cudaEvent_t)ev[0], s);
-  if (nwc) {
-    if (odd) k_boundary<S, true><<<nwc, kSL, kSmemOdd, s>>>(d, p);
-    else k_boundary<S, false><<<nwc, kSL, kSmemEven, s>>>(d, p);
+  if (nb) {
+    if (p.step & 1) k_step<S, true><<<nb, kWarpsPerCta * 32, 0, s>>>(d, p);
+    else k_step<S, false><<<nb, kWarpsPerCta * 32, 0, s>>>(d, p);
   }
   if (ev) cudaEventRecord((cudaEvent_t)ev[1], s);
-  if (nbc) {
-    if (odd) k_bulk<S, true><<<nbc, kBulkWarpsPerCta * 32, 0, s>>>(d, p);
-    else k_bulk<S, false><<<nbc, kBulkWarpsPerCta * 32, 0, s>>>(d, p);
-  }
-  if (ev) cudaEventRecord((cudaEvent_t)ev[2], s);
   return (int)cudaGetLastError();
 }
 

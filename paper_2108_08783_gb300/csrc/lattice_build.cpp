@@ -184,14 +184,14 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   // ---- tiles
   const int64_t T = (n + kTile - 1) / kTile;
   L.n_tiles = T;
-  L.bulk_desc.clear();
-  L.tile_ref.assign(T, 0);
-  std::vector<TileDesc> irregular, uniform;
+  L.tiles.assign(T, TileDesc{});
+  L.n_bulk = L.n_uniform = L.n_irregular = L.bulk_sites = 0;
+  int64_t nb_tiles = 0;  // boundary tiles so far
   for (int64_t t = 0; t < T; ++t) {
     const int64_t x0 = t * kTile;
     const int lanes = (int)std::min<int64_t>(kTile, n - x0);
-    TileDesc d{};
-    d.tile = (int32_t)t;
+    TileDesc& d = L.tiles[t];
+    d.slot = -1;
     bool uni = true;
     uint32_t flags = 0;
     for (int l = 0; l < lanes; ++l) flags |= site_mask[x0 + l] & (kHasWall | kHasInlet);
@@ -213,37 +213,36 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
       }
     }
     if (uni && d.mask == 0) {
-      L.tile_ref[t] = (int32_t)L.bulk_desc.size();
-      L.bulk_desc.push_back(d);
+      ++L.n_bulk;
+      L.bulk_sites += lanes;
       continue;
     }
     if (!uni) {
       for (int i = 0; i < 18; ++i) d.code[i] = 0;
       d.mask = kIrregular;
+      ++L.n_irregular;
+    } else {
+      ++L.n_uniform;
     }
     d.mask |= flags;
-    (uni ? uniform : irregular).push_back(d);
+    d.slot = (int32_t)(nb_tiles * kTile);
+    ++nb_tiles;
   }
-  L.n_irregular = (int64_t)irregular.size();
-  L.wall_desc = irregular;
-  L.wall_desc.insert(L.wall_desc.end(), uniform.begin(), uniform.end());
-  const int64_t nw = (int64_t)L.wall_desc.size();
   // ---- boundary slots
-  const int64_t S = nw * kTile;
+  const int64_t S = nb_tiles * kTile;
   L.n_slots = S;
   L.slot_mask.assign(S, 0);
   L.slot_nbr.assign((size_t)18 * S, 0);
   L.slot_prof.assign((size_t)3 * S, 0.0);
-  std::vector<int64_t> slot_of_site_wall;  // filled below for wall sites
-  const double nu = (tau - 0.5) / 3.0;     // Eq. (Viscosity), c_s^2 = 1/3
+  const double nu = (tau - 0.5) / 3.0;  // Eq. (Viscosity), c_s^2 = 1/3
   std::vector<int64_t> slot_of(n, -1);
-  for (int64_t r = 0; r < nw; ++r) {
-    const TileDesc& d = L.wall_desc[r];
-    L.tile_ref[d.tile] = (int32_t)(-1 - r);
-    const int64_t x0 = (int64_t)d.tile * kTile;
+  for (int64_t t = 0; t < T; ++t) {
+    const TileDesc& d = L.tiles[t];
+    if (d.slot < 0) continue;
+    const int64_t x0 = t * kTile;
     const int lanes = (int)std::min<int64_t>(kTile, n - x0);
     for (int l = 0; l < lanes; ++l) {
-      const int64_t x = x0 + l, m = r * kTile + l;
+      const int64_t x = x0 + l, m = (int64_t)d.slot + l;
       slot_of[x] = m;
       L.slot_mask[m] = site_mask[x] | kValid;
       for (int i = 0; i < 18; ++i) L.slot_nbr[(size_t)i * S + m] = L.nbr[(size_t)18 * x + i];
@@ -268,7 +267,8 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
         if (io.profile == LBM_PROFILE_WOMERSLEY) {
           ps = 0.0;
           if (q < 1.0) {
-            const double alpha = io.period > 0.0 ? io.radius * std::sqrt(2.0 * M_PI / io.period / nu) : 0.0;
+            const double alpha =
+                io.period > 0.0 ? io.radius * std::sqrt(2.0 * M_PI / io.period / nu) : 0.0;
             const cplx sh = womersley(alpha, std::sqrt(std::max(q, 0.0)));
             ps = sh.real();
             pc = sh.imag();
@@ -282,13 +282,6 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   }
   L.wall_slot.resize(L.wall_sites.size());
   for (size_t w = 0; w < L.wall_sites.size(); ++w) L.wall_slot[w] = slot_of[L.wall_sites[w]];
-  const int64_t nc = (nw + kWallTilesPerCta - 1) / kWallTilesPerCta;
-  L.cta_flags.assign(nc, 0);
-  for (int64_t r = 0; r < nw; ++r) {
-    const uint32_t m = L.wall_desc[r].mask;
-    if (m & kIrregular) L.cta_flags[r / kWallTilesPerCta] |= kCtaIrregular;
-    if (m & kHasInlet) L.cta_flags[r / kWallTilesPerCta] |= kCtaInlet;
-  }
   return LBM_OK;
 }
 

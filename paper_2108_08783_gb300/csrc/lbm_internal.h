@@ -14,8 +14,7 @@ namespace lbm {
 
 constexpr int kQ = 19;
 constexpr int kTile = 32;          // sites per tile = one warp
-constexpr int kWallTilesPerCta = 4;  // boundary kernel: tiles (warps) per CTA
-constexpr int kBulkWarpsPerCta = 8;  // bulk kernel: tiles (warps) per CTA
+constexpr int kWarpsPerCta = 8;    // step kernel: tiles (warps) per CTA
 
 // Flag bits shared by TileDesc::mask and the per-slot masks.  Bits 1..18 mark
 // the non-fluid directions (wall or iolet links).
@@ -27,26 +26,22 @@ constexpr uint32_t kHasInlet = 1u << 29;  // a velocity-inlet link is present
 constexpr uint32_t kHasWall = 1u << 30;   // a wall link is present
 constexpr uint32_t kIrregular = 1u << 31; // tile: links differ from lane to lane
 
-// Per-CTA flags of the boundary kernel.
-constexpr uint32_t kCtaIrregular = 1u;
-constexpr uint32_t kCtaInlet = 2u;
-
 // Sticky device error bits (ctx->err).
 constexpr int kErrUnstable = 1;
 constexpr int kErrTimeout = 2;
 
-// One tile of 32 consecutive sites, 80 bytes (a multiple of 16 so that a run
-// of descriptors can be bulk-copied into shared memory).
-//  uniform tile: code[i-1] is, for direction i, the constant offset
-//    nbr(x, i) - x when that link is fluid for every lane, or the common
-//    non-fluid code (-1 wall, -2-k iolet k); mask bits 1..18 mark the
-//    non-fluid directions.
-//  irregular tile (kIrregular): codes unused; per-site links live in the
-//    slot arrays.
+// One tile of 32 consecutive sites, 80 bytes, read by one warp (lanes 0..19).
+//  bulk tile: mask == 0 and code[i-1] = nbr(x, i) - x, the same for every
+//    lane; slot = -1.
+//  uniform boundary tile: as above, except that for the non-fluid directions
+//    (mask bits 1..18) code[i-1] is the common non-fluid code (-1 wall, -2-k
+//    iolet k); mask also carries kHasWall / kHasInlet; slot = first slot.
+//  irregular tile (kIrregular): links differ between lanes; codes unused and
+//    the per-site links live in the slot arrays.
 struct alignas(16) TileDesc {
   int32_t code[18];
   uint32_t mask;
-  int32_t tile;
+  int32_t slot;
 };
 static_assert(sizeof(TileDesc) == 80, "TileDesc must be 80 bytes");
 
@@ -69,19 +64,16 @@ struct HostLattice {
   std::vector<int32_t> nbr;       // [n][18]
   std::vector<int64_t> wall_sites;
   int64_t n_wall_links = 0;
-  // tiles
+  // tiles (32 sites each, in site order)
   int64_t n_tiles = 0;
-  std::vector<TileDesc> bulk_desc;   // bulk tiles (all 18 links fluid, uniform)
-  std::vector<TileDesc> wall_desc;   // boundary tiles: irregular first, then uniform
-  int64_t n_irregular = 0;
-  std::vector<int32_t> tile_ref;     // [n_tiles]: >= 0 bulk index, < 0: -1 - boundary index
-  // boundary slots (32 per boundary tile)
+  std::vector<TileDesc> tiles;
+  int64_t n_bulk = 0, n_uniform = 0, n_irregular = 0, bulk_sites = 0;
+  // boundary slots (32 per boundary tile, in tile order)
   int64_t n_slots = 0;
   std::vector<uint32_t> slot_mask;   // [n_slots]
   std::vector<int32_t> slot_nbr;     // [18][n_slots] absolute neighbour or non-fluid code
   std::vector<double> slot_prof;     // [3][n_slots] inlet shape p0, ps, pc
   std::vector<int64_t> wall_slot;    // [n_wall_sites] slot of each wall site
-  std::vector<uint32_t> cta_flags;   // [ceil(wall tiles / kWallTilesPerCta)]
   // iolet site lists (sites with a link into iolet k), CSR
   std::vector<int64_t> iolet_off;    // [n_iolets + 1]
   std::vector<int64_t> iolet_sites;
@@ -98,13 +90,8 @@ struct DevLattice {
   void* pop = nullptr;   // [19][npad] storage elements
   int64_t npad = 0;
   int64_t n = 0;
-  const TileDesc* bulk_desc = nullptr;
-  int32_t n_bulk = 0;
-  const TileDesc* wall_desc = nullptr;
-  int32_t n_wall_tiles = 0;
-  int32_t n_irregular = 0;
-  const int32_t* tile_ref = nullptr;
-  const uint32_t* cta_flags = nullptr;
+  const TileDesc* tiles = nullptr;
+  int64_t n_tiles = 0;
   const uint32_t* slot_mask = nullptr;
   const int32_t* slot_nbr = nullptr;   // [18][slot_stride]
   const double* slot_prof = nullptr;   // [3][slot_stride]
@@ -128,8 +115,7 @@ struct StepParams {
 
 // Kernel launchers (kernels.cu); storage is LBM_F64 ... LBM_BF16S.
 // All return cudaError_t values cast to int.
-// events: NULL, or three cudaEvent_t recorded before the boundary kernel,
-// between the two kernels and after the bulk kernel.
+// events: NULL, or two cudaEvent_t recorded before and after the step kernel.
 int launch_step(int storage, const DevLattice& d, const StepParams& p, void* stream,
                 void* const* events);
 int launch_init(int storage, const DevLattice& d, const double* rho, const double* u,

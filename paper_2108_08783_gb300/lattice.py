@@ -212,11 +212,11 @@ class Lattice:
         self._check(self._lib.lbm_profile(self.h, 1 if enable else 0))
 
     def profile_read(self):
-        """(ms, launches) per kernel: index 0 bulk tiles, 1 boundary tiles."""
-        ms = np.zeros(2)
-        n = np.zeros(2, np.int64)
+        """(summed device ms, launch count) of the step kernel since profile(True)."""
+        ms = np.zeros(1)
+        n = np.zeros(1, np.int64)
         self._check(self._lib.lbm_profile_read(self.h, _ptr(ms), _ptr(n)))
-        return ms, n
+        return float(ms[0]), int(n[0])
 
     def wss(self, sites, normals):
         sites = np.ascontiguousarray(sites, np.int64)
