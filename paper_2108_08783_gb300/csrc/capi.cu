@@ -281,6 +281,20 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     lbm_destroy(c);
     return rc;
   }
+  {
+    int dev = 0, sms = 0;
+    cudaError_t ge = cudaGetDevice(&dev);
+    if (ge == cudaSuccess) ge = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = ge == cudaSuccess ? lbm::step_grid(storage, sms) : -(int)ge;
+    if (grid <= 0) {
+      rc = cuda_fail(c, grid < 0 ? (cudaError_t)(-grid) : cudaErrorInvalidConfiguration,
+                     "step kernel occupancy");
+      g_build_err = c->err;
+      lbm_destroy(c);
+      return rc;
+    }
+    d.step_grid = grid;
+  }
   rc = check_launch(c, lbm::launch_init(storage, d, nullptr, nullptr, c->stream), "init kernel");
   if (rc == LBM_OK) rc = sync(c, "lbm_build_lattice");
   if (rc != LBM_OK) {
@@ -355,6 +369,15 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
   for (int64_t s = 0; s < n_steps; ++s) {
     p.step = c->step;
     p.write_state = s == n_steps - 1 ? 1 : 0;
+    for (int k = 0; k < lbm::kMaxTimedInlets; ++k) {
+      p.inlet_sin[k] = p.inlet_cos[k] = 0.0;
+      if (k < (int)c->iolets.size() && c->iolets[k].period > 0.0) {
+        const lbm_iolet& io = c->iolets[k];
+        const double th = 2.0 * M_PI * (double)c->step / io.period + io.phase;
+        p.inlet_sin[k] = io.u_amp * std::sin(th);
+        p.inlet_cos[k] = io.u_amp * std::cos(th);
+      }
+    }
     void* ev[2] = {nullptr, nullptr};
     if (c->prof) {
       while (c->ev.size() < c->ev_used + 2) {

@@ -248,7 +248,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Branch-free update of a site whose 18 links are fluid.
 template <class S, bool ODD>
-__device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t (&off)[kQ],
+__device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t* dsc,
                                             const StepParams& p, int* err) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
@@ -257,7 +257,7 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
     constexpr int j = decltype(J)::value;
     constexpr int o = dir_opp(j);
     if constexpr (!ODD || j == 0) g[j] = Cd::ld(P + j * np + x, j);
-    else g[j] = Cd::ld(P + o * np + x + off[o], j);
+    else g[j] = Cd::ld(P + o * np + x + dsc[o - 1], j);
   });
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(err, kErrUnstable);
@@ -268,8 +268,8 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
     const C sa = g[a] + omega * (geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[a]);
     const C sb = g[b] + omega * (geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[b]);
     if constexpr (ODD) {
-      Cd::st(P + a * np + x + off[a], a, sa);
-      Cd::st(P + b * np + x + off[b], b, sb);
+      Cd::st(P + a * np + x + dsc[a - 1], a, sa);
+      Cd::st(P + b * np + x + dsc[b - 1], b, sb);
     } else {
       Cd::st(P + b * np + x, a, sa);
       Cd::st(P + a * np + x, b, sb);
@@ -281,7 +281,7 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
 // offsets / non-fluid codes; irregular tiles use the staged per-site table.
 template <class S, bool ODD>
 __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepParams& p, S* P,
-                                                int64_t x, const int32_t (&code)[kQ], bool irr,
+                                                int64_t x, const int32_t* dsc, bool irr,
                                                 uint32_t smask, const unsigned char* st, int lane,
                                                 int64_t slot) {
   using Cd = Codec<S>;
@@ -290,11 +290,11 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   const int32_t* nbr_s = reinterpret_cast<const int32_t*>(st + kStNbr);
   // neighbour index of a fluid link i (odd steps)
   auto nb = [&](int i) -> int64_t {
-    return irr ? (int64_t)nbr_s[(i - 1) * kTile + lane] : x + code[i];
+    return irr ? (int64_t)nbr_s[(i - 1) * kTile + lane] : x + dsc[i - 1];
   };
   // code of a non-fluid link i: -1 wall, -2-k iolet k
   auto nfc = [&](int i) -> int32_t {
-    if (!irr) return code[i];
+    if (!irr) return dsc[i - 1];
     if constexpr (ODD) return nbr_s[(i - 1) * kTile + lane];
     else return __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
   };
@@ -338,13 +338,24 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   C uix = C(0), uiy = C(0), uiz = C(0);
   if (smask & kHasInlet) {
     const double* prof = reinterpret_cast<const double*>(st + kStProf);
-    const IoletDev& io = d.iolets[(smask & kInletBits) >> kInletShift];
+    const int k = (int)((smask & kInletBits) >> kInletShift);
+    const IoletDev& io = d.iolets[k];
     double gval = io.u_mean * prof[lane];
     if (!io.steady) {
-      const double th = 2.0 * M_PI * (double)p.step / io.period + io.phase;
-      double sn, cs;
-      sincos(th, &sn, &cs);
-      gval += io.u_amp * (prof[kTile + lane] * sn + prof[2 * kTile + lane] * cs);
+      // time factors u_amp sin(th), u_amp cos(th) of this step, from the host
+      // for the first kMaxTimedInlets iolets, else evaluated here
+      double as, ac;
+      if (k < kMaxTimedInlets) {
+        as = p.inlet_sin[k];
+        ac = p.inlet_cos[k];
+      } else {
+        const double th = 2.0 * M_PI * (double)p.step / io.period + io.phase;
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        as = io.u_amp * sn;
+        ac = io.u_amp * cs;
+      }
+      gval += prof[kTile + lane] * as + prof[2 * kTile + lane] * ac;
     }
     uix = C(gval * io.axis[0]);
     uiy = C(gval * io.axis[1]);
@@ -408,51 +419,58 @@ template <class S, bool ODD>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<S>::value)
     k_step(const DevLattice d, const StepParams p) {
   __shared__ __align__(128) unsigned char stage[kWarpsPerCta][kStBytes];
+  __shared__ __align__(16) int32_t desc_s[kWarpsPerCta][20];
   __shared__ uint64_t bars[kWarpsPerCta];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t t = (int64_t)blockIdx.x * kWarpsPerCta + w;
-  if (t >= d.n_tiles) return;  // warp-uniform
-  const int32_t* dw = reinterpret_cast<const int32_t*>(d.tiles + t);
-  const int32_t word = lane < 20 ? __ldg(dw + lane) : 0;
-  const uint32_t tmask = (uint32_t)__shfl_sync(kFull, word, 18);
-  const int32_t slot0 = __shfl_sync(kFull, word, 19);
-  int32_t code[kQ];
-  code[0] = 0;
-#pragma unroll
-  for (int i = 1; i < kQ; ++i) code[i] = __shfl_sync(kFull, word, i - 1);
-  const int64_t x = t * kTile + lane;
-  S* P = static_cast<S*>(d.pop);
-  if (tmask == 0) {
-    if (x < d.n) bulk_update<S, ODD>(P, d.npad, x, code, p, d.err);
-    return;
-  }
   unsigned char* st = stage[w];
+  int32_t* dsc = desc_s[w];
   uint64_t* bar = &bars[w];
-  const bool irr = tmask & kIrregular;
   if (lane == 0) mbar_init(bar, 1);
   __syncwarp();
-  if (lane == 0) {
-    const int64_t ss = d.slot_stride;
-    const bool wall = tmask & kHasWall, inl = tmask & kHasInlet, nbr = ODD && irr;
-    mbar_expect_tx(bar, 128u + (wall ? 512u : 0u) + (inl ? 768u : 0u) + (nbr ? 2304u : 0u));
-    bulk_g2s(st + kStMask, d.slot_mask + slot0, 128, bar);
-    if (wall) {
-      bulk_g2s(st + kStF, d.slot_F + slot0, 256, bar);
-      bulk_g2s(st + kStK, d.slot_kappa + slot0, 256, bar);
+  uint32_t phase = 0;
+  S* P = static_cast<S*>(d.pop);
+  const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerCta;
+  // persistent: every warp strides over the tiles
+  for (int64_t t = (int64_t)blockIdx.x * kWarpsPerCta + w; t < d.n_tiles; t += nwarps) {
+    if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.tiles + t) + lane);
+    __syncwarp();
+    const uint32_t tmask = (uint32_t)dsc[18];
+    const int64_t x = t * kTile + lane;
+    if (tmask == 0) {
+      if (x < d.n) bulk_update<S, ODD>(P, d.npad, x, dsc, p, d.err);
+    } else {
+      const int32_t slot0 = dsc[19];
+      const bool irr = tmask & kIrregular;
+      if (lane == 0) {
+        const int64_t ss = d.slot_stride;
+        const bool wall = tmask & kHasWall, inl = tmask & kHasInlet, nbr = ODD && irr;
+        // order this warp's earlier generic reads of the staging area before the async writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, 128u + (wall ? 512u : 0u) + (inl ? 768u : 0u) + (nbr ? 2304u : 0u));
+        bulk_g2s(st + kStMask, d.slot_mask + slot0, 128, bar);
+        if (wall) {
+          bulk_g2s(st + kStF, d.slot_F + slot0, 256, bar);
+          bulk_g2s(st + kStK, d.slot_kappa + slot0, 256, bar);
+        }
+        if (inl)
+          for (int c = 0; c < 3; ++c)
+            bulk_g2s(st + kStProf + 256 * c, d.slot_prof + c * ss + slot0, 256, bar);
+        if (nbr)
+          for (int i = 0; i < 18; ++i)
+            bulk_g2s(st + kStNbr + 128 * i, d.slot_nbr + i * ss + slot0, 128, bar);
+      }
+      if (!mbar_wait_bounded(bar, phase)) {
+        if (lane == 0) atomicOr(d.err, kErrTimeout);
+        mbar_wait_bounded(bar, phase);  // a second bounded chance for copies in flight
+        return;
+      }
+      phase ^= 1u;
+      const uint32_t smask = reinterpret_cast<const uint32_t*>(st + kStMask)[lane];
+      if (smask & kValid)
+        boundary_update<S, ODD>(d, p, P, x, dsc, irr, smask, st, lane, (int64_t)slot0 + lane);
     }
-    if (inl)
-      for (int c = 0; c < 3; ++c) bulk_g2s(st + kStProf + 256 * c, d.slot_prof + c * ss + slot0, 256, bar);
-    if (nbr)
-      for (int i = 0; i < 18; ++i) bulk_g2s(st + kStNbr + 128 * i, d.slot_nbr + i * ss + slot0, 128, bar);
+    __syncwarp();  // the tile's descriptor and staging area are free again
   }
-  if (!mbar_wait_bounded(bar, 0)) {
-    if (lane == 0) atomicOr(d.err, kErrTimeout);
-    mbar_wait_bounded(bar, 0);  // a second bounded chance for copies still in flight
-    return;
-  }
-  const uint32_t smask = reinterpret_cast<const uint32_t*>(st + kStMask)[lane];
-  if (!(smask & kValid)) return;
-  boundary_update<S, ODD>(d, p, P, x, code, irr, smask, st, lane, (int64_t)slot0 + lane);
 }
 
 // ------------------------------------------------ state conversion kernels
@@ -647,8 +665,20 @@ __global__ void k_wss(const DevLattice d, int odd, double tau, const int64_t* si
 // ------------------------------------------------------------- dispatch
 
 template <class S>
+int step_grid_t(int sms) {
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<S, false>,
+                                                                kWarpsPerCta * 32, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<S, true>, kWarpsPerCta * 32, 0);
+  if (e != cudaSuccess) return -(int)e;
+  return (a < b ? a : b) * sms;
+}
+
+template <class S>
 int step_t(const DevLattice& d, const StepParams& p, cudaStream_t s, void* const* ev) {
-  const unsigned nb = (unsigned)((d.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta);
+  const int64_t need = (d.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta;
+  const unsigned nb = (unsigned)(need < d.step_grid ? need : d.step_grid);
   if (ev) cudaEventRecord((cudaEvent_t)ev[0], s);
   if (nb) {
     if (p.step & 1) k_step<S, true><<<nb, kWarpsPerCta * 32, 0, s>>>(d, p);
@@ -682,6 +712,13 @@ size_t storage_bytes(int storage) {
 }
 
 int reduce_partials() { return kRedBlocks; }
+
+int step_grid(int storage, int sms) {
+  return dispatch(storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    return step_grid_t<S>(sms);
+  });
+}
 
 int launch_step(int storage, const DevLattice& d, const StepParams& p, void* stream,
                 void* const* events) {

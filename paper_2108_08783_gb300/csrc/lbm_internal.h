@@ -103,7 +103,11 @@ struct DevLattice {
   const IoletDev* iolets = nullptr;
   int32_t n_iolets = 0;
   int* err = nullptr;
+  int64_t step_grid = 1;  // CTAs of the persistent step kernel (resident CTAs x SMs)
 };
+
+// Iolets whose inlet time factors are evaluated on the host each step.
+constexpr int kMaxTimedInlets = 8;
 
 struct StepParams {
   double omega;      // 1 / tau
@@ -111,6 +115,9 @@ struct StepParams {
   int32_t elastic;   // 1: elastic GZS wall, 0: bounce-back
   int32_t write_state;
   int64_t step;
+  // u_amp sin(th_k), u_amp cos(th_k), th_k = 2 pi step / period_k + phase_k
+  double inlet_sin[kMaxTimedInlets];
+  double inlet_cos[kMaxTimedInlets];
 };
 
 // Kernel launchers (kernels.cu); storage is LBM_F64 ... LBM_BF16S.
@@ -132,6 +139,8 @@ int launch_wss(int storage, const DevLattice& d, int odd_layout, double tau,
                const int64_t* sites, const double* normals, int64_t m, double* out,
                void* stream);
 size_t storage_bytes(int storage);
+// Grid of the persistent step kernel for `sms` SMs, or -cudaError on failure.
+int step_grid(int storage, int sms);
 int reduce_partials();
 
 }  // namespace lbm
