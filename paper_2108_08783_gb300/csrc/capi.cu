@@ -214,6 +214,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   const size_t sz = lbm::storage_bytes(storage);
   d.pop = dev_alloc<unsigned char>(c, (size_t)lbm::kQ * d.npad * sz);
   lbm::TileDesc* td = dev_alloc<lbm::TileDesc>(c, L.tiles.size());
+  int32_t* to = dev_alloc<int32_t>(c, L.tile_order.size());
   uint32_t* sm = dev_alloc<uint32_t>(c, S);
   int32_t* sn = dev_alloc<int32_t>(c, 18 * S);
   double* sp = dev_alloc<double>(c, 3 * S);
@@ -227,13 +228,14 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   c->iolet_sites = dev_alloc<int64_t>(c, L.iolet_sites.size());
   c->partial = dev_alloc<double>(c, lbm::reduce_partials());
   c->red_out = dev_alloc<double>(c, 1 + n_iolets);
-  if (!d.pop || !td || !sm || !sn || !sp || !sF || !sK || !sdE || !sUw ||
+  if (!d.pop || !td || !to || !sm || !sn || !sp || !sF || !sK || !sdE || !sUw ||
       !io || !err || !c->iolet_off || !c->iolet_sites || !c->partial || !c->red_out) {
     g_build_err = "device allocation failed";
     lbm_destroy(c);
     return LBM_ENOMEM;
   }
   d.tiles = td;
+  d.tile_order = to;
   d.slot_mask = sm;
   d.slot_nbr = sn;
   d.slot_prof = sp;
@@ -261,6 +263,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   chk(h2d(c, td, L.tiles.data(), L.tiles.size()));
+  chk(h2d(c, to, L.tile_order.data(), L.tile_order.size()));
   chk(h2d(c, sm, L.slot_mask.data(), S));
   chk(h2d(c, sn, L.slot_nbr.data(), 18 * S));
   chk(h2d(c, sp, L.slot_prof.data(), 3 * S));
@@ -280,20 +283,6 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     g_build_err = c->err;
     lbm_destroy(c);
     return rc;
-  }
-  {
-    int dev = 0, sms = 0;
-    cudaError_t ge = cudaGetDevice(&dev);
-    if (ge == cudaSuccess) ge = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = ge == cudaSuccess ? lbm::step_grid(storage, sms) : -(int)ge;
-    if (grid <= 0) {
-      rc = cuda_fail(c, grid < 0 ? (cudaError_t)(-grid) : cudaErrorInvalidConfiguration,
-                     "step kernel occupancy");
-      g_build_err = c->err;
-      lbm_destroy(c);
-      return rc;
-    }
-    d.step_grid = grid;
   }
   rc = check_launch(c, lbm::launch_init(storage, d, nullptr, nullptr, c->stream), "init kernel");
   if (rc == LBM_OK) rc = sync(c, "lbm_build_lattice");

@@ -422,55 +422,51 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<S>::value)
   __shared__ __align__(16) int32_t desc_s[kWarpsPerCta][20];
   __shared__ uint64_t bars[kWarpsPerCta];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* st = stage[w];
+  // boundary tiles come first in the order, so the slower CTAs start first
+  // and every CTA holds tiles of one kind
+  const int64_t k = (int64_t)blockIdx.x * kWarpsPerCta + w;
+  if (k >= d.n_tiles) return;  // warp-uniform
+  const int64_t t = __ldg(d.tile_order + k);
   int32_t* dsc = desc_s[w];
+  if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.tiles + t) + lane);
+  __syncwarp();
+  const uint32_t tmask = (uint32_t)dsc[18];
+  const int64_t x = t * kTile + lane;
+  S* P = static_cast<S*>(d.pop);
+  if (tmask == 0) {
+    if (x < d.n) bulk_update<S, ODD>(P, d.npad, x, dsc, p, d.err);
+    return;
+  }
+  unsigned char* st = stage[w];
   uint64_t* bar = &bars[w];
+  const int32_t slot0 = dsc[19];
+  const bool irr = tmask & kIrregular;
   if (lane == 0) mbar_init(bar, 1);
   __syncwarp();
-  uint32_t phase = 0;
-  S* P = static_cast<S*>(d.pop);
-  const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerCta;
-  // persistent: every warp strides over the tiles
-  for (int64_t t = (int64_t)blockIdx.x * kWarpsPerCta + w; t < d.n_tiles; t += nwarps) {
-    if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.tiles + t) + lane);
-    __syncwarp();
-    const uint32_t tmask = (uint32_t)dsc[18];
-    const int64_t x = t * kTile + lane;
-    if (tmask == 0) {
-      if (x < d.n) bulk_update<S, ODD>(P, d.npad, x, dsc, p, d.err);
-    } else {
-      const int32_t slot0 = dsc[19];
-      const bool irr = tmask & kIrregular;
-      if (lane == 0) {
-        const int64_t ss = d.slot_stride;
-        const bool wall = tmask & kHasWall, inl = tmask & kHasInlet, nbr = ODD && irr;
-        // order this warp's earlier generic reads of the staging area before the async writes
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, 128u + (wall ? 512u : 0u) + (inl ? 768u : 0u) + (nbr ? 2304u : 0u));
-        bulk_g2s(st + kStMask, d.slot_mask + slot0, 128, bar);
-        if (wall) {
-          bulk_g2s(st + kStF, d.slot_F + slot0, 256, bar);
-          bulk_g2s(st + kStK, d.slot_kappa + slot0, 256, bar);
-        }
-        if (inl)
-          for (int c = 0; c < 3; ++c)
-            bulk_g2s(st + kStProf + 256 * c, d.slot_prof + c * ss + slot0, 256, bar);
-        if (nbr)
-          for (int i = 0; i < 18; ++i)
-            bulk_g2s(st + kStNbr + 128 * i, d.slot_nbr + i * ss + slot0, 128, bar);
-      }
-      if (!mbar_wait_bounded(bar, phase)) {
-        if (lane == 0) atomicOr(d.err, kErrTimeout);
-        mbar_wait_bounded(bar, phase);  // a second bounded chance for copies in flight
-        return;
-      }
-      phase ^= 1u;
-      const uint32_t smask = reinterpret_cast<const uint32_t*>(st + kStMask)[lane];
-      if (smask & kValid)
-        boundary_update<S, ODD>(d, p, P, x, dsc, irr, smask, st, lane, (int64_t)slot0 + lane);
+  if (lane == 0) {
+    const int64_t ss = d.slot_stride;
+    const bool wall = tmask & kHasWall, inl = tmask & kHasInlet, nbr = ODD && irr;
+    mbar_expect_tx(bar, 128u + (wall ? 512u : 0u) + (inl ? 768u : 0u) + (nbr ? 2304u : 0u));
+    bulk_g2s(st + kStMask, d.slot_mask + slot0, 128, bar);
+    if (wall) {
+      bulk_g2s(st + kStF, d.slot_F + slot0, 256, bar);
+      bulk_g2s(st + kStK, d.slot_kappa + slot0, 256, bar);
     }
-    __syncwarp();  // the tile's descriptor and staging area are free again
+    if (inl)
+      for (int c = 0; c < 3; ++c)
+        bulk_g2s(st + kStProf + 256 * c, d.slot_prof + c * ss + slot0, 256, bar);
+    if (nbr)
+      for (int i = 0; i < 18; ++i)
+        bulk_g2s(st + kStNbr + 128 * i, d.slot_nbr + i * ss + slot0, 128, bar);
   }
+  if (!mbar_wait_bounded(bar, 0)) {
+    if (lane == 0) atomicOr(d.err, kErrTimeout);
+    mbar_wait_bounded(bar, 0);  // a second bounded chance for copies still in flight
+    return;
+  }
+  const uint32_t smask = reinterpret_cast<const uint32_t*>(st + kStMask)[lane];
+  if (smask & kValid)
+    boundary_update<S, ODD>(d, p, P, x, dsc, irr, smask, st, lane, (int64_t)slot0 + lane);
 }
 
 // ------------------------------------------------ state conversion kernels
@@ -665,20 +661,8 @@ __global__ void k_wss(const DevLattice d, int odd, double tau, const int64_t* si
 // ------------------------------------------------------------- dispatch
 
 template <class S>
-int step_grid_t(int sms) {
-  int a = 0, b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<S, false>,
-                                                                kWarpsPerCta * 32, 0);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<S, true>, kWarpsPerCta * 32, 0);
-  if (e != cudaSuccess) return -(int)e;
-  return (a < b ? a : b) * sms;
-}
-
-template <class S>
 int step_t(const DevLattice& d, const StepParams& p, cudaStream_t s, void* const* ev) {
-  const int64_t need = (d.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta;
-  const unsigned nb = (unsigned)(need < d.step_grid ? need : d.step_grid);
+  const unsigned nb = (unsigned)((d.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta);
   if (ev) cudaEventRecord((cudaEvent_t)ev[0], s);
   if (nb) {
     if (p.step & 1) k_step<S, true><<<nb, kWarpsPerCta * 32, 0, s>>>(d, p);
@@ -712,13 +696,6 @@ size_t storage_bytes(int storage) {
 }
 
 int reduce_partials() { return kRedBlocks; }
-
-int step_grid(int storage, int sms) {
-  return dispatch(storage, [&](auto tag) {
-    using S = std::remove_pointer_t<decltype(tag)>;
-    return step_grid_t<S>(sms);
-  });
-}
 
 int launch_step(int storage, const DevLattice& d, const StepParams& p, void* stream,
                 void* const* events) {

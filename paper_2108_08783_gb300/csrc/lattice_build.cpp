@@ -228,6 +228,12 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     d.slot = (int32_t)(nb_tiles * kTile);
     ++nb_tiles;
   }
+  L.tile_order.clear();
+  L.tile_order.reserve(T);
+  for (int64_t t = 0; t < T; ++t)
+    if (L.tiles[t].slot >= 0) L.tile_order.push_back((int32_t)t);
+  for (int64_t t = 0; t < T; ++t)
+    if (L.tiles[t].slot < 0) L.tile_order.push_back((int32_t)t);
   // ---- boundary slots
   const int64_t S = nb_tiles * kTile;
   L.n_slots = S;

@@ -67,6 +67,7 @@ struct HostLattice {
   // tiles (32 sites each, in site order)
   int64_t n_tiles = 0;
   std::vector<TileDesc> tiles;
+  std::vector<int32_t> tile_order;  // boundary tiles (ascending), then bulk tiles
   int64_t n_bulk = 0, n_uniform = 0, n_irregular = 0, bulk_sites = 0;
   // boundary slots (32 per boundary tile, in tile order)
   int64_t n_slots = 0;
@@ -91,6 +92,7 @@ struct DevLattice {
   int64_t npad = 0;
   int64_t n = 0;
   const TileDesc* tiles = nullptr;
+  const int32_t* tile_order = nullptr;  // boundary tiles (ascending), then bulk tiles
   int64_t n_tiles = 0;
   const uint32_t* slot_mask = nullptr;
   const int32_t* slot_nbr = nullptr;   // [18][slot_stride]
@@ -103,7 +105,6 @@ struct DevLattice {
   const IoletDev* iolets = nullptr;
   int32_t n_iolets = 0;
   int* err = nullptr;
-  int64_t step_grid = 1;  // CTAs of the persistent step kernel (resident CTAs x SMs)
 };
 
 // Iolets whose inlet time factors are evaluated on the host each step.
@@ -139,8 +140,6 @@ int launch_wss(int storage, const DevLattice& d, int odd_layout, double tau,
                const int64_t* sites, const double* normals, int64_t m, double* out,
                void* stream);
 size_t storage_bytes(int storage);
-// Grid of the persistent step kernel for `sms` SMs, or -cudaError on failure.
-int step_grid(int storage, int sms);
 int reduce_partials();
 
 }  // namespace lbm
