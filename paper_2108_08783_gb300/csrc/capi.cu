@@ -13,6 +13,10 @@
 
 #include "lbm_internal.h"
 
+#ifndef LBM_DEFAULT_PREFETCH
+#define LBM_DEFAULT_PREFETCH 0
+#endif
+
 using lbm::DevLattice;
 using lbm::HostLattice;
 
@@ -35,6 +39,7 @@ struct lbm_ctx {
   double* partial = nullptr;
   double* red_out = nullptr;
   std::string err;
+  int64_t prefetch = LBM_DEFAULT_PREFETCH;  // L2 prefetch distance (tiles)
   // optional per-kernel timing (lbm_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;  // 2 per profiled step
@@ -214,7 +219,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   const size_t sz = lbm::storage_bytes(storage);
   d.pop = dev_alloc<unsigned char>(c, (size_t)lbm::kQ * d.npad * sz);
   lbm::TileDesc* td = dev_alloc<lbm::TileDesc>(c, L.tiles.size());
-  int32_t* to = dev_alloc<int32_t>(c, L.tile_order.size());
+  lbm::LaunchDesc* to = dev_alloc<lbm::LaunchDesc>(c, L.launch.size());
   uint32_t* sm = dev_alloc<uint32_t>(c, S);
   int32_t* sn = dev_alloc<int32_t>(c, 18 * S);
   double* sp = dev_alloc<double>(c, 3 * S);
@@ -235,7 +240,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     return LBM_ENOMEM;
   }
   d.tiles = td;
-  d.tile_order = to;
+  d.launch = to;
   d.slot_mask = sm;
   d.slot_nbr = sn;
   d.slot_prof = sp;
@@ -263,7 +268,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   chk(h2d(c, td, L.tiles.data(), L.tiles.size()));
-  chk(h2d(c, to, L.tile_order.data(), L.tile_order.size()));
+  chk(h2d(c, to, L.launch.data(), L.launch.size()));
   chk(h2d(c, sm, L.slot_mask.data(), S));
   chk(h2d(c, sn, L.slot_nbr.data(), 18 * S));
   chk(h2d(c, sp, L.slot_prof.data(), 3 * S));
@@ -355,6 +360,7 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
   p.omega = 1.0 / c->tau;
   p.rho0 = c->rho0;
   p.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
+  p.prefetch = c->prefetch;
   for (int64_t s = 0; s < n_steps; ++s) {
     p.step = c->step;
     p.write_state = s == n_steps - 1 ? 1 : 0;

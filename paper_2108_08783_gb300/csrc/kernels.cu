@@ -203,6 +203,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// Asynchronous prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(src)),
+               "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -426,10 +432,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<S>::value)
   // and every CTA holds tiles of one kind
   const int64_t k = (int64_t)blockIdx.x * kWarpsPerCta + w;
   if (k >= d.n_tiles) return;  // warp-uniform
-  const int64_t t = __ldg(d.tile_order + k);
   int32_t* dsc = desc_s[w];
-  if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.tiles + t) + lane);
+  if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
+  // Stream the populations of the tile `prefetch` positions ahead in launch
+  // order into L2 (one 32-site segment per direction, lanes 0..18), so that
+  // DRAM traffic does not wait for registers of warps not yet resident.
+  if (p.prefetch > 0 && k + p.prefetch < d.n_tiles && lane < kQ) {
+    const int64_t tp = __ldg(&d.launch[k + p.prefetch].tile);
+    bulk_prefetch_l2(static_cast<const S*>(d.pop) + lane * d.npad + tp * kTile,
+                     kTile * sizeof(S));
+  }
   __syncwarp();
+  const int64_t t = dsc[19];
   const uint32_t tmask = (uint32_t)dsc[18];
   const int64_t x = t * kTile + lane;
   S* P = static_cast<S*>(d.pop);
@@ -439,7 +453,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<S>::value)
   }
   unsigned char* st = stage[w];
   uint64_t* bar = &bars[w];
-  const int32_t slot0 = dsc[19];
+  const int32_t slot0 = (int32_t)(k * kTile);  // boundary tiles lead the launch order
   const bool irr = tmask & kIrregular;
   if (lane == 0) mbar_init(bar, 1);
   __syncwarp();

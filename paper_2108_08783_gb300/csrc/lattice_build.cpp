@@ -228,12 +228,18 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     d.slot = (int32_t)(nb_tiles * kTile);
     ++nb_tiles;
   }
-  L.tile_order.clear();
-  L.tile_order.reserve(T);
-  for (int64_t t = 0; t < T; ++t)
-    if (L.tiles[t].slot >= 0) L.tile_order.push_back((int32_t)t);
-  for (int64_t t = 0; t < T; ++t)
-    if (L.tiles[t].slot < 0) L.tile_order.push_back((int32_t)t);
+  L.launch.clear();
+  L.launch.reserve(T);
+  for (int pass = 0; pass < 2; ++pass)
+    for (int64_t t = 0; t < T; ++t) {
+      const TileDesc& d = L.tiles[t];
+      if ((d.slot >= 0) != (pass == 0)) continue;
+      LaunchDesc e;
+      for (int i = 0; i < 18; ++i) e.code[i] = d.code[i];
+      e.mask = d.mask;
+      e.tile = (int32_t)t;
+      L.launch.push_back(e);
+    }
   // ---- boundary slots
   const int64_t S = nb_tiles * kTile;
   L.n_slots = S;

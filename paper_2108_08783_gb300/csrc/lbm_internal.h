@@ -14,7 +14,10 @@ namespace lbm {
 
 constexpr int kQ = 19;
 constexpr int kTile = 32;          // sites per tile = one warp
-constexpr int kWarpsPerCta = 8;    // step kernel: tiles (warps) per CTA
+#ifndef LBM_WARPS_PER_CTA
+#define LBM_WARPS_PER_CTA 8
+#endif
+constexpr int kWarpsPerCta = LBM_WARPS_PER_CTA;  // step kernel: tiles (warps) per CTA
 
 // Flag bits shared by TileDesc::mask and the per-slot masks.  Bits 1..18 mark
 // the non-fluid directions (wall or iolet links).
@@ -45,6 +48,16 @@ struct alignas(16) TileDesc {
 };
 static_assert(sizeof(TileDesc) == 80, "TileDesc must be 80 bytes");
 
+// The same descriptor in launch order (boundary tiles first, then bulk tiles):
+// `tile` replaces `slot`; a boundary tile at launch position k owns slots
+// [32 k, 32 k + 32).
+struct alignas(16) LaunchDesc {
+  int32_t code[18];
+  uint32_t mask;
+  int32_t tile;
+};
+static_assert(sizeof(LaunchDesc) == 80, "LaunchDesc must be 80 bytes");
+
 // Iolet as the kernels see it.
 struct IoletDev {
   int32_t kind;   // LBM_IOLET_VELOCITY / LBM_IOLET_DENSITY
@@ -67,7 +80,7 @@ struct HostLattice {
   // tiles (32 sites each, in site order)
   int64_t n_tiles = 0;
   std::vector<TileDesc> tiles;
-  std::vector<int32_t> tile_order;  // boundary tiles (ascending), then bulk tiles
+  std::vector<LaunchDesc> launch;   // boundary tiles (ascending), then bulk tiles
   int64_t n_bulk = 0, n_uniform = 0, n_irregular = 0, bulk_sites = 0;
   // boundary slots (32 per boundary tile, in tile order)
   int64_t n_slots = 0;
@@ -92,7 +105,7 @@ struct DevLattice {
   int64_t npad = 0;
   int64_t n = 0;
   const TileDesc* tiles = nullptr;
-  const int32_t* tile_order = nullptr;  // boundary tiles (ascending), then bulk tiles
+  const LaunchDesc* launch = nullptr;  // boundary tiles (ascending), then bulk tiles
   int64_t n_tiles = 0;
   const uint32_t* slot_mask = nullptr;
   const int32_t* slot_nbr = nullptr;   // [18][slot_stride]
@@ -116,6 +129,7 @@ struct StepParams {
   int32_t elastic;   // 1: elastic GZS wall, 0: bounce-back
   int32_t write_state;
   int64_t step;
+  int64_t prefetch;  // L2 prefetch distance in tiles of launch order (0: off)
   // u_amp sin(th_k), u_amp cos(th_k), th_k = 2 pi step / period_k + phase_k
   double inlet_sin[kMaxTimedInlets];
   double inlet_cos[kMaxTimedInlets];
