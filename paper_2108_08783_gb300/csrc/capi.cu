@@ -14,7 +14,7 @@
 #include "lbm_internal.h"
 
 #ifndef LBM_DEFAULT_PREFETCH
-#define LBM_DEFAULT_PREFETCH 0
+#define LBM_DEFAULT_PREFETCH 2048
 #endif
 
 using lbm::DevLattice;

@@ -411,10 +411,10 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
 // registers per thread (ALU-bound anyway); the 32/16-bit paths trade a few
 // boundary-path spills for occupancy of the HBM-bound bulk path.
 #ifndef LBM_MINB_F64
-#define LBM_MINB_F64 2
+#define LBM_MINB_F64 4
 #endif
 #ifndef LBM_MINB_F32
-#define LBM_MINB_F32 3
+#define LBM_MINB_F32 8
 #endif
 template <class S>
 struct MinBlocks {

@@ -15,7 +15,7 @@ namespace lbm {
 constexpr int kQ = 19;
 constexpr int kTile = 32;          // sites per tile = one warp
 #ifndef LBM_WARPS_PER_CTA
-#define LBM_WARPS_PER_CTA 8
+#define LBM_WARPS_PER_CTA 4
 #endif
 constexpr int kWarpsPerCta = LBM_WARPS_PER_CTA;  // step kernel: tiles (warps) per CTA
 
