@@ -179,6 +179,26 @@ int lbm_wall_state(lbm_ctx *ctx, double *dE, double *Uw);
  * out is a host array [1 + n_iolets]; the call waits for the stream. */
 int lbm_reduce(lbm_ctx *ctx, double *out);
 
+/* lbm_reduce_noalloc - the same diagnostics as lbm_reduce, for callers that
+ * must not allocate device memory during the call (for example a monitoring
+ * hook that runs while another component's memory pool owns the whole device,
+ * where cudaMalloc can fail or force the pool to shrink, or a latency-bound
+ * loop that cannot take the synchronisation cudaMalloc/cudaFree may cause).
+ * The paper has no counterpart: this is a property of the library, not of the
+ * method.  Scratch (1024 partial sums and up to 256 outputs, 10 KiB) lives in
+ * a fixed device array that every GPU loading the library holds until the
+ * process exits; the call itself allocates nothing.
+ *   out            [1 + n_iolets] doubles, laid out as for lbm_reduce;
+ *   out_is_device  != 0: out is device memory, written asynchronously on the
+ *                  context's stream; 0: out is host memory, the call waits.
+ * The first call on a device looks up the array's device address (with the
+ * context's device current) and caches it; make that first call before any
+ * stream capture.  All calls share the array, so calls that overlap on the
+ * GPU race; serialise them (one stream, or wait between calls).
+ * Errors: LBM_EINVAL for NULL arguments or more than 255 iolets (beyond the
+ * array); LBM_ECUDA. */
+int lbm_reduce_noalloc(lbm_ctx *ctx, double *out, int32_t out_is_device);
+
 /* lbm_get_populations / lbm_set_populations - the pre-collision populations
  * f[n_sites][19] (FP64, canonical site order, canonical directions),
  * converting to or from the in-place storage layout.  set also sets the step

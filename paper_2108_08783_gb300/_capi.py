@@ -23,7 +23,7 @@ EXPORTS = (
     "lbm_sync", "lbm_info", "lbm_export_lattice", "lbm_wall_state", "lbm_reduce",
     "lbm_get_populations", "lbm_set_populations", "lbm_checkpoint_bytes", "lbm_checkpoint_save",
     "lbm_checkpoint_load", "lbm_wss", "lbm_set_stream", "lbm_last_error", "lbm_status_string",
-    "lbm_destroy", "lbm_profile", "lbm_profile_read",
+    "lbm_destroy", "lbm_profile", "lbm_profile_read", "lbm_reduce_noalloc",
 )
 
 
@@ -84,6 +84,7 @@ def lib():
         "lbm_destroy": ([P], None),
         "lbm_profile": ([P, i32], C.c_int),
         "lbm_profile_read": ([P, P, P], C.c_int),
+        "lbm_reduce_noalloc": ([P, P, i32], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -610,3 +611,71 @@ int lbm_wss(lbm_ctx* c, const int64_t* sites, const double* normals, int64_t m, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// lbm_reduce_noalloc: the FP64 diagnostics of lbm_reduce for callers that must
+// not allocate device memory while the call runs - for example a monitoring
+// hook that runs while another component's memory pool holds the whole device
+// (a cudaMalloc there can fail or force the pool to release memory), or a
+// latency-bound loop that cannot afford the device-wide synchronisation that
+// cudaMalloc/cudaFree may imply.  Its scratch (per-block partial sums and the
+// result) lives in the fixed device array below instead of the context's
+// buffers; the call allocates nothing.
+namespace {
+
+constexpr int kNoAllocPartials = 1024;  // partial sums of the mass reduction
+constexpr int kNoAllocOutputs = 256;    // 1 + n_iolets at most
+// Held by every GPU that loads this library until the process exits
+// (10 KiB).  Shared by every call: calls that overlap on the GPU race.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocPartials + kNoAllocOutputs];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+int noalloc_scratch(lbm_ctx* c, double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_reduce_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(c, LBM_EINVAL, "lbm_reduce_noalloc: device ordinal beyond 63");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_reduce_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int lbm_reduce_noalloc(lbm_ctx* c, double* out, int32_t out_is_device) {
+  if (!c || !out) return LBM_EINVAL;
+  c->err.clear();
+  const int k = (int)c->iolets.size();
+  if (1 + k > kNoAllocOutputs)
+    return fail(c, LBM_EINVAL, "lbm_reduce_noalloc: more than 255 iolets");
+  if (lbm::reduce_partials() > kNoAllocPartials)
+    return fail(c, LBM_EINVAL, "lbm_reduce_noalloc: scratch smaller than the reduction grid");
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(c, &scratch);
+  if (rc != LBM_OK) return rc;
+  // Every partial and every output is written by the kernels before it is
+  // read, so nothing left by an earlier call needs clearing.
+  double* dst = out_is_device ? out : scratch + kNoAllocPartials;
+  rc = check_launch(c, lbm::launch_reduce(c->storage, c->d, odd_layout(c), c->iolet_off,
+                                          c->iolet_sites, scratch, kNoAllocPartials, dst,
+                                          c->stream),
+                    "reduce kernels");
+  if (rc != LBM_OK || out_is_device) return rc;
+  cudaError_t e = cudaMemcpyAsync(out, dst, (1 + k) * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_reduce_noalloc copy");
+  return sync(c, "lbm_reduce_noalloc");
+}
