@@ -78,8 +78,9 @@ enum {
   LBM_ESTATE = -6     /* call not valid in the context's current state */
 };
 
-/* Population storage.  *S variants store f_i - w_i (the deviation from the
- * rest equilibrium) so that half-precision keeps its significant bits. */
+/* Population storage.  Every variant stores f_i - w_i (the deviation from the
+ * rest equilibrium), so that the stored value keeps its significant bits
+ * (essential for the 16-bit *S variants, a free accuracy gain for the others). */
 enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 };
 enum { LBM_WALL_BOUNCEBACK = 0, LBM_WALL_ELASTIC_GZS = 1 };
 enum { LBM_IOLET_VELOCITY = 0, LBM_IOLET_DENSITY = 1 };

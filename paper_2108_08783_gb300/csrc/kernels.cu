@@ -89,25 +89,32 @@ __device__ __forceinline__ C geq(C drho, C rho, C ux, C uy, C uz, C usq) {
 }
 
 // ------------------------------------------------------------- storage codecs
-// ld/st convert between the stored value and g = f - w in the compute type C;
-// get/put convert between the stored value and f in double.
+// Every storage type holds g = f - w (the deviation from the rest
+// equilibrium).  ld/st convert between the stored value and g in the compute
+// type C; get/put convert between the stored value and f in double.
 template <class S>
 struct Codec;
 template <>
 struct Codec<double> {
   using C = double;  // compute type
-  static __device__ __forceinline__ C ld(const double* p, int i) { return *p - weight<C>(i); }
-  static __device__ __forceinline__ void st(double* p, int i, C g) { *p = g + weight<C>(i); }
-  static __device__ __forceinline__ double get(const double* p, int) { return *p; }
-  static __device__ __forceinline__ void put(double* p, int, double f) { *p = f; }
+  static __device__ __forceinline__ C ld(const double* p, int) { return *p; }
+  static __device__ __forceinline__ void st(double* p, int, C g) { *p = g; }
+  static __device__ __forceinline__ double get(const double* p, int i) { return *p + weight<double>(i); }
+  static __device__ __forceinline__ void put(double* p, int i, double f) { *p = f - weight<double>(i); }
+  static __device__ __forceinline__ void st_init(double* p, double g) { *p = g; }
 };
 template <>
 struct Codec<float> {
   using C = float;
-  static __device__ __forceinline__ C ld(const float* p, int i) { return *p - weight<C>(i); }
-  static __device__ __forceinline__ void st(float* p, int i, C g) { *p = g + weight<C>(i); }
-  static __device__ __forceinline__ double get(const float* p, int) { return (double)*p; }
-  static __device__ __forceinline__ void put(float* p, int, double f) { *p = (float)f; }
+  static __device__ __forceinline__ C ld(const float* p, int) { return *p; }
+  static __device__ __forceinline__ void st(float* p, int, C g) { *p = g; }
+  static __device__ __forceinline__ double get(const float* p, int i) {
+    return (double)*p + weight<double>(i);
+  }
+  static __device__ __forceinline__ void put(float* p, int i, double f) {
+    *p = (float)(f - weight<double>(i));
+  }
+  static __device__ __forceinline__ void st_init(float* p, double g) { *p = (float)g; }
 };
 template <>
 struct Codec<__half> {
@@ -120,6 +127,7 @@ struct Codec<__half> {
   static __device__ __forceinline__ void put(__half* p, int i, double f) {
     *p = __float2half_rn((float)(f - weight<double>(i)));
   }
+  static __device__ __forceinline__ void st_init(__half* p, double g) { *p = __float2half_rn((float)g); }
 };
 template <>
 struct Codec<__nv_bfloat16> {
@@ -132,9 +140,13 @@ struct Codec<__nv_bfloat16> {
   static __device__ __forceinline__ void put(__nv_bfloat16* p, int i, double f) {
     *p = __float2bfloat16_rn((float)(f - weight<double>(i)));
   }
+  static __device__ __forceinline__ void st_init(__nv_bfloat16* p, double g) { *p = __float2bfloat16_rn((float)g); }
 };
 
 // ------------------------------------------------------------------ collision
+
+__device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double recip(double v) { return __drcp_rn(v); }
 
 template <class C>
 struct Mom {
@@ -155,7 +167,7 @@ __device__ __forceinline__ Mom<C> moments(const C (&g)[kQ]) {
   const C jy = (a3 + a7) - (a9 - a15) + a17;
   const C jz = (a5 + a11) - (a13 - a15) - a17;
   m.rho = C(1) + m.drho;
-  const C inv = C(1) / m.rho;
+  const C inv = recip(m.rho);
   m.ux = jx * inv;
   m.uy = jy * inv;
   m.uz = jz * inv;
@@ -520,9 +532,8 @@ __global__ void k_init(const DevLattice d, const double* rho, const double* u) {
   S* P = static_cast<S*>(d.pop);
   unroll<kQ>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    // f^eq (Eq. feq) = w_i + g^eq_i
-    const double f = weight<double>(i) + geq<i, double>(r - 1.0, r, ux, uy, uz, usq);
-    Codec<S>::put(P + i * d.npad + x, i, f);
+    // f^eq (Eq. feq) = w_i + g^eq_i; the shifted part is stored directly
+    Codec<S>::st_init(P + i * d.npad + x, geq<i, double>(r - 1.0, r, ux, uy, uz, usq));
   });
 }
 
