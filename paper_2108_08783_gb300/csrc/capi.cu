@@ -211,8 +211,9 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   HostLattice& L = c->L;
   DevLattice& d = c->d;
   d.n = L.n;
-  d.npad = ((L.n + 127) / 128) * 128;
-  if (d.npad == 0) d.npad = 128;
+  // slack past the last site: the step kernel copies 16-byte-aligned runs of
+  // 32 + 16/sizeof(storage) elements that may reach up to 8 elements beyond it
+  d.npad = ((L.n + 64 + 127) / 128) * 128;
   d.n_tiles = L.n_tiles;
   d.slot_stride = L.n_slots;
   d.n_iolets = n_iolets;
@@ -289,6 +290,20 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     g_build_err = c->err;
     lbm_destroy(c);
     return rc;
+  }
+  {
+    int dev = 0, sms = 0;
+    cudaError_t ge = cudaGetDevice(&dev);
+    if (ge == cudaSuccess) ge = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = ge == cudaSuccess ? lbm::step_grid(storage, sms) : -(int)ge;
+    if (grid <= 0) {
+      rc = cuda_fail(c, grid < 0 ? (cudaError_t)(-grid) : cudaErrorInvalidConfiguration,
+                     "step kernel occupancy");
+      g_build_err = c->err;
+      lbm_destroy(c);
+      return rc;
+    }
+    d.step_grid = grid;
   }
   rc = check_launch(c, lbm::launch_init(storage, d, nullptr, nullptr, c->stream), "init kernel");
   if (rc == LBM_OK) rc = sync(c, "lbm_build_lattice");

@@ -118,6 +118,7 @@ struct DevLattice {
   const IoletDev* iolets = nullptr;
   int32_t n_iolets = 0;
   int* err = nullptr;
+  int64_t step_grid = 1;  // CTAs of the persistent step kernel (resident CTAs x SMs)
 };
 
 // Iolets whose inlet time factors are evaluated on the host each step.
@@ -154,6 +155,9 @@ int launch_wss(int storage, const DevLattice& d, int odd_layout, double tau,
                const int64_t* sites, const double* normals, int64_t m, double* out,
                void* stream);
 size_t storage_bytes(int storage);
+// Grid of the persistent step kernel for `sms` SMs (also sets its shared-memory
+// limit), or -cudaError on failure.
+int step_grid(int storage, int sms);
 int reduce_partials();
 
 }  // namespace lbm
