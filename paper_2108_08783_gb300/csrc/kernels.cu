@@ -421,11 +421,18 @@ __device__ __forceinline__ void collide_store(const DevLattice& d, const StepPar
   }
 }
 
-// Start the copies of launch position k into stage b (whole warp).
+// Word `lane` (< 20) of the descriptor at launch position k.
+__device__ __forceinline__ int32_t desc_word(const DevLattice& d, int64_t k, int lane) {
+  return (lane < 20 && k < d.n_tiles) ? __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane)
+                                      : 0;
+}
+
+// Start the copies of launch position k into stage b (whole warp); `word` is
+// the lane's word of k's descriptor, fetched an iteration earlier.
 template <class S, bool ODD, int NST>
 __device__ __forceinline__ void issue_tile(const DevLattice& d, WarpSmem<S, NST>& sm, int b,
-                                           int64_t k, int lane) {
-  if (lane < 20) sm.dsc[b][lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
+                                           int64_t k, int32_t word, int lane) {
+  if (lane < 20) sm.dsc[b][lane] = word;
   __syncwarp();
   const int32_t* dsc = sm.dsc[b];
   const uint32_t tm = (uint32_t)dsc[18];
@@ -479,23 +486,26 @@ __global__ void __launch_bounds__(Pipe<S>::WARPS * 32)
   const int64_t W = (int64_t)gridDim.x * Pipe<S>::WARPS;
   const int64_t k0 = (int64_t)blockIdx.x * Pipe<S>::WARPS + w;
   uint32_t phase = 0, phx = 0, pending = 0;
-  // prologue: the first NST-1 tiles
+  // prologue: the first NST-1 tiles, and the descriptor of the next one
   for (int b = 0; b < NST - 1; ++b) {
     const int64_t k = k0 + b * W;
     if (k < d.n_tiles) {
-      issue_tile<S, ODD, NST>(d, sm, b, k, lane);
+      issue_tile<S, ODD, NST>(d, sm, b, k, desc_word(d, k, lane), lane);
       pending |= 1u << b;
     }
   }
+  int32_t dnext = desc_word(d, k0 + (int64_t)(NST - 1) * W, lane);
   int b = 0;
   for (int64_t k = k0; k < d.n_tiles; k += W) {
-    // refill the stage freed by the previous tile
+    // refill the stage freed by the previous tile; fetch the descriptor of the
+    // tile after it, to be used one iteration from now
     const int ba = (b + NST - 1) % NST;
     const int64_t ka = k + (int64_t)(NST - 1) * W;
     if (ka < d.n_tiles) {
-      issue_tile<S, ODD, NST>(d, sm, ba, ka, lane);
+      issue_tile<S, ODD, NST>(d, sm, ba, ka, dnext, lane);
       pending |= 1u << ba;
     }
+    dnext = desc_word(d, ka + W, lane);
     if (!mbar_wait_bounded(&sm.bar[b], (phase >> b) & 1u)) {
       if (lane == 0) atomicOr(d.err, kErrTimeout);
       for (int s = 0; s < NST; ++s)  // a bounded wait on every stage still in flight
