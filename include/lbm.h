@@ -20,8 +20,10 @@
  *     13/14 (+1,0,-1)/(-1,0,+1); 15/16 (0,+1,+1)/(0,-1,-1);
  *     17/18 (0,+1,-1)/(0,-1,+1).
  *   - Device memory comes from the caller's allocator (or cudaMalloc when it
- *     is NULL) and is released by lbm_destroy.  All kernels run on the CUDA
- *     stream given at build time (lbm_set_stream changes it).
+ *     is NULL) and is released by lbm_destroy.  All work is ordered on the
+ *     CUDA stream given at build time (lbm_set_stream changes it); inside a
+ *     step the boundary kernel runs on a private stream forked from and
+ *     joined back into that stream.
  *   - One context per host thread; contexts share no state.
  *   - Device-side faults of the method (non-finite or non-positive density)
  *     are sticky flags reported by lbm_sync as LBM_EUNSTABLE.
@@ -151,13 +153,15 @@ int lbm_sync(lbm_ctx *ctx);
  *   [11] sites in bulk tiles. */
 int lbm_info(const lbm_ctx *ctx, int64_t out[12]);
 
-/* lbm_profile - when enable != 0, lbm_step records a CUDA event on the
- * context's stream before and after each launch of its step kernel;
- * lbm_profile_read waits for the stream, returns the summed device time of
- * those launches (*ms) and their count (*launches), then clears the record.
- * Measurement only: no work is skipped. */
+/* lbm_profile - when enable != 0, lbm_step records CUDA events on the
+ * context's stream around each step: before the boundary kernel is forked to
+ * the library's side stream, after the bulk kernel, and after the join.
+ * lbm_profile_read waits, returns the summed device time of the steps
+ * (ms[0], both kernels) and of the bulk kernel (ms[1]) and the launch counts
+ * of the bulk (launches[0]) and boundary (launches[1]) kernels, then clears
+ * the record.  Measurement only: no work is skipped. */
 int lbm_profile(lbm_ctx *ctx, int32_t enable);
-int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches);
+int lbm_profile_read(lbm_ctx *ctx, double ms[2], int64_t launches[2]);
 
 /* lbm_export_lattice - the integer lattice (host arrays, any may be NULL):
  *   coords [n_sites][3] int32 voxel coordinates;

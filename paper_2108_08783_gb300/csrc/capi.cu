@@ -43,7 +43,10 @@ struct lbm_ctx {
   int64_t prefetch = LBM_DEFAULT_PREFETCH;  // L2 prefetch distance (tiles)
   // optional per-kernel timing (lbm_profile)
   bool prof = false;
-  std::vector<cudaEvent_t> ev;  // 2 per profiled step
+  std::vector<cudaEvent_t> ev;  // 3 per profiled step
+  // side stream of the boundary kernel, and the fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   size_t ev_used = 0;
 };
 
@@ -144,8 +147,12 @@ const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_bui
 void lbm_destroy(lbm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->side) cudaStreamSynchronize(c->side);
   for (void* p : c->owned) dev_free_raw(c, p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 
@@ -160,14 +167,17 @@ int lbm_profile_read(lbm_ctx* c, double* ms, int64_t* launches) {
   if (!c || !ms || !launches) return LBM_EINVAL;
   int rc = sync(c, "lbm_profile_read");
   if (rc != LBM_OK) return rc;
-  *ms = 0.0;
-  *launches = 0;
-  for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
-    float a = 0.f;
-    cudaError_t e = cudaEventElapsedTime(&a, c->ev[k], c->ev[k + 1]);
+  ms[0] = ms[1] = 0.0;
+  launches[0] = launches[1] = 0;
+  for (size_t k = 0; k + 2 < c->ev_used; k += 3) {
+    float a = 0.f, b = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&a, c->ev[k], c->ev[k + 2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, c->ev[k], c->ev[k + 1]);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_profile_read");
-    *ms += a;
-    *launches += c->d.n_tiles > 0;
+    ms[0] += a;
+    ms[1] += b;
+    launches[0] += c->d.n_tiles > c->d.n_boundary;
+    launches[1] += c->d.n_boundary > 0;
   }
   c->ev_used = 0;
   return LBM_OK;
@@ -215,6 +225,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   // 32 + 16/sizeof(storage) elements that may reach up to 8 elements beyond it
   d.npad = ((L.n + 64 + 127) / 128) * 128;
   d.n_tiles = L.n_tiles;
+  d.n_boundary = L.n_uniform + L.n_irregular;
   d.slot_stride = L.n_slots;
   d.n_iolets = n_iolets;
   const size_t S = (size_t)L.n_slots;
@@ -292,18 +303,16 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     return rc;
   }
   {
-    int dev = 0, sms = 0;
-    cudaError_t ge = cudaGetDevice(&dev);
-    if (ge == cudaSuccess) ge = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = ge == cudaSuccess ? lbm::step_grid(storage, sms) : -(int)ge;
-    if (grid <= 0) {
-      rc = cuda_fail(c, grid < 0 ? (cudaError_t)(-grid) : cudaErrorInvalidConfiguration,
-                     "step kernel occupancy");
+    // side stream and fork/join events of the boundary kernel
+    cudaError_t ge = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (ge == cudaSuccess) ge = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+    if (ge == cudaSuccess) ge = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
+    if (ge != cudaSuccess) {
+      rc = cuda_fail(c, ge, "side stream");
       g_build_err = c->err;
       lbm_destroy(c);
       return rc;
     }
-    d.step_grid = grid;
   }
   rc = check_launch(c, lbm::launch_init(storage, d, nullptr, nullptr, c->stream), "init kernel");
   if (rc == LBM_OK) rc = sync(c, "lbm_build_lattice");
@@ -389,18 +398,19 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
         p.inlet_cos[k] = io.u_amp * std::cos(th);
       }
     }
-    void* ev[2] = {nullptr, nullptr};
+    void* ev[3] = {nullptr, nullptr, nullptr};
     if (c->prof) {
-      while (c->ev.size() < c->ev_used + 2) {
+      while (c->ev.size() < c->ev_used + 3) {
         cudaEvent_t e;
         cudaError_t r = cudaEventCreate(&e);
         if (r != cudaSuccess) return cuda_fail(c, r, "lbm_step event");
         c->ev.push_back(e);
       }
-      for (int k = 0; k < 2; ++k) ev[k] = c->ev[c->ev_used + k];
-      c->ev_used += 2;
+      for (int k = 0; k < 3; ++k) ev[k] = c->ev[c->ev_used + k];
+      c->ev_used += 3;
     }
-    int rc = lbm::launch_step(c->storage, c->d, p, c->stream, c->prof ? ev : nullptr);
+    const lbm::StepStreams ss{c->stream, c->side, c->fork, c->join};
+    int rc = lbm::launch_step(c->storage, c->d, p, ss, c->prof ? ev : nullptr);
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "step kernels");
     ++c->step;
   }

@@ -240,349 +240,260 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-// --------------------------------------------------------------- step kernel
+// --------------------------------------------------------------- step kernels
 //
-// k_step: persistent, software-pipelined.  Every warp owns a stride of the
-// launch-ordered tile list (boundary tiles first, then bulk tiles, so each
-// warp gets its share of both) and processes one tile of 32 sites at a time
-// while the shared-memory stages of its next NST-1 tiles fill:
-//   - populations of bulk and uniform boundary tiles: 19 cp.async.bulk copies
-//     (one per direction, one lane each).  On odd steps a direction's 32
-//     values start at an arbitrary element (x + offset), so the copy takes the
-//     16-byte-aligned run of 32 + A elements that contains them (A = 16 bytes
-//     per element) and the lanes index past the misalignment;
-//   - per-site boundary data (link masks, F, kappa) of boundary tiles;
-//   - all copies of a stage complete on that stage's mbarrier.
-// Irregular tiles (links differ from lane to lane) gather their populations
-// with per-lane loads; their per-site neighbour table and any inlet profile
-// are staged synchronously into a per-warp area.  Results are written with
-// ordinary stores straight to the slots the AA pattern assigns.
+// One warp per tile of 32 consecutive sites; the launch-ordered descriptor
+// list holds the boundary tiles first and the bulk tiles after them.  Two
+// kernels per step, on two streams so that they overlap (they touch disjoint
+// slots):
+//   k_bulk over the bulk tiles: branch-free update with the tile's 18
+//     neighbour offsets, lean enough in registers to keep many warps resident,
+//     and an L2 prefetch (cp.async.bulk.prefetch) of the populations of the
+//     tile `prefetch` positions ahead;
+//   k_boundary over the boundary tiles: lane 0 stages the tile's per-site link
+//     data (link masks; F and kappa if a wall link is present; the inlet
+//     profile if an inlet link is present; on odd steps of an irregular tile
+//     the per-site neighbour table) into the warp's shared-memory area with
+//     cp.async.bulk copies that complete on the warp's mbarrier, then every
+//     lane applies the collision and, for each link leaving the fluid, the
+//     boundary rule.
+
+// Per-warp staging area, every block 16-byte aligned.
+constexpr int kStMask = 0;               // 32 x u32
+constexpr int kStF = kStMask + 128;      // 32 x f64
+constexpr int kStK = kStF + 256;         // 32 x f64
+constexpr int kStProf = kStK + 256;      // 3 x 32 x f64
+constexpr int kStNbr = kStProf + 768;    // 18 x 32 x i32
+constexpr int kStBytes = kStNbr + 2304;  // 3712
+static_assert(kStBytes % 16 == 0, "staging blocks must stay 16-byte aligned");
 
 constexpr unsigned kFull = 0xffffffffu;
 
-template <class S>
-struct Seg {
-  static constexpr int A = 16 / (int)sizeof(S);  // elements per 16 bytes
-  static constexpr int E = kTile + A;            // elements copied per direction
-  static constexpr int B = E * (int)sizeof(S);   // bytes copied per direction
-};
-
-// Per-warp shared memory; every copy destination is 16-byte aligned.
-template <class S, int NST>
-struct alignas(16) WarpSmem {
-  S pop[NST][kQ][Seg<S>::E];
-  uint32_t mask[NST][kTile];
-  double F[NST][kTile];
-  double K[NST][kTile];
-  int32_t dsc[NST][20];
-  double prof[3][kTile];  // synchronous extras: inlet profile
-  int32_t nbr[18][kTile]; //                    per-site neighbours (irregular, odd)
-  uint64_t bar[NST];
-  uint64_t barx;
-};
-
-template <class S>
-struct Pipe {
-  static constexpr int NST = sizeof(S) == 8 ? 2 : 3;  // stages per warp
-  static constexpr int WARPS = 4;                      // warps per CTA
-};
-
-template <class S>
-constexpr size_t smem_bytes() {
-  return sizeof(WarpSmem<S, Pipe<S>::NST>) * Pipe<S>::WARPS;
+// Branch-free update of a site whose 18 links are fluid.
+template <class S, bool ODD>
+__device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t* dsc,
+                                            const StepParams& p, int* err) {
+  using Cd = Codec<S>;
+  using C = typename Cd::C;
+  C g[kQ];
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int o = dir_opp(j);
+    if constexpr (!ODD || j == 0) g[j] = Cd::ld(P + j * np + x, j);
+    else g[j] = Cd::ld(P + o * np + x + dsc[o - 1], j);
+  });
+  const Mom<C> m = moments(g);
+  if (unstable(m.rho)) atomicOr(err, kErrUnstable);
+  const C omega = C(p.omega);
+  Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
+  unroll<9>([&](auto Pi) {
+    constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
+    const C sa = g[a] + omega * (geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[a]);
+    const C sb = g[b] + omega * (geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[b]);
+    if constexpr (ODD) {
+      Cd::st(P + a * np + x + dsc[a - 1], a, sa);
+      Cd::st(P + b * np + x + dsc[b - 1], b, sb);
+    } else {
+      Cd::st(P + b * np + x, a, sa);
+      Cd::st(P + a * np + x, b, sb);
+    }
+  });
 }
 
-// Collision (and, for boundary sites, the boundary rule) of one site whose
-// pre-collision populations are g, followed by the stores of the AA pattern.
-//   dsc: the tile's descriptor; smask: the site's link mask (0 for bulk);
-//   F, K: the site's wall parameters; prof: inlet profile rows (stride kTile);
-//   nbr: per-site neighbour rows (irregular tiles on odd steps).
-template <class S, bool ODD, bool BND>
-__device__ __forceinline__ void collide_store(const DevLattice& d, const StepParams& p, S* P,
-                                              int64_t x, typename Codec<S>::C (&g)[kQ],
-                                              const int32_t* dsc, bool irr, uint32_t smask,
-                                              double Fw, double Kw, const double* prof,
-                                              const int32_t* nbr, int lane, int64_t slot) {
+// Update of a site of a boundary tile.  `code[i]` holds the tile's uniform
+// offsets / non-fluid codes; irregular tiles use the staged per-site table.
+template <class S, bool ODD>
+__device__ __forceinline__ void boundary_update(const DevLattice& d, const StepParams& p, S* P,
+                                                int64_t x, const int32_t* dsc, bool irr,
+                                                uint32_t smask, const unsigned char* st, int lane,
+                                                int64_t slot) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
   const int64_t np = d.npad;
+  const int32_t* nbr_s = reinterpret_cast<const int32_t*>(st + kStNbr);
+  // neighbour index of a fluid link i (odd steps)
+  auto nb = [&](int i) -> int64_t {
+    return irr ? (int64_t)nbr_s[(i - 1) * kTile + lane] : x + dsc[i - 1];
+  };
+  // code of a non-fluid link i: -1 wall, -2-k iolet k
+  auto nfc = [&](int i) -> int32_t {
+    if (!irr) return dsc[i - 1];
+    if constexpr (ODD) return nbr_s[(i - 1) * kTile + lane];
+    else return __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
+  };
+  C g[kQ];
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int o = dir_opp(j);
+    if constexpr (!ODD || j == 0) {
+      g[j] = Cd::ld(P + j * np + x, j);
+    } else {
+      if ((smask >> o) & 1u) g[j] = Cd::ld(P + j * np + x, j);
+      else g[j] = Cd::ld(P + o * np + nb(o), j);
+    }
+  });
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
   const C omega = C(p.omega);
-  // neighbour index of a fluid link i (odd steps)
-  auto nb = [&](int i) -> int64_t {
-    if constexpr (BND) {
-      if (irr) return (int64_t)nbr[(i - 1) * kTile + lane];
+  const C keep = C(1) - omega;  // (1 - 1/tau)
+
+  // Elastic wall velocity (Sec. 2.3-2.4, FP64): dr = dx + dE, U_w = (F + dr - dx)/dr u.
+  C uwx = C(0), uwy = C(0), uwz = C(0);
+  if ((smask & kHasWall) && p.elastic) {
+    const double* F_s = reinterpret_cast<const double*>(st + kStF);
+    const double* K_s = reinterpret_cast<const double*>(st + kStK);
+    const double pr = ((double)m.rho - p.rho0) / 3.0;
+    const double dE = K_s[lane] * (pr > 0.0 ? pr : 0.0);
+    const double dr = 1.0 + dE;
+    const double sc = (F_s[lane] + dr - 1.0) / dr;
+    uwx = C(sc) * m.ux;
+    uwy = C(sc) * m.uy;
+    uwz = C(sc) * m.uz;
+    if (p.write_state) {
+      const int64_t ss = d.slot_stride;
+      d.slot_dE[slot] = dE;
+      d.slot_Uw[slot] = (double)uwx;
+      d.slot_Uw[ss + slot] = (double)uwy;
+      d.slot_Uw[2 * ss + slot] = (double)uwz;
     }
-    return x + dsc[i - 1];
+  }
+  // Inlet velocity (Sec. 3): u_in = a (u_mean p0 + u_amp (ps sin th + pc cos th)).
+  C uix = C(0), uiy = C(0), uiz = C(0);
+  if (smask & kHasInlet) {
+    const double* prof = reinterpret_cast<const double*>(st + kStProf);
+    const int k = (int)((smask & kInletBits) >> kInletShift);
+    const IoletDev& io = d.iolets[k];
+    double gval = io.u_mean * prof[lane];
+    if (!io.steady) {
+      // time factors u_amp sin(th), u_amp cos(th) of this step, from the host
+      // for the first kMaxTimedInlets iolets, else evaluated here
+      double as, ac;
+      if (k < kMaxTimedInlets) {
+        as = p.inlet_sin[k];
+        ac = p.inlet_cos[k];
+      } else {
+        const double th = 2.0 * M_PI * (double)p.step / io.period + io.phase;
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        as = io.u_amp * sn;
+        ac = io.u_amp * cs;
+      }
+      gval += prof[kTile + lane] * as + prof[2 * kTile + lane] * ac;
+    }
+    uix = C(gval * io.axis[0]);
+    uiy = C(gval * io.axis[1]);
+    uiz = C(gval * io.axis[2]);
+  }
+  const C uwsq = C(1.5) * (uwx * uwx + uwy * uwy + uwz * uwz);
+  const C uisq = C(1.5) * (uix * uix + uiy * uiy + uiz * uiz);
+
+  // Boundary population for direction J when the opposite link leaves the
+  // fluid through `c`: bounce-back (sopp = f*_opp(J)) or the GZS form
+  // f^eq_J(rho_b, u_b) + (1 - 1/tau) f^neq_J.
+  auto bc = [&](auto Jc, int32_t c, C sopp, C fneqJ) -> C {
+    constexpr int J = decltype(Jc)::value;
+    if (c == -1) {
+      if (!p.elastic) return sopp;
+      return geq<J, C>(m.drho, m.rho, uwx, uwy, uwz, uwsq) + keep * fneqJ;
+    }
+    const IoletDev& io = d.iolets[-2 - c];
+    if (io.kind == LBM_IOLET_VELOCITY)
+      return geq<J, C>(m.drho, m.rho, uix, uiy, uiz, uisq) + keep * fneqJ;
+    return geq<J, C>(C(io.rho - 1.0), C(io.rho), m.ux, m.uy, m.uz, m.usq) + keep * fneqJ;
   };
+
   Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
-  if constexpr (!BND) {
-    unroll<9>([&](auto Pi) {
-      constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
-      const C sa = g[a] + omega * (geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[a]);
-      const C sb = g[b] + omega * (geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[b]);
-      if constexpr (ODD) {
-        Cd::st(P + a * np + nb(a), a, sa);
-        Cd::st(P + b * np + nb(b), b, sb);
-      } else {
-        Cd::st(P + b * np + x, a, sa);
-        Cd::st(P + a * np + x, b, sb);
-      }
-    });
-    return;
-  } else {
-    const C keep = C(1) - omega;  // (1 - 1/tau)
-    // code of a non-fluid link i: -1 wall, -2-k iolet k
-    auto nfc = [&](int i) -> int32_t {
-      if (!irr) return dsc[i - 1];
-      if constexpr (ODD) return nbr[(i - 1) * kTile + lane];
-      else return __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
-    };
-    // Elastic wall velocity (Sec. 2.3-2.4, FP64): dr = dx + dE, U_w = (F + dr - dx)/dr u.
-    C uwx = C(0), uwy = C(0), uwz = C(0);
-    if ((smask & kHasWall) && p.elastic) {
-      const double pr = ((double)m.rho - p.rho0) / 3.0;
-      const double dE = Kw * (pr > 0.0 ? pr : 0.0);
-      const double dr = 1.0 + dE;
-      const double sc = (Fw + dr - 1.0) / dr;
-      uwx = C(sc) * m.ux;
-      uwy = C(sc) * m.uy;
-      uwz = C(sc) * m.uz;
-      if (p.write_state) {
-        const int64_t ss = d.slot_stride;
-        d.slot_dE[slot] = dE;
-        d.slot_Uw[slot] = (double)uwx;
-        d.slot_Uw[ss + slot] = (double)uwy;
-        d.slot_Uw[2 * ss + slot] = (double)uwz;
-      }
+  unroll<9>([&](auto Pi) {
+    constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
+    const C na = g[a] - geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
+    const C nbq = g[b] - geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
+    const C sa = g[a] - omega * na;
+    const C sb = g[b] - omega * nbq;
+    if (!((smask >> a) & 1u)) {
+      if constexpr (ODD) Cd::st(P + a * np + nb(a), a, sa);
+      else Cd::st(P + b * np + x, a, sa);
+    } else {
+      Cd::st(P + b * np + x, b, bc(std::integral_constant<int, b>{}, nfc(a), sa, nbq));
     }
-    // Inlet velocity (Sec. 3): u_in = a (u_mean p0 + u_amp (ps sin th + pc cos th)).
-    C uix = C(0), uiy = C(0), uiz = C(0);
-    if (smask & kHasInlet) {
-      const int k = (int)((smask & kInletBits) >> kInletShift);
-      const IoletDev& io = d.iolets[k];
-      double gval = io.u_mean * prof[lane];
-      if (!io.steady) {
-        // u_amp sin(th), u_amp cos(th) of this step: from the host for the
-        // first kMaxTimedInlets iolets, else evaluated here
-        double as, ac;
-        if (k < kMaxTimedInlets) {
-          as = p.inlet_sin[k];
-          ac = p.inlet_cos[k];
-        } else {
-          const double th = 2.0 * M_PI * (double)p.step / io.period + io.phase;
-          double sn, cs;
-          sincos(th, &sn, &cs);
-          as = io.u_amp * sn;
-          ac = io.u_amp * cs;
-        }
-        gval += prof[kTile + lane] * as + prof[2 * kTile + lane] * ac;
-      }
-      uix = C(gval * io.axis[0]);
-      uiy = C(gval * io.axis[1]);
-      uiz = C(gval * io.axis[2]);
+    if (!((smask >> b) & 1u)) {
+      if constexpr (ODD) Cd::st(P + b * np + nb(b), b, sb);
+      else Cd::st(P + a * np + x, b, sb);
+    } else {
+      Cd::st(P + a * np + x, a, bc(std::integral_constant<int, a>{}, nfc(b), sb, na));
     }
-    const C uwsq = C(1.5) * (uwx * uwx + uwy * uwy + uwz * uwz);
-    const C uisq = C(1.5) * (uix * uix + uiy * uiy + uiz * uiz);
-    // Boundary population for direction J when the opposite link leaves the
-    // fluid through `c`: bounce-back (sopp = f*_opp(J)) or the GZS form
-    // f^eq_J(rho_b, u_b) + (1 - 1/tau) f^neq_J.
-    auto bc = [&](auto Jc, int32_t c, C sopp, C fneqJ) -> C {
-      constexpr int J = decltype(Jc)::value;
-      if (c == -1) {
-        if (!p.elastic) return sopp;
-        return geq<J, C>(m.drho, m.rho, uwx, uwy, uwz, uwsq) + keep * fneqJ;
-      }
-      const IoletDev& io = d.iolets[-2 - c];
-      if (io.kind == LBM_IOLET_VELOCITY)
-        return geq<J, C>(m.drho, m.rho, uix, uiy, uiz, uisq) + keep * fneqJ;
-      return geq<J, C>(C(io.rho - 1.0), C(io.rho), m.ux, m.uy, m.uz, m.usq) + keep * fneqJ;
-    };
-    unroll<9>([&](auto Pi) {
-      constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
-      const C na = g[a] - geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
-      const C nbq = g[b] - geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
-      const C sa = g[a] - omega * na;
-      const C sb = g[b] - omega * nbq;
-      if (!((smask >> a) & 1u)) {
-        if constexpr (ODD) Cd::st(P + a * np + nb(a), a, sa);
-        else Cd::st(P + b * np + x, a, sa);
-      } else {
-        Cd::st(P + b * np + x, b, bc(std::integral_constant<int, b>{}, nfc(a), sa, nbq));
-      }
-      if (!((smask >> b) & 1u)) {
-        if constexpr (ODD) Cd::st(P + b * np + nb(b), b, sb);
-        else Cd::st(P + a * np + x, b, sb);
-      } else {
-        Cd::st(P + a * np + x, a, bc(std::integral_constant<int, a>{}, nfc(b), sb, na));
-      }
-    });
-  }
+  });
 }
 
-// Word `lane` (< 20) of the descriptor at launch position k.
-__device__ __forceinline__ int32_t desc_word(const DevLattice& d, int64_t k, int lane) {
-  return (lane < 20 && k < d.n_tiles) ? __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane)
-                                      : 0;
-}
+#ifndef LBM_BULK_MINB
+#define LBM_BULK_MINB 4
+#endif
+constexpr int kBulkWarps = 8;      // k_bulk: tiles (warps) per CTA
+constexpr int kBoundaryWarps = 4;  // k_boundary: tiles (warps) per CTA
 
-// Start the copies of launch position k into stage b (whole warp); `word` is
-// the lane's word of k's descriptor, fetched an iteration earlier.
-template <class S, bool ODD, int NST>
-__device__ __forceinline__ void issue_tile(const DevLattice& d, WarpSmem<S, NST>& sm, int b,
-                                           int64_t k, int32_t word, int lane) {
-  if (lane < 20) sm.dsc[b][lane] = word;
-  __syncwarp();
-  const int32_t* dsc = sm.dsc[b];
-  const uint32_t tm = (uint32_t)dsc[18];
-  const int64_t t = dsc[19];
-  const bool irr = tm & kIrregular, bnd = tm != 0, wall = tm & kHasWall;
-  const uint32_t bytes = (irr ? 0u : (uint32_t)(kQ * Seg<S>::B)) +
-                         (bnd ? 128u + (wall ? 512u : 0u) : 0u);
-  // order this warp's earlier reads of the stage before the async writes
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (lane == 0) mbar_expect_tx(&sm.bar[b], bytes);
-  __syncwarp();
-  if (!irr && lane < kQ) {
-    const int j = lane;
-    const int64_t np = d.npad, x0 = t * kTile;
-    int64_t e = j * np + x0;
-    if (ODD && j != 0) {
-      const int o = dir_opp(j);
-      if (!((tm >> o) & 1u)) {
-        const int64_t q = x0 + dsc[o - 1];
-        e = o * np + (q & ~(int64_t)(Seg<S>::A - 1));
-      }
-    }
-    bulk_g2s(sm.pop[b][j], static_cast<const S*>(d.pop) + e, Seg<S>::B, &sm.bar[b]);
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK_MINB)
+    k_bulk(const DevLattice d, const StepParams p) {
+  __shared__ __align__(16) int32_t desc_s[kBulkWarps][20];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k = d.n_boundary + (int64_t)blockIdx.x * kBulkWarps + w;
+  if (k >= d.n_tiles) return;  // warp-uniform
+  int32_t* dsc = desc_s[w];
+  if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
+  if (p.prefetch > 0 && k + p.prefetch < d.n_tiles && lane < kQ) {
+    const int64_t tp = __ldg(&d.launch[k + p.prefetch].tile);
+    bulk_prefetch_l2(static_cast<const S*>(d.pop) + lane * d.npad + tp * kTile,
+                     kTile * sizeof(S));
   }
-  if (bnd && lane == 0) {
-    const int64_t s0 = k * kTile;  // boundary tiles lead the launch order
-    bulk_g2s(sm.mask[b], d.slot_mask + s0, 128, &sm.bar[b]);
-    if (wall) {
-      bulk_g2s(sm.F[b], d.slot_F + s0, 256, &sm.bar[b]);
-      bulk_g2s(sm.K[b], d.slot_kappa + s0, 256, &sm.bar[b]);
-    }
-  }
+  __syncwarp();
+  const int64_t x = (int64_t)dsc[19] * kTile + lane;
+  if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p, d.err);
 }
 
 template <class S, bool ODD>
-__global__ void __launch_bounds__(Pipe<S>::WARPS * 32)
-    k_step(const DevLattice d, const StepParams p) {
-  using Cd = Codec<S>;
-  using C = typename Cd::C;
-  constexpr int NST = Pipe<S>::NST;
-  constexpr int A = Seg<S>::A;
-  extern __shared__ __align__(128) unsigned char dyn[];
+__global__ void __launch_bounds__(kBoundaryWarps * 32)
+    k_boundary(const DevLattice d, const StepParams p) {
+  __shared__ __align__(128) unsigned char stage[kBoundaryWarps][kStBytes];
+  __shared__ __align__(16) int32_t desc_s[kBoundaryWarps][20];
+  __shared__ uint64_t bars[kBoundaryWarps];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpSmem<S, NST>& sm = reinterpret_cast<WarpSmem<S, NST>*>(dyn)[w];
-  if (lane == 0) {
-    for (int b = 0; b < NST; ++b) mbar_init(&sm.bar[b], 1);
-    mbar_init(&sm.barx, 1);
-  }
+  const int64_t k = (int64_t)blockIdx.x * kBoundaryWarps + w;
+  if (k >= d.n_boundary) return;  // warp-uniform
+  int32_t* dsc = desc_s[w];
+  if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
   __syncwarp();
-  S* P = static_cast<S*>(d.pop);
-  const int64_t W = (int64_t)gridDim.x * Pipe<S>::WARPS;
-  const int64_t k0 = (int64_t)blockIdx.x * Pipe<S>::WARPS + w;
-  uint32_t phase = 0, phx = 0, pending = 0;
-  // prologue: the first NST-1 tiles, and the descriptor of the next one
-  for (int b = 0; b < NST - 1; ++b) {
-    const int64_t k = k0 + b * W;
-    if (k < d.n_tiles) {
-      issue_tile<S, ODD, NST>(d, sm, b, k, desc_word(d, k, lane), lane);
-      pending |= 1u << b;
+  const uint32_t tmask = (uint32_t)dsc[18];
+  const int64_t x = (int64_t)dsc[19] * kTile + lane;
+  unsigned char* st = stage[w];
+  uint64_t* bar = &bars[w];
+  const int64_t slot0 = k * kTile;  // boundary tiles lead the launch order
+  const bool irr = tmask & kIrregular;
+  if (lane == 0) mbar_init(bar, 1);
+  __syncwarp();
+  if (lane == 0) {
+    const int64_t ss = d.slot_stride;
+    const bool wall = tmask & kHasWall, inl = tmask & kHasInlet, nbr = ODD && irr;
+    mbar_expect_tx(bar, 128u + (wall ? 512u : 0u) + (inl ? 768u : 0u) + (nbr ? 2304u : 0u));
+    bulk_g2s(st + kStMask, d.slot_mask + slot0, 128, bar);
+    if (wall) {
+      bulk_g2s(st + kStF, d.slot_F + slot0, 256, bar);
+      bulk_g2s(st + kStK, d.slot_kappa + slot0, 256, bar);
     }
+    if (inl)
+      for (int c = 0; c < 3; ++c)
+        bulk_g2s(st + kStProf + 256 * c, d.slot_prof + c * ss + slot0, 256, bar);
+    if (nbr)
+      for (int i = 0; i < 18; ++i)
+        bulk_g2s(st + kStNbr + 128 * i, d.slot_nbr + i * ss + slot0, 128, bar);
   }
-  int32_t dnext = desc_word(d, k0 + (int64_t)(NST - 1) * W, lane);
-  int b = 0;
-  for (int64_t k = k0; k < d.n_tiles; k += W) {
-    // refill the stage freed by the previous tile; fetch the descriptor of the
-    // tile after it, to be used one iteration from now
-    const int ba = (b + NST - 1) % NST;
-    const int64_t ka = k + (int64_t)(NST - 1) * W;
-    if (ka < d.n_tiles) {
-      issue_tile<S, ODD, NST>(d, sm, ba, ka, dnext, lane);
-      pending |= 1u << ba;
-    }
-    dnext = desc_word(d, ka + W, lane);
-    if (!mbar_wait_bounded(&sm.bar[b], (phase >> b) & 1u)) {
-      if (lane == 0) atomicOr(d.err, kErrTimeout);
-      for (int s = 0; s < NST; ++s)  // a bounded wait on every stage still in flight
-        if ((pending >> s) & 1u) mbar_wait_bounded(&sm.bar[s], (phase >> s) & 1u);
-      return;
-    }
-    phase ^= 1u << b;
-    pending &= ~(1u << b);
-    const int32_t* dsc = sm.dsc[b];
-    const uint32_t tm = (uint32_t)dsc[18];
-    const int64_t t = dsc[19];
-    const int64_t x = t * kTile + lane;
-    const bool irr = tm & kIrregular;
-    C g[kQ];
-    if (!irr) {
-      // populations from the stage: direction j of lane l at pop[b][j][l + m_j]
-      unroll<kQ>([&](auto J) {
-        constexpr int j = decltype(J)::value;
-        int mj = 0;
-        if constexpr (ODD && j != 0) {
-          constexpr int o = dir_opp(j);
-          if (!((tm >> o) & 1u)) mj = (int)((t * kTile + dsc[o - 1]) & (A - 1));
-        }
-        g[j] = Cd::ld(&sm.pop[b][j][lane + mj], j);
-      });
-    }
-    if (tm == 0) {
-      if (x < d.n)
-        collide_store<S, ODD, false>(d, p, P, x, g, dsc, false, 0u, 0.0, 0.0, nullptr, nullptr,
-                                     lane, 0);
-    } else {
-      const int64_t slot = k * kTile + lane;
-      const bool inl = tm & kHasInlet, nbrx = ODD && irr;
-      if (inl || nbrx) {
-        // synchronous extras: inlet profile, per-site neighbours
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) {
-          const int64_t ss = d.slot_stride, s0 = k * kTile;
-          mbar_expect_tx(&sm.barx, (inl ? 768u : 0u) + (nbrx ? 2304u : 0u));
-          if (inl)
-            for (int c = 0; c < 3; ++c) bulk_g2s(sm.prof[c], d.slot_prof + c * ss + s0, 256, &sm.barx);
-          if (nbrx)
-            for (int i = 0; i < 18; ++i) bulk_g2s(sm.nbr[i], d.slot_nbr + i * ss + s0, 128, &sm.barx);
-        }
-        if (!mbar_wait_bounded(&sm.barx, phx)) {
-          if (lane == 0) atomicOr(d.err, kErrTimeout);
-          mbar_wait_bounded(&sm.barx, phx);
-          for (int s = 0; s < NST; ++s)
-            if ((pending >> s) & 1u) mbar_wait_bounded(&sm.bar[s], (phase >> s) & 1u);
-          return;
-        }
-        phx ^= 1u;
-      }
-      const uint32_t smask = sm.mask[b][lane];
-      if (smask & kValid) {
-        if (irr) {
-          // per-lane gather of the pre-collision populations
-          const int64_t np = d.npad;
-          unroll<kQ>([&](auto J) {
-            constexpr int j = decltype(J)::value;
-            constexpr int o = dir_opp(j);
-            if constexpr (!ODD || j == 0) {
-              g[j] = Cd::ld(P + j * np + x, j);
-            } else {
-              if ((smask >> o) & 1u) g[j] = Cd::ld(P + j * np + x, j);
-              else g[j] = Cd::ld(P + o * np + sm.nbr[o - 1][lane], j);
-            }
-          });
-        }
-        collide_store<S, ODD, true>(d, p, P, x, g, dsc, irr, smask, sm.F[b][lane], sm.K[b][lane],
-                                    &sm.prof[0][0], &sm.nbr[0][0], lane, slot);
-      }
-    }
-    __syncwarp();  // the stage is free again
-    b = (b + 1) % NST;
+  if (!mbar_wait_bounded(bar, 0)) {
+    if (lane == 0) atomicOr(d.err, kErrTimeout);
+    mbar_wait_bounded(bar, 0);  // a second bounded chance for copies still in flight
+    return;
   }
+  const uint32_t smask = reinterpret_cast<const uint32_t*>(st + kStMask)[lane];
+  if (smask & kValid)
+    boundary_update<S, ODD>(d, p, static_cast<S*>(d.pop), x, dsc, irr, smask, st, lane,
+                            slot0 + lane);
 }
 
 // ------------------------------------------------ state conversion kernels
@@ -775,33 +686,33 @@ __global__ void k_wss(const DevLattice d, int odd, double tau, const int64_t* si
 
 // ------------------------------------------------------------- dispatch
 
+// One step: k_boundary on the side stream, k_bulk on the main stream, joined
+// on the main stream.  ev (profiling): before the fork, after k_bulk, after
+// the join, all on the main stream.
 template <class S>
-int step_grid_t(int sms) {
-  const size_t sb = smem_bytes<S>();
-  cudaError_t e = cudaFuncSetAttribute(k_step<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sb);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_step<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-  int a = 0, c = 0;
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<S, false>, Pipe<S>::WARPS * 32, sb);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_step<S, true>, Pipe<S>::WARPS * 32, sb);
-  if (e != cudaSuccess) return -(int)e;
-  return (a < c ? a : c) * sms;
-}
-
-template <class S>
-int step_t(const DevLattice& d, const StepParams& p, cudaStream_t s, void* const* ev) {
-  const int64_t need = (d.n_tiles + Pipe<S>::WARPS - 1) / Pipe<S>::WARPS;
-  const unsigned nb = (unsigned)(need < d.step_grid ? need : d.step_grid);
-  const size_t sb = smem_bytes<S>();
-  if (ev) cudaEventRecord((cudaEvent_t)ev[0], s);
-  if (nb) {
-    if (p.step & 1) k_step<S, true><<<nb, Pipe<S>::WARPS * 32, sb, s>>>(d, p);
-    else k_step<S, false><<<nb, Pipe<S>::WARPS * 32, sb, s>>>(d, p);
+int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void* const* ev) {
+  cudaStream_t m = (cudaStream_t)ss.main, side = (cudaStream_t)ss.side;
+  const unsigned nbnd = (unsigned)((d.n_boundary + kBoundaryWarps - 1) / kBoundaryWarps);
+  const int64_t nbulk_tiles = d.n_tiles - d.n_boundary;
+  const unsigned nbulk = (unsigned)((nbulk_tiles + kBulkWarps - 1) / kBulkWarps);
+  const bool odd = p.step & 1;
+  if (ev) cudaEventRecord((cudaEvent_t)ev[0], m);
+  if (nbnd) {
+    cudaEventRecord((cudaEvent_t)ss.fork, m);
+    cudaStreamWaitEvent(side, (cudaEvent_t)ss.fork, 0);
+    if (odd) k_boundary<S, true><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
+    else k_boundary<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
   }
-  if (ev) cudaEventRecord((cudaEvent_t)ev[1], s);
+  if (nbulk) {
+    if (odd) k_bulk<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+    else k_bulk<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+  }
+  if (ev) cudaEventRecord((cudaEvent_t)ev[1], m);
+  if (nbnd) {
+    cudaEventRecord((cudaEvent_t)ss.join, side);
+    cudaStreamWaitEvent(m, (cudaEvent_t)ss.join, 0);
+  }
+  if (ev) cudaEventRecord((cudaEvent_t)ev[2], m);
   return (int)cudaGetLastError();
 }
 
@@ -830,18 +741,11 @@ size_t storage_bytes(int storage) {
 
 int reduce_partials() { return kRedBlocks; }
 
-int step_grid(int storage, int sms) {
-  return dispatch(storage, [&](auto tag) {
-    using S = std::remove_pointer_t<decltype(tag)>;
-    return step_grid_t<S>(sms);
-  });
-}
-
-int launch_step(int storage, const DevLattice& d, const StepParams& p, void* stream,
+int launch_step(int storage, const DevLattice& d, const StepParams& p, const StepStreams& ss,
                 void* const* events) {
   return dispatch(storage, [&](auto tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    return step_t<S>(d, p, (cudaStream_t)stream, events);
+    return step_t<S>(d, p, ss, events);
   });
 }
 

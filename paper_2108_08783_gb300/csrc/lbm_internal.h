@@ -118,7 +118,7 @@ struct DevLattice {
   const IoletDev* iolets = nullptr;
   int32_t n_iolets = 0;
   int* err = nullptr;
-  int64_t step_grid = 1;  // CTAs of the persistent step kernel (resident CTAs x SMs)
+  int64_t n_boundary = 0;  // boundary tiles = leading entries of the launch order
 };
 
 // Iolets whose inlet time factors are evaluated on the host each step.
@@ -138,8 +138,17 @@ struct StepParams {
 
 // Kernel launchers (kernels.cu); storage is LBM_F64 ... LBM_BF16S.
 // All return cudaError_t values cast to int.
-// events: NULL, or two cudaEvent_t recorded before and after the step kernel.
-int launch_step(int storage, const DevLattice& d, const StepParams& p, void* stream,
+// Streams and events of one step: the boundary kernel runs on `side`,
+// forked from and joined back into `main` with the two events.
+struct StepStreams {
+  void* main;
+  void* side;
+  void* fork;
+  void* join;
+};
+// events: NULL, or three cudaEvent_t recorded on the main stream before the
+// fork, after the bulk kernel and after the join.
+int launch_step(int storage, const DevLattice& d, const StepParams& p, const StepStreams& ss,
                 void* const* events);
 int launch_init(int storage, const DevLattice& d, const double* rho, const double* u,
                 void* stream);
@@ -155,9 +164,7 @@ int launch_wss(int storage, const DevLattice& d, int odd_layout, double tau,
                const int64_t* sites, const double* normals, int64_t m, double* out,
                void* stream);
 size_t storage_bytes(int storage);
-// Grid of the persistent step kernel for `sms` SMs (also sets its shared-memory
-// limit), or -cudaError on failure.
-int step_grid(int storage, int sms);
+
 int reduce_partials();
 
 }  // namespace lbm

@@ -212,11 +212,11 @@ class Lattice:
         self._check(self._lib.lbm_profile(self.h, 1 if enable else 0))
 
     def profile_read(self):
-        """(summed device ms, launch count) of the step kernel since profile(True)."""
-        ms = np.zeros(1)
-        n = np.zeros(1, np.int64)
+        """Since profile(True): ((step ms, bulk-kernel ms), (bulk launches, boundary launches))."""
+        ms = np.zeros(2)
+        n = np.zeros(2, np.int64)
         self._check(self._lib.lbm_profile_read(self.h, _ptr(ms), _ptr(n)))
-        return float(ms[0]), int(n[0])
+        return (float(ms[0]), float(ms[1])), (int(n[0]), int(n[1]))
 
     def wss(self, sites, normals):
         sites = np.ascontiguousarray(sites, np.int64)
