@@ -14,6 +14,9 @@
 
 #include "lbm_internal.h"
 
+#ifndef LBM_SIDE_PRIORITY
+#define LBM_SIDE_PRIORITY 1
+#endif
 #ifndef LBM_DEFAULT_PREFETCH
 #define LBM_DEFAULT_PREFETCH 2048
 #endif
@@ -304,7 +307,12 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   }
   {
     // side stream and fork/join events of the boundary kernel
-    cudaError_t ge = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    // higher priority, so that the block scheduler dispatches boundary CTAs
+    // as soon as bulk CTAs retire instead of after the whole bulk grid
+    int lo = 0, hi = 0;
+    cudaError_t ge = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (ge == cudaSuccess)
+      ge = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, LBM_SIDE_PRIORITY ? hi : lo);
     if (ge == cudaSuccess) ge = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
     if (ge == cudaSuccess) ge = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
     if (ge != cudaSuccess) {

@@ -302,11 +302,35 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
 
 // Update of a site of a boundary tile.  `code[i]` holds the tile's uniform
 // offsets / non-fluid codes; irregular tiles use the staged per-site table.
+// Pre-collision populations of a boundary site: direction j comes from its own
+// slot when the link opp(j) leaves the fluid (bit opp(j) of `nf`), else (odd
+// steps) from the neighbour along opp(j).
+template <class S, bool ODD>
+__device__ __forceinline__ void boundary_load(const S* P, int64_t np, int64_t x, uint32_t nf,
+                                              const int32_t* dsc, bool irr, const int32_t* nbr_s,
+                                              int lane, typename Codec<S>::C (&g)[kQ]) {
+  using Cd = Codec<S>;
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int o = dir_opp(j);
+    if constexpr (!ODD || j == 0) {
+      g[j] = Cd::ld(P + j * np + x, j);
+    } else {
+      if ((nf >> o) & 1u) {
+        g[j] = Cd::ld(P + j * np + x, j);
+      } else {
+        const int64_t y = irr ? (int64_t)nbr_s[(o - 1) * kTile + lane] : x + dsc[o - 1];
+        g[j] = Cd::ld(P + o * np + y, j);
+      }
+    }
+  });
+}
+
 template <class S, bool ODD>
 __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepParams& p, S* P,
                                                 int64_t x, const int32_t* dsc, bool irr,
                                                 uint32_t smask, const unsigned char* st, int lane,
-                                                int64_t slot) {
+                                                int64_t slot, typename Codec<S>::C (&g)[kQ]) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
   const int64_t np = d.npad;
@@ -321,34 +345,28 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
     if constexpr (ODD) return nbr_s[(i - 1) * kTile + lane];
     else return __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
   };
-  C g[kQ];
-  unroll<kQ>([&](auto J) {
-    constexpr int j = decltype(J)::value;
-    constexpr int o = dir_opp(j);
-    if constexpr (!ODD || j == 0) {
-      g[j] = Cd::ld(P + j * np + x, j);
-    } else {
-      if ((smask >> o) & 1u) g[j] = Cd::ld(P + j * np + x, j);
-      else g[j] = Cd::ld(P + o * np + nb(o), j);
-    }
-  });
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
   const C omega = C(p.omega);
   const C keep = C(1) - omega;  // (1 - 1/tau)
 
-  // Elastic wall velocity (Sec. 2.3-2.4, FP64): dr = dx + dE, U_w = (F + dr - dx)/dr u.
+  // Elastic wall velocity (Sec. 2.3-2.4): the tube-law expansion dE and the
+  // distance dr = dx + dE in FP64; the ratio U_w/u_f = (F + dr - dx)/dr in the
+  // compute type (FP64 throughput is low on this GPU and the ratio only
+  // scales an FP32 velocity on the FP32 paths).
   C uwx = C(0), uwy = C(0), uwz = C(0);
   if ((smask & kHasWall) && p.elastic) {
     const double* F_s = reinterpret_cast<const double*>(st + kStF);
     const double* K_s = reinterpret_cast<const double*>(st + kStK);
-    const double pr = ((double)m.rho - p.rho0) / 3.0;
+    const double pr = ((double)m.rho - p.rho0) * (1.0 / 3.0);
     const double dE = K_s[lane] * (pr > 0.0 ? pr : 0.0);
     const double dr = 1.0 + dE;
-    const double sc = (F_s[lane] + dr - 1.0) / dr;
-    uwx = C(sc) * m.ux;
-    uwy = C(sc) * m.uy;
-    uwz = C(sc) * m.uz;
+    C sc;
+    if constexpr (std::is_same<C, double>::value) sc = (F_s[lane] + dr - 1.0) / dr;
+    else sc = C(F_s[lane] + dE) * recip(C(dr));
+    uwx = sc * m.ux;
+    uwy = sc * m.uy;
+    uwz = sc * m.uz;
     if (p.write_state) {
       const int64_t ss = d.slot_stride;
       d.slot_dE[slot] = dE;
@@ -449,8 +467,11 @@ __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK
   if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p, d.err);
 }
 
+#ifndef LBM_BOUNDARY_MINB
+#define LBM_BOUNDARY_MINB 6
+#endif
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kBoundaryWarps * 32)
+__global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_BOUNDARY_MINB)
     k_boundary(const DevLattice d, const StepParams p) {
   __shared__ __align__(128) unsigned char stage[kBoundaryWarps][kStBytes];
   __shared__ __align__(16) int32_t desc_s[kBoundaryWarps][20];
@@ -485,15 +506,23 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32)
       for (int i = 0; i < 18; ++i)
         bulk_g2s(st + kStNbr + 128 * i, d.slot_nbr + i * ss + slot0, 128, bar);
   }
+  // A uniform tile's links are the same in every lane: its populations can be
+  // read while the staging copies are in flight.
+  using C = typename Codec<S>::C;
+  C g[kQ];
+  S* P = static_cast<S*>(d.pop);
+  const int32_t* nbr_s = reinterpret_cast<const int32_t*>(st + kStNbr);
+  if (!irr && x < d.n)
+    boundary_load<S, ODD>(P, d.npad, x, tmask & kDirBits, dsc, false, nbr_s, lane, g);
   if (!mbar_wait_bounded(bar, 0)) {
     if (lane == 0) atomicOr(d.err, kErrTimeout);
     mbar_wait_bounded(bar, 0);  // a second bounded chance for copies still in flight
     return;
   }
   const uint32_t smask = reinterpret_cast<const uint32_t*>(st + kStMask)[lane];
-  if (smask & kValid)
-    boundary_update<S, ODD>(d, p, static_cast<S*>(d.pop), x, dsc, irr, smask, st, lane,
-                            slot0 + lane);
+  if (!(smask & kValid)) return;
+  if (irr) boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, true, nbr_s, lane, g);
+  boundary_update<S, ODD>(d, p, P, x, dsc, irr, smask, st, lane, slot0 + lane, g);
 }
 
 // ------------------------------------------------ state conversion kernels
