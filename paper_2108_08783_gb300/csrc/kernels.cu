@@ -467,8 +467,149 @@ __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK
   if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p, d.err);
 }
 
+#ifndef LBM_BULK2_MINB
+#define LBM_BULK2_MINB 3
+#endif
+#ifndef LBM_BULK_SITES
+#define LBM_BULK_SITES 2
+#endif
+// ------------------------------------------------- packed two-site bulk path
+//
+// On the FP32-compute paths each thread of k_bulk2 updates the same lane of two
+// bulk tiles at once, holding the pair of sites in float2 registers, so the
+// collision runs on Blackwell's packed f32x2 add/mul/fma (one instruction per
+// two sites).  Loads and stores stay per site (the two sites are 32 tiles
+// apart in memory at most, never adjacent).
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b as one fused operation: b * (-1) + a, rounded once
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
+
+// c . u of the first direction of pair P (directions 2P-1, 2P), P = 1..9.
+template <int P>
+__device__ __forceinline__ float2 dpair(float2 ux, float2 uy, float2 uz) {
+  if constexpr (P == 1) return ux;
+  else if constexpr (P == 2) return uy;
+  else if constexpr (P == 3) return uz;
+  else if constexpr (P == 4) return add2(ux, uy);
+  else if constexpr (P == 5) return sub2(ux, uy);
+  else if constexpr (P == 6) return add2(ux, uz);
+  else if constexpr (P == 7) return sub2(ux, uz);
+  else if constexpr (P == 8) return add2(uy, uz);
+  else return sub2(uy, uz);
+}
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBulkWarps * 32, LBM_BULK2_MINB)
+    k_bulk2(const DevLattice d, const StepParams p) {
+  using Cd = Codec<S>;
+  __shared__ __align__(16) int32_t desc_s[kBulkWarps][2][20];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ka = d.n_boundary + 2 * ((int64_t)blockIdx.x * kBulkWarps + w);
+  if (ka >= d.n_tiles) return;  // warp-uniform
+  const bool two = ka + 1 < d.n_tiles;
+  int32_t* da = desc_s[w][0];
+  int32_t* db = desc_s[w][1];
+  if (lane < 20) {
+    da[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + ka) + lane);
+    db[lane] = two ? __ldg(reinterpret_cast<const int32_t*>(d.launch + ka + 1) + lane) : 0;
+  }
+  if (p.prefetch > 0 && lane < kQ) {
+    for (int q = 0; q < 2; ++q) {
+      const int64_t kp = ka + q + p.prefetch;
+      if (kp < d.n_tiles) {
+        const int64_t tp = __ldg(&d.launch[kp].tile);
+        bulk_prefetch_l2(static_cast<const S*>(d.pop) + lane * d.npad + tp * kTile,
+                         kTile * sizeof(S));
+      }
+    }
+  }
+  __syncwarp();
+  const int64_t xa = (int64_t)da[19] * kTile + lane;
+  const int64_t xb = (int64_t)db[19] * kTile + lane;
+  const bool va = xa < d.n, vb = two && xb < d.n;
+  S* P = static_cast<S*>(d.pop);
+  const int64_t np = d.npad;
+  float2 g[kQ];
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int o = dir_opp(j);
+    int64_t ia, ib;
+    if constexpr (!ODD || j == 0) {
+      ia = j * np + xa;
+      ib = j * np + xb;
+    } else {
+      ia = o * np + xa + da[o - 1];
+      ib = o * np + xb + db[o - 1];
+    }
+    g[j].x = va ? Cd::ld(P + ia, j) : 0.f;
+    g[j].y = vb ? Cd::ld(P + ib, j) : 0.f;
+  });
+  // moments (Eqs. Density, Momentum)
+  const float2 a1 = sub2(g[1], g[2]), a3 = sub2(g[3], g[4]), a5 = sub2(g[5], g[6]);
+  const float2 a7 = sub2(g[7], g[8]), a9 = sub2(g[9], g[10]), a11 = sub2(g[11], g[12]);
+  const float2 a13 = sub2(g[13], g[14]), a15 = sub2(g[15], g[16]), a17 = sub2(g[17], g[18]);
+  const float2 drho =
+      add2(add2(add2(g[0], add2(g[1], g[2])), add2(add2(g[3], g[4]), add2(g[5], g[6]))),
+           add2(add2(add2(add2(g[7], g[8]), add2(g[9], g[10])),
+                     add2(add2(g[11], g[12]), add2(g[13], g[14]))),
+                add2(add2(g[15], g[16]), add2(g[17], g[18]))));
+  const float2 jx = add2(add2(add2(a1, a7), add2(a9, a11)), a13);
+  const float2 jy = add2(sub2(add2(a3, a7), sub2(a9, a15)), a17);
+  const float2 jz = sub2(sub2(add2(a5, a11), sub2(a13, a15)), a17);
+  const float2 rho = add2(f2(1.f), drho);
+  if (unstable(rho.x) || (vb && unstable(rho.y))) atomicOr(d.err, kErrUnstable);
+  const float2 inv = make_float2(recip(rho.x), vb ? recip(rho.y) : 0.f);
+  const float2 ux = mul2(jx, inv), uy = mul2(jy, inv), uz = mul2(jz, inv);
+  const float2 usq = mul2(f2(1.5f), fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
+  const float2 om = f2((float)p.omega);
+  // BGK relaxation (Eq. LBE_SRT) with the shifted equilibrium, pairwise:
+  //   s = w (drho + rho (4.5 d^2 - u.u 1.5)), a = 3 w rho d,
+  //   g^eq(2P-1) = s + a, g^eq(2P) = s - a.
+  const float2 r3w_ax = mul2(f2(3.f / 18.f), rho), r3w_dg = mul2(f2(3.f / 36.f), rho);
+  {
+    const float2 e0 = mul2(f2(1.f / 3.f), fma2(rho, sub2(f2(0.f), usq), drho));
+    const float2 s0 = fma2(om, sub2(e0, g[0]), g[0]);
+    if (va) Cd::st(P + xa, 0, s0.x);
+    if (vb) Cd::st(P + xb, 0, s0.y);
+  }
+  unroll<9>([&](auto Pi) {
+    constexpr int pr = decltype(Pi)::value + 1;
+    constexpr int a = 2 * pr - 1, b = a + 1;
+    const float2 wv = f2(pr <= 3 ? 1.f / 18.f : 1.f / 36.f);
+    const float2 r3w = pr <= 3 ? r3w_ax : r3w_dg;
+    const float2 dd = dpair<pr>(ux, uy, uz);
+    const float2 s = mul2(wv, fma2(rho, fma2(f2(4.5f), mul2(dd, dd), sub2(f2(0.f), usq)), drho));
+    const float2 an = mul2(r3w, dd);
+    const float2 sa = fma2(om, sub2(add2(s, an), g[a]), g[a]);
+    const float2 sb = fma2(om, sub2(sub2(s, an), g[b]), g[b]);
+    if constexpr (ODD) {
+      if (va) {
+        Cd::st(P + a * np + xa + da[a - 1], a, sa.x);
+        Cd::st(P + b * np + xa + da[b - 1], b, sb.x);
+      }
+      if (vb) {
+        Cd::st(P + a * np + xb + db[a - 1], a, sa.y);
+        Cd::st(P + b * np + xb + db[b - 1], b, sb.y);
+      }
+    } else {
+      if (va) {
+        Cd::st(P + b * np + xa, a, sa.x);
+        Cd::st(P + a * np + xa, b, sb.x);
+      }
+      if (vb) {
+        Cd::st(P + b * np + xb, a, sa.y);
+        Cd::st(P + a * np + xb, b, sb.y);
+      }
+    }
+  });
+}
+
 #ifndef LBM_BOUNDARY_MINB
-#define LBM_BOUNDARY_MINB 6
+#define LBM_BOUNDARY_MINB 8
 #endif
 template <class S, bool ODD>
 __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_BOUNDARY_MINB)
@@ -723,7 +864,10 @@ int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void
   cudaStream_t m = (cudaStream_t)ss.main, side = (cudaStream_t)ss.side;
   const unsigned nbnd = (unsigned)((d.n_boundary + kBoundaryWarps - 1) / kBoundaryWarps);
   const int64_t nbulk_tiles = d.n_tiles - d.n_boundary;
-  const unsigned nbulk = (unsigned)((nbulk_tiles + kBulkWarps - 1) / kBulkWarps);
+  // FP32-compute paths: two tiles per warp (packed f32x2 collision)
+  constexpr bool kTwo = !std::is_same<S, double>::value && LBM_BULK_SITES == 2;
+  const int64_t per_cta = kBulkWarps * (kTwo ? 2 : 1);
+  const unsigned nbulk = (unsigned)((nbulk_tiles + per_cta - 1) / per_cta);
   const bool odd = p.step & 1;
   if (ev) cudaEventRecord((cudaEvent_t)ev[0], m);
   if (nbnd) {
@@ -733,8 +877,13 @@ int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void
     else k_boundary<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
   }
   if (nbulk) {
-    if (odd) k_bulk<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
-    else k_bulk<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+    if constexpr (kTwo) {
+      if (odd) k_bulk2<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+      else k_bulk2<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+    } else {
+      if (odd) k_bulk<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+      else k_bulk<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+    }
   }
   if (ev) cudaEventRecord((cudaEvent_t)ev[1], m);
   if (nbnd) {
