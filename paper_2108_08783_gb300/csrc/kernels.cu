@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK
 #define LBM_BULK2_MINB 3
 #endif
 #ifndef LBM_BULK_SITES
-#define LBM_BULK_SITES 2
+#define LBM_BULK_SITES 1
 #endif
 // ------------------------------------------------- packed two-site bulk path
 //
