@@ -448,14 +448,10 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
 constexpr int kBulkWarps = 8;      // k_bulk: tiles (warps) per CTA
 constexpr int kBoundaryWarps = 4;  // k_boundary: tiles (warps) per CTA
 
+// Bulk tile at launch position k (whole warp); dsc: the warp's 20-word area.
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK_MINB)
-    k_bulk(const DevLattice d, const StepParams p) {
-  __shared__ __align__(16) int32_t desc_s[kBulkWarps][20];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t k = d.n_boundary + (int64_t)blockIdx.x * kBulkWarps + w;
-  if (k >= d.n_tiles) return;  // warp-uniform
-  int32_t* dsc = desc_s[w];
+__device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams& p, int64_t k,
+                                          int32_t* dsc, int lane) {
   if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
   if (p.prefetch > 0 && k + p.prefetch < d.n_tiles && lane < kQ) {
     const int64_t tp = __ldg(&d.launch[k + p.prefetch].tile);
@@ -465,6 +461,16 @@ __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK
   __syncwarp();
   const int64_t x = (int64_t)dsc[19] * kTile + lane;
   if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p, d.err);
+}
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK_MINB)
+    k_bulk(const DevLattice d, const StepParams p) {
+  __shared__ __align__(16) int32_t desc_s[kBulkWarps][20];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k = d.n_boundary + (int64_t)blockIdx.x * kBulkWarps + w;
+  if (k >= d.n_tiles) return;  // warp-uniform
+  bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
 }
 
 #ifndef LBM_BULK2_MINB
@@ -608,25 +614,25 @@ __global__ void __launch_bounds__(kBulkWarps * 32, LBM_BULK2_MINB)
   });
 }
 
+#ifndef LBM_MIX_MINB
+#define LBM_MIX_MINB 8
+#endif
+#ifndef LBM_STEP_MIXED
+#define LBM_STEP_MIXED 0
+#endif
 #ifndef LBM_BOUNDARY_MINB
 #define LBM_BOUNDARY_MINB 8
 #endif
+// Boundary tile at launch position k (whole warp); st, bar: the warp's
+// staging area and mbarrier; dsc: its 20-word descriptor area.
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_BOUNDARY_MINB)
-    k_boundary(const DevLattice d, const StepParams p) {
-  __shared__ __align__(128) unsigned char stage[kBoundaryWarps][kStBytes];
-  __shared__ __align__(16) int32_t desc_s[kBoundaryWarps][20];
-  __shared__ uint64_t bars[kBoundaryWarps];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t k = (int64_t)blockIdx.x * kBoundaryWarps + w;
-  if (k >= d.n_boundary) return;  // warp-uniform
-  int32_t* dsc = desc_s[w];
+__device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepParams& p, int64_t k,
+                                              int32_t* dsc, unsigned char* st, uint64_t* bar,
+                                              int lane) {
   if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
   __syncwarp();
   const uint32_t tmask = (uint32_t)dsc[18];
   const int64_t x = (int64_t)dsc[19] * kTile + lane;
-  unsigned char* st = stage[w];
-  uint64_t* bar = &bars[w];
   const int64_t slot0 = k * kTile;  // boundary tiles lead the launch order
   const bool irr = tmask & kIrregular;
   if (lane == 0) mbar_init(bar, 1);
@@ -664,6 +670,41 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
   if (!(smask & kValid)) return;
   if (irr) boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, true, nbr_s, lane, g);
   boundary_update<S, ODD>(d, p, P, x, dsc, irr, smask, st, lane, slot0 + lane, g);
+}
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_BOUNDARY_MINB)
+    k_boundary(const DevLattice d, const StepParams p) {
+  __shared__ __align__(128) unsigned char stage[kBoundaryWarps][kStBytes];
+  __shared__ __align__(16) int32_t desc_s[kBoundaryWarps][20];
+  __shared__ uint64_t bars[kBoundaryWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k = (int64_t)blockIdx.x * kBoundaryWarps + w;
+  if (k >= d.n_boundary) return;  // warp-uniform
+  boundary_tile<S, ODD>(d, p, k, desc_s[w], stage[w], &bars[w], lane);
+}
+
+// Single-launch step: CTA c is a boundary CTA or a bulk CTA, the boundary CTAs
+// spread evenly over the grid so that their latency-bound work runs beside
+// bandwidth-bound bulk CTAs.  Both roles use kMixWarps tiles per CTA.
+constexpr int kMixWarps = 4;
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kMixWarps * 32, sizeof(S) == 8 ? 4 : LBM_MIX_MINB)
+    k_step_mixed(const DevLattice d, const StepParams p, int64_t nb_ctas, int64_t total_ctas) {
+  __shared__ __align__(128) unsigned char stage[kMixWarps][kStBytes];
+  __shared__ __align__(16) int32_t desc_s[kMixWarps][20];
+  __shared__ uint64_t bars[kMixWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = blockIdx.x;
+  const int64_t before = c * nb_ctas / total_ctas;        // boundary CTAs before c
+  const bool bnd = (c + 1) * nb_ctas / total_ctas > before;
+  if (bnd) {
+    const int64_t k = before * kMixWarps + w;
+    if (k < d.n_boundary) boundary_tile<S, ODD>(d, p, k, desc_s[w], stage[w], &bars[w], lane);
+  } else {
+    const int64_t k = d.n_boundary + (c - before) * kMixWarps + w;
+    if (k < d.n_tiles) bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
+  }
 }
 
 // ------------------------------------------------ state conversion kernels
@@ -862,6 +903,22 @@ __global__ void k_wss(const DevLattice d, int odd, double tau, const int64_t* si
 template <class S>
 int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void* const* ev) {
   cudaStream_t m = (cudaStream_t)ss.main, side = (cudaStream_t)ss.side;
+#if LBM_STEP_MIXED
+  {
+    const int64_t nb = (d.n_boundary + kMixWarps - 1) / kMixWarps;
+    const int64_t nu = (d.n_tiles - d.n_boundary + kMixWarps - 1) / kMixWarps;
+    const int64_t total = nb + nu;
+    if (ev) cudaEventRecord((cudaEvent_t)ev[0], m);
+    if (total) {
+      if (p.step & 1) k_step_mixed<S, true><<<(unsigned)total, kMixWarps * 32, 0, m>>>(d, p, nb, total);
+      else k_step_mixed<S, false><<<(unsigned)total, kMixWarps * 32, 0, m>>>(d, p, nb, total);
+    }
+    if (ev) cudaEventRecord((cudaEvent_t)ev[1], m);
+    if (ev) cudaEventRecord((cudaEvent_t)ev[2], m);
+    (void)side;
+    return (int)cudaGetLastError();
+  }
+#endif
   const unsigned nbnd = (unsigned)((d.n_boundary + kBoundaryWarps - 1) / kBoundaryWarps);
   const int64_t nbulk_tiles = d.n_tiles - d.n_boundary;
   // FP32-compute paths: two tiles per warp (packed f32x2 collision)
