@@ -237,6 +237,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   lbm::TileDesc* td = dev_alloc<lbm::TileDesc>(c, L.tiles.size());
   lbm::LaunchDesc* to = dev_alloc<lbm::LaunchDesc>(c, L.launch.size());
   uint32_t* sm = dev_alloc<uint32_t>(c, S);
+  uint32_t* sio = dev_alloc<uint32_t>(c, S);
   int32_t* sn = dev_alloc<int32_t>(c, 18 * S);
   double* sp = dev_alloc<double>(c, 3 * S);
   double* sF = dev_alloc<double>(c, S);
@@ -249,7 +250,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   c->iolet_sites = dev_alloc<int64_t>(c, L.iolet_sites.size());
   c->partial = dev_alloc<double>(c, lbm::reduce_partials());
   c->red_out = dev_alloc<double>(c, 1 + n_iolets);
-  if (!d.pop || !td || !to || !sm || !sn || !sp || !sF || !sK || !sdE || !sUw ||
+  if (!d.pop || !td || !to || !sm || !sio || !sn || !sp || !sF || !sK || !sdE || !sUw ||
       !io || !err || !c->iolet_off || !c->iolet_sites || !c->partial || !c->red_out) {
     g_build_err = "device allocation failed";
     lbm_destroy(c);
@@ -258,6 +259,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   d.tiles = td;
   d.launch = to;
   d.slot_mask = sm;
+  d.slot_io = sio;
   d.slot_nbr = sn;
   d.slot_prof = sp;
   d.slot_F = sF;
@@ -286,6 +288,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   chk(h2d(c, td, L.tiles.data(), L.tiles.size()));
   chk(h2d(c, to, L.launch.data(), L.launch.size()));
   chk(h2d(c, sm, L.slot_mask.data(), S));
+  chk(h2d(c, sio, L.slot_io.data(), S));
   chk(h2d(c, sn, L.slot_nbr.data(), 18 * S));
   chk(h2d(c, sp, L.slot_prof.data(), 3 * S));
   chk(h2d(c, io, hio.data(), hio.size()));

@@ -250,22 +250,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 //     neighbour offsets, lean enough in registers to keep many warps resident,
 //     and an L2 prefetch (cp.async.bulk.prefetch) of the populations of the
 //     tile `prefetch` positions ahead;
-//   k_boundary over the boundary tiles: lane 0 stages the tile's per-site link
-//     data (link masks; F and kappa if a wall link is present; the inlet
-//     profile if an inlet link is present; on odd steps of an irregular tile
-//     the per-site neighbour table) into the warp's shared-memory area with
-//     cp.async.bulk copies that complete on the warp's mbarrier, then every
-//     lane applies the collision and, for each link leaving the fluid, the
+//   k_boundary over the boundary tiles: every lane reads its site's link
+//     masks (which links leave the fluid, which of those are iolet links, the
+//     iolet id), F, kappa and inlet profile in the same round trip as the
+//     tile descriptor; on odd steps of an irregular tile, lane 0 stages the
+//     tile's per-site neighbour table into the warp's shared memory with
+//     cp.async.bulk copies completing on the warp's mbarrier; then every lane
+//     applies the collision and, for each link leaving the fluid, the
 //     boundary rule.
-
-// Per-warp staging area, every block 16-byte aligned.
-constexpr int kStMask = 0;               // 32 x u32
-constexpr int kStF = kStMask + 128;      // 32 x f64
-constexpr int kStK = kStF + 256;         // 32 x f64
-constexpr int kStProf = kStK + 256;      // 3 x 32 x f64
-constexpr int kStNbr = kStProf + 768;    // 18 x 32 x i32
-constexpr int kStBytes = kStNbr + 2304;  // 3712
-static_assert(kStBytes % 16 == 0, "staging blocks must stay 16-byte aligned");
 
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -326,24 +318,34 @@ __device__ __forceinline__ void boundary_load(const S* P, int64_t np, int64_t x,
   });
 }
 
+// Collision, boundary rule and stores of a boundary site with pre-collision
+// populations g.  smask, iom: the site's link masks; Fw, Kw: its wall
+// parameters; pr0..pr2: its inlet profile (p0, ps, pc); nbr_s: the staged
+// per-site neighbour rows (irregular tiles on odd steps).
 template <class S, bool ODD>
 __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepParams& p, S* P,
                                                 int64_t x, const int32_t* dsc, bool irr,
-                                                uint32_t smask, const unsigned char* st, int lane,
-                                                int64_t slot, typename Codec<S>::C (&g)[kQ]) {
+                                                uint32_t smask, uint32_t iom, double Fw, double Kw,
+                                                double pr0, double pr1, double pr2,
+                                                const int32_t* nbr_s, int lane, int64_t slot,
+                                                typename Codec<S>::C (&g)[kQ]) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
   const int64_t np = d.npad;
-  const int32_t* nbr_s = reinterpret_cast<const int32_t*>(st + kStNbr);
   // neighbour index of a fluid link i (odd steps)
   auto nb = [&](int i) -> int64_t {
     return irr ? (int64_t)nbr_s[(i - 1) * kTile + lane] : x + dsc[i - 1];
   };
-  // code of a non-fluid link i: -1 wall, -2-k iolet k
+  // code of a non-fluid link i: -1 wall, -2-k iolet k.  A site that links into
+  // one iolet at most is described by its masks; otherwise the neighbour
+  // table holds the code.
+  const int32_t io_code = -2 - (int32_t)((smask & kInletBits) >> kInletShift);
   auto nfc = [&](int i) -> int32_t {
-    if (!irr) return dsc[i - 1];
-    if constexpr (ODD) return nbr_s[(i - 1) * kTile + lane];
-    else return __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
+    if (smask & kMultiIolet) {
+      if (ODD && irr) return nbr_s[(i - 1) * kTile + lane];
+      return __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
+    }
+    return ((iom >> i) & 1u) ? io_code : -1;
   };
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
@@ -356,14 +358,12 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   // scales an FP32 velocity on the FP32 paths).
   C uwx = C(0), uwy = C(0), uwz = C(0);
   if ((smask & kHasWall) && p.elastic) {
-    const double* F_s = reinterpret_cast<const double*>(st + kStF);
-    const double* K_s = reinterpret_cast<const double*>(st + kStK);
     const double pr = ((double)m.rho - p.rho0) * (1.0 / 3.0);
-    const double dE = K_s[lane] * (pr > 0.0 ? pr : 0.0);
+    const double dE = Kw * (pr > 0.0 ? pr : 0.0);
     const double dr = 1.0 + dE;
     C sc;
-    if constexpr (std::is_same<C, double>::value) sc = (F_s[lane] + dr - 1.0) / dr;
-    else sc = C(F_s[lane] + dE) * recip(C(dr));
+    if constexpr (std::is_same<C, double>::value) sc = (Fw + dr - 1.0) / dr;
+    else sc = C(Fw + dE) * recip(C(dr));
     uwx = sc * m.ux;
     uwy = sc * m.uy;
     uwz = sc * m.uz;
@@ -378,10 +378,9 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   // Inlet velocity (Sec. 3): u_in = a (u_mean p0 + u_amp (ps sin th + pc cos th)).
   C uix = C(0), uiy = C(0), uiz = C(0);
   if (smask & kHasInlet) {
-    const double* prof = reinterpret_cast<const double*>(st + kStProf);
     const int k = (int)((smask & kInletBits) >> kInletShift);
     const IoletDev& io = d.iolets[k];
-    double gval = io.u_mean * prof[lane];
+    double gval = io.u_mean * pr0;
     if (!io.steady) {
       // time factors u_amp sin(th), u_amp cos(th) of this step, from the host
       // for the first kMaxTimedInlets iolets, else evaluated here
@@ -396,7 +395,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
         as = io.u_amp * sn;
         ac = io.u_amp * cs;
       }
-      gval += prof[kTile + lane] * as + prof[2 * kTile + lane] * ac;
+      gval += pr1 * as + pr2 * ac;
     }
     uix = C(gval * io.axis[0]);
     uiy = C(gval * io.axis[1]);
@@ -623,59 +622,67 @@ __global__ void __launch_bounds__(kBulkWarps * 32, LBM_BULK2_MINB)
 #ifndef LBM_BOUNDARY_MINB
 #define LBM_BOUNDARY_MINB 8
 #endif
-// Boundary tile at launch position k (whole warp); st, bar: the warp's
-// staging area and mbarrier; dsc: its 20-word descriptor area.
+// Boundary tile at launch position k (whole warp); nbr_s, bar: the warp's
+// staging area (18 rows of per-site neighbours) and mbarrier; dsc: its
+// 20-word descriptor area.
 template <class S, bool ODD>
 __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepParams& p, int64_t k,
-                                              int32_t* dsc, unsigned char* st, uint64_t* bar,
+                                              int32_t* dsc, int32_t* nbr_s, uint64_t* bar,
                                               int lane) {
+  using C = typename Codec<S>::C;
+  const int64_t slot = k * kTile + lane;  // boundary tiles lead the launch order
+  // per-site data and the descriptor, all in one round trip
+  const uint32_t smask = __ldg(d.slot_mask + slot);
+  const uint32_t iom = __ldg(d.slot_io + slot);
   if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
   __syncwarp();
   const uint32_t tmask = (uint32_t)dsc[18];
-  const int64_t x = (int64_t)dsc[19] * kTile + lane;
-  const int64_t slot0 = k * kTile;  // boundary tiles lead the launch order
   const bool irr = tmask & kIrregular;
-  if (lane == 0) mbar_init(bar, 1);
-  __syncwarp();
-  if (lane == 0) {
-    const int64_t ss = d.slot_stride;
-    const bool wall = tmask & kHasWall, inl = tmask & kHasInlet, nbr = ODD && irr;
-    mbar_expect_tx(bar, 128u + (wall ? 512u : 0u) + (inl ? 768u : 0u) + (nbr ? 2304u : 0u));
-    bulk_g2s(st + kStMask, d.slot_mask + slot0, 128, bar);
-    if (wall) {
-      bulk_g2s(st + kStF, d.slot_F + slot0, 256, bar);
-      bulk_g2s(st + kStK, d.slot_kappa + slot0, 256, bar);
-    }
-    if (inl)
-      for (int c = 0; c < 3; ++c)
-        bulk_g2s(st + kStProf + 256 * c, d.slot_prof + c * ss + slot0, 256, bar);
-    if (nbr)
+  const int64_t x = (int64_t)dsc[19] * kTile + lane;
+  // odd steps of an irregular tile: stage the per-site neighbour rows
+  // (cp.async.bulk into shared memory, completing on the warp's mbarrier)
+  const bool stage = ODD && irr;
+  if (stage) {
+    if (lane == 0) mbar_init(bar, 1);
+    __syncwarp();
+    if (lane == 0) {
+      mbar_expect_tx(bar, 18u * kTile * 4u);
       for (int i = 0; i < 18; ++i)
-        bulk_g2s(st + kStNbr + 128 * i, d.slot_nbr + i * ss + slot0, 128, bar);
+        bulk_g2s(nbr_s + i * kTile, d.slot_nbr + i * d.slot_stride + k * kTile, kTile * 4, bar);
+    }
   }
-  // A uniform tile's links are the same in every lane: its populations can be
-  // read while the staging copies are in flight.
-  using C = typename Codec<S>::C;
+  const bool valid = smask & kValid;
+  double Fw = 0.0, Kw = 0.0, pr0 = 0.0, pr1 = 0.0, pr2 = 0.0;
+  if (valid && (smask & kHasWall)) {
+    Fw = __ldg(d.slot_F + slot);
+    Kw = __ldg(d.slot_kappa + slot);
+  }
+  if (valid && (smask & kHasInlet)) {
+    pr0 = __ldg(d.slot_prof + slot);
+    pr1 = __ldg(d.slot_prof + d.slot_stride + slot);
+    pr2 = __ldg(d.slot_prof + 2 * d.slot_stride + slot);
+  }
   C g[kQ];
   S* P = static_cast<S*>(d.pop);
-  const int32_t* nbr_s = reinterpret_cast<const int32_t*>(st + kStNbr);
-  if (!irr && x < d.n)
-    boundary_load<S, ODD>(P, d.npad, x, tmask & kDirBits, dsc, false, nbr_s, lane, g);
-  if (!mbar_wait_bounded(bar, 0)) {
-    if (lane == 0) atomicOr(d.err, kErrTimeout);
-    mbar_wait_bounded(bar, 0);  // a second bounded chance for copies still in flight
-    return;
+  if (!stage && valid)
+    boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g);
+  if (stage) {
+    if (!mbar_wait_bounded(bar, 0)) {
+      if (lane == 0) atomicOr(d.err, kErrTimeout);
+      mbar_wait_bounded(bar, 0);  // a second bounded chance for copies still in flight
+      return;
+    }
+    if (valid) boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, true, nbr_s, lane, g);
   }
-  const uint32_t smask = reinterpret_cast<const uint32_t*>(st + kStMask)[lane];
-  if (!(smask & kValid)) return;
-  if (irr) boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, true, nbr_s, lane, g);
-  boundary_update<S, ODD>(d, p, P, x, dsc, irr, smask, st, lane, slot0 + lane, g);
+  if (!valid) return;
+  boundary_update<S, ODD>(d, p, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s, lane,
+                          slot, g);
 }
 
 template <class S, bool ODD>
 __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_BOUNDARY_MINB)
     k_boundary(const DevLattice d, const StepParams p) {
-  __shared__ __align__(128) unsigned char stage[kBoundaryWarps][kStBytes];
+  __shared__ __align__(128) int32_t stage[kBoundaryWarps][18 * kTile];
   __shared__ __align__(16) int32_t desc_s[kBoundaryWarps][20];
   __shared__ uint64_t bars[kBoundaryWarps];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -691,7 +698,7 @@ constexpr int kMixWarps = 4;
 template <class S, bool ODD>
 __global__ void __launch_bounds__(kMixWarps * 32, sizeof(S) == 8 ? 4 : LBM_MIX_MINB)
     k_step_mixed(const DevLattice d, const StepParams p, int64_t nb_ctas, int64_t total_ctas) {
-  __shared__ __align__(128) unsigned char stage[kMixWarps][kStBytes];
+  __shared__ __align__(128) int32_t stage[kMixWarps][18 * kTile];
   __shared__ __align__(16) int32_t desc_s[kMixWarps][20];
   __shared__ uint64_t bars[kMixWarps];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;

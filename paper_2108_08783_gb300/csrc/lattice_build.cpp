@@ -8,8 +8,10 @@
 // of 32 sites is classified once:
 //   bulk      all 18 links fluid and, per direction, the same neighbour offset
 //             for every lane -> 18 offsets describe the whole tile;
-//   uniform   the same, except that some directions are non-fluid for every
-//             lane with the same code (a straight wall or iolet plane);
+//   coherent  some links leave the fluid, but in every direction the lanes
+//             whose link is fluid share one offset (a straight wall column,
+//             or a tile at an inlet/outlet plane) -> 18 offsets per tile plus
+//             per-site masks saying which links are wall or iolet links;
 //   irregular anything else -> per-site link codes.
 // Uniform and irregular tiles are the boundary tiles; their per-site data
 // (link masks, wall parameters, inlet profile) live in "slots", 32 per tile.
@@ -139,15 +141,15 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
       }
   site_of.clear();
   site_of.shrink_to_fit();
-  // ---- per-site summary: wall links, velocity-inlet id
-  std::vector<uint32_t> site_mask(n, 0);
+  // ---- per-site summary: link masks, iolet links, the site's iolet id
+  std::vector<uint32_t> site_mask(n, 0), site_io(n, 0);
   std::vector<int32_t> site_inlet(n, -1);
   L.wall_sites.clear();
   L.n_wall_links = 0;
   std::vector<std::vector<int64_t>> io_sites(n_iolets);
   for (int64_t s = 0; s < n; ++s) {
-    uint32_t m = 0;
-    int walls = 0;
+    uint32_t m = 0, io = 0;
+    int walls = 0, first_io = -1;
     const int32_t* nb = &L.nbr[(size_t)18 * s];
     for (int i = 1; i < kQ; ++i) {
       const int32_t c = nb[i - 1];
@@ -159,6 +161,9 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
         continue;
       }
       const int k = -2 - c;
+      io |= 1u << i;
+      if (first_io < 0) first_io = k;
+      else if (first_io != k) m |= kMultiIolet;
       if (io_sites[k].empty() || io_sites[k].back() != s) io_sites[k].push_back(s);
       if (iolets[k].kind == LBM_IOLET_VELOCITY) {
         if (site_inlet[s] >= 0 && site_inlet[s] != k) {
@@ -168,10 +173,13 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
           return LBM_EINVAL;
         }
         site_inlet[s] = k;
-        m |= kHasInlet | ((uint32_t)k << kInletShift);
+        m |= kHasInlet;
       }
     }
+    const int id = site_inlet[s] >= 0 ? site_inlet[s] : first_io;
+    if (id >= 0) m |= (uint32_t)id << kInletShift;
     site_mask[s] = m;
+    site_io[s] = io;
     if (walls) L.wall_sites.push_back(s);
     L.n_wall_links += walls;
   }
@@ -192,36 +200,41 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     const int lanes = (int)std::min<int64_t>(kTile, n - x0);
     TileDesc& d = L.tiles[t];
     d.slot = -1;
-    bool uni = true;
-    uint32_t flags = 0;
-    for (int l = 0; l < lanes; ++l) flags |= site_mask[x0 + l] & (kHasWall | kHasInlet);
-    for (int i = 1; i < kQ && uni; ++i) {
-      const int32_t c0 = L.nbr[(size_t)18 * x0 + (i - 1)];
-      for (int l = 1; l < lanes; ++l) {
+    uint32_t flags = 0, nonfluid = 0;
+    for (int l = 0; l < lanes; ++l) {
+      flags |= site_mask[x0 + l] & (kHasWall | kHasInlet);
+      nonfluid |= site_mask[x0 + l] & kDirBits;
+    }
+    // coherent: in every direction, the lanes whose link is fluid share one offset
+    bool coherent = true;
+    for (int i = 1; i < kQ && coherent; ++i) {
+      bool have = false;
+      int64_t off = 0;
+      for (int l = 0; l < lanes; ++l) {
         const int32_t c = L.nbr[(size_t)18 * (x0 + l) + (i - 1)];
-        if ((c < 0) != (c0 < 0) || (c < 0 && c != c0) ||
-            (c >= 0 && (int64_t)c - (x0 + l) != (int64_t)c0 - x0)) {
-          uni = false;
+        if (c < 0) continue;
+        const int64_t o = (int64_t)c - (x0 + l);
+        if (!have) {
+          have = true;
+          off = o;
+        } else if (o != off) {
+          coherent = false;
           break;
         }
       }
-      if (c0 < 0) {
-        d.code[i - 1] = c0;
-        d.mask |= 1u << i;
-      } else {
-        d.code[i - 1] = (int32_t)((int64_t)c0 - x0);
-      }
+      d.code[i - 1] = (int32_t)off;
     }
-    if (uni && d.mask == 0) {
+    if (coherent && nonfluid == 0) {
       ++L.n_bulk;
       L.bulk_sites += lanes;
       continue;
     }
-    if (!uni) {
+    if (!coherent) {
       for (int i = 0; i < 18; ++i) d.code[i] = 0;
       d.mask = kIrregular;
       ++L.n_irregular;
     } else {
+      d.mask = nonfluid;
       ++L.n_uniform;
     }
     d.mask |= flags;
@@ -244,6 +257,7 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   const int64_t S = nb_tiles * kTile;
   L.n_slots = S;
   L.slot_mask.assign(S, 0);
+  L.slot_io.assign(S, 0);
   L.slot_nbr.assign((size_t)18 * S, 0);
   L.slot_prof.assign((size_t)3 * S, 0.0);
   const double nu = (tau - 0.5) / 3.0;  // Eq. (Viscosity), c_s^2 = 1/3
@@ -257,6 +271,7 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
       const int64_t x = x0 + l, m = (int64_t)d.slot + l;
       slot_of[x] = m;
       L.slot_mask[m] = site_mask[x] | kValid;
+      L.slot_io[m] = site_io[x];
       for (int i = 0; i < 18; ++i) L.slot_nbr[(size_t)i * S + m] = L.nbr[(size_t)18 * x + i];
       const int k = site_inlet[x];
       if (k < 0) continue;

@@ -22,12 +22,14 @@ constexpr int kWarpsPerCta = LBM_WARPS_PER_CTA;  // step kernel: tiles (warps) p
 // Flag bits shared by TileDesc::mask and the per-slot masks.  Bits 1..18 mark
 // the non-fluid directions (wall or iolet links).
 constexpr uint32_t kDirBits = 0x7FFFEu;
-constexpr int kInletShift = 20;           // slot masks: bits 20..27 = velocity-inlet id
-constexpr uint32_t kInletBits = 0xFFu << kInletShift;
-constexpr uint32_t kValid = 1u << 28;     // slot holds a site (slot masks only)
-constexpr uint32_t kHasInlet = 1u << 29;  // a velocity-inlet link is present
-constexpr uint32_t kHasWall = 1u << 30;   // a wall link is present
-constexpr uint32_t kIrregular = 1u << 31; // tile: links differ from lane to lane
+constexpr uint32_t kMultiIolet = 1u << 19; // site links into two or more iolets: the
+                                           // per-link codes of the neighbour table decide
+constexpr int kInletShift = 20;            // slot masks: bits 20..27 = iolet id (the
+constexpr uint32_t kInletBits = 0xFFu << kInletShift;  // velocity inlet if any)
+constexpr uint32_t kValid = 1u << 28;      // slot holds a site (slot masks only)
+constexpr uint32_t kHasInlet = 1u << 29;   // a velocity-inlet link is present
+constexpr uint32_t kHasWall = 1u << 30;    // a wall link is present
+constexpr uint32_t kIrregular = 1u << 31;  // tile: fluid-link offsets differ between lanes
 
 // Sticky device error bits (ctx->err).
 constexpr int kErrUnstable = 1;
@@ -36,11 +38,12 @@ constexpr int kErrTimeout = 2;
 // One tile of 32 consecutive sites, 80 bytes, read by one warp (lanes 0..19).
 //  bulk tile: mask == 0 and code[i-1] = nbr(x, i) - x, the same for every
 //    lane; slot = -1.
-//  uniform boundary tile: as above, except that for the non-fluid directions
-//    (mask bits 1..18) code[i-1] is the common non-fluid code (-1 wall, -2-k
-//    iolet k); mask also carries kHasWall / kHasInlet; slot = first slot.
-//  irregular tile (kIrregular): links differ between lanes; codes unused and
-//    the per-site links live in the slot arrays.
+//  coherent boundary tile: some links leave the fluid (per-site masks in the
+//    slot arrays), and in every direction the lanes whose link is fluid share
+//    one offset code[i-1]; mask carries kHasWall / kHasInlet and the union of
+//    the non-fluid directions; slot = first slot.
+//  irregular tile (kIrregular): fluid-link offsets differ between lanes; the
+//    per-site neighbour table in the slot arrays gives every link.
 struct alignas(16) TileDesc {
   int32_t code[18];
   uint32_t mask;
@@ -81,10 +84,11 @@ struct HostLattice {
   int64_t n_tiles = 0;
   std::vector<TileDesc> tiles;
   std::vector<LaunchDesc> launch;   // boundary tiles (ascending), then bulk tiles
-  int64_t n_bulk = 0, n_uniform = 0, n_irregular = 0, bulk_sites = 0;
+  int64_t n_bulk = 0, n_uniform = 0, n_irregular = 0, bulk_sites = 0;  // uniform = coherent
   // boundary slots (32 per boundary tile, in tile order)
   int64_t n_slots = 0;
   std::vector<uint32_t> slot_mask;   // [n_slots]
+  std::vector<uint32_t> slot_io;     // [n_slots] bits 1..18: the non-fluid link is an iolet link
   std::vector<int32_t> slot_nbr;     // [18][n_slots] absolute neighbour or non-fluid code
   std::vector<double> slot_prof;     // [3][n_slots] inlet shape p0, ps, pc
   std::vector<int64_t> wall_slot;    // [n_wall_sites] slot of each wall site
@@ -108,6 +112,7 @@ struct DevLattice {
   const LaunchDesc* launch = nullptr;  // boundary tiles (ascending), then bulk tiles
   int64_t n_tiles = 0;
   const uint32_t* slot_mask = nullptr;
+  const uint32_t* slot_io = nullptr;
   const int32_t* slot_nbr = nullptr;   // [18][slot_stride]
   const double* slot_prof = nullptr;   // [3][slot_stride]
   const double* slot_F = nullptr;
