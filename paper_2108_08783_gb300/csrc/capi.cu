@@ -229,6 +229,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   d.npad = ((L.n + 64 + 127) / 128) * 128;
   d.n_tiles = L.n_tiles;
   d.n_boundary = L.n_uniform + L.n_irregular;
+  d.idx32 = (uint64_t)lbm::kQ * (uint64_t)d.npad < (1ull << 32) ? 1 : 0;
   d.slot_stride = L.n_slots;
   d.n_iolets = n_iolets;
   const size_t S = (size_t)L.n_slots;

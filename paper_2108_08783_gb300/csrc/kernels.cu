@@ -259,11 +259,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 //     applies the collision and, for each link leaving the fluid, the
 //     boundary rule.
 
-constexpr unsigned kFull = 0xffffffffu;
-
-// Branch-free update of a site whose 18 links are fluid.
-template <class S, bool ODD>
-__device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t* dsc,
+// Branch-free update of a site whose 18 links are fluid.  IX is the element
+// index type: 32-bit whenever 19 * npad < 2^32 (fewer address instructions),
+// else 64-bit.
+template <class S, bool ODD, class IX>
+__device__ __forceinline__ void bulk_update(S* P, IX np, IX x, const int32_t* dsc,
                                             const StepParams& p, int* err) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
@@ -271,8 +271,8 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
   unroll<kQ>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int o = dir_opp(j);
-    if constexpr (!ODD || j == 0) g[j] = Cd::ld(P + j * np + x, j);
-    else g[j] = Cd::ld(P + o * np + x + dsc[o - 1], j);
+    if constexpr (!ODD || j == 0) g[j] = Cd::ld(P + (IX)(j * np + x), j);
+    else g[j] = Cd::ld(P + (IX)(o * np + x + (IX)dsc[o - 1]), j);
   });
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(err, kErrUnstable);
@@ -283,11 +283,11 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
     const C sa = g[a] + omega * (geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[a]);
     const C sb = g[b] + omega * (geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[b]);
     if constexpr (ODD) {
-      Cd::st(P + a * np + x + dsc[a - 1], a, sa);
-      Cd::st(P + b * np + x + dsc[b - 1], b, sb);
+      Cd::st(P + (IX)(a * np + x + (IX)dsc[a - 1]), a, sa);
+      Cd::st(P + (IX)(b * np + x + (IX)dsc[b - 1]), b, sb);
     } else {
-      Cd::st(P + b * np + x, a, sa);
-      Cd::st(P + a * np + x, b, sb);
+      Cd::st(P + (IX)(b * np + x), a, sa);
+      Cd::st(P + (IX)(a * np + x), b, sb);
     }
   });
 }
@@ -318,40 +318,76 @@ __device__ __forceinline__ void boundary_load(const S* P, int64_t np, int64_t x,
   });
 }
 
+// D3Q19 vectors and weights for directions known only at run time (the
+// boundary rule loops over the links that leave the fluid).
+__constant__ float c_dir_f[4][kQ] = {
+    {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1},
+    {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1},
+    {1.f / 3, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 36, 1.f / 36,
+     1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36,
+     1.f / 36}};
+__constant__ double c_dir_d[4][kQ] = {
+    {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1},
+    {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1},
+    {1.0 / 3, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 36, 1.0 / 36,
+     1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36,
+     1.0 / 36}};
+
+template <class C>
+__device__ __forceinline__ C dir_tab(int row, int i) {
+  if constexpr (std::is_same<C, double>::value) return c_dir_d[row][i];
+  else return c_dir_f[row][i];
+}
+
+// Shifted equilibrium of direction j (run time), as geq<j>.
+template <class C>
+__device__ __forceinline__ C geq_rt(int j, C drho, C rho, C ux, C uy, C uz, C usq) {
+  const C cu = dir_tab<C>(0, j) * ux + dir_tab<C>(1, j) * uy + dir_tab<C>(2, j) * uz;
+  return dir_tab<C>(3, j) * (drho + rho * (C(3) * cu + C(4.5) * cu * cu - usq));
+}
+
 // Collision, boundary rule and stores of a boundary site with pre-collision
 // populations g.  smask, iom: the site's link masks; Fw, Kw: its wall
 // parameters; pr0..pr2: its inlet profile (p0, ps, pc); nbr_s: the staged
-// per-site neighbour rows (irregular tiles on odd steps).
+// per-site neighbour rows (irregular tiles on odd steps); gsm: the warp's
+// [19][32] shared-memory area where g is parked for the boundary rule.
 template <class S, bool ODD>
 __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepParams& p, S* P,
                                                 int64_t x, const int32_t* dsc, bool irr,
                                                 uint32_t smask, uint32_t iom, double Fw, double Kw,
                                                 double pr0, double pr1, double pr2,
                                                 const int32_t* nbr_s, int lane, int64_t slot,
-                                                typename Codec<S>::C (&g)[kQ]) {
+                                                typename Codec<S>::C (&g)[kQ],
+                                                typename Codec<S>::C* gsm) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
   const int64_t np = d.npad;
-  // neighbour index of a fluid link i (odd steps)
-  auto nb = [&](int i) -> int64_t {
-    return irr ? (int64_t)nbr_s[(i - 1) * kTile + lane] : x + dsc[i - 1];
-  };
-  // code of a non-fluid link i: -1 wall, -2-k iolet k.  A site that links into
-  // one iolet at most is described by its masks; otherwise the neighbour
-  // table holds the code.
-  const int32_t io_code = -2 - (int32_t)((smask & kInletBits) >> kInletShift);
-  auto nfc = [&](int i) -> int32_t {
-    if (smask & kMultiIolet) {
-      if (ODD && irr) return nbr_s[(i - 1) * kTile + lane];
-      return __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
-    }
-    return ((iom >> i) & 1u) ? io_code : -1;
-  };
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
   const C omega = C(p.omega);
   const C keep = C(1) - omega;  // (1 - 1/tau)
-
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    gsm[j * kTile + lane] = g[j];
+  });
+  // neighbour index of a fluid link i (odd steps)
+  auto nb = [&](int i) -> int64_t {
+    return irr ? (int64_t)nbr_s[(i - 1) * kTile + lane] : x + dsc[i - 1];
+  };
+  // Rest population and the links that stay in the fluid: stream f*.
+  Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
+  unroll<kQ - 1>([&](auto I0) {
+    constexpr int i = decltype(I0)::value + 1;
+    if (!((smask >> i) & 1u)) {
+      const C si = g[i] + omega * (geq<i, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[i]);
+      if constexpr (ODD) Cd::st(P + i * np + nb(i), i, si);
+      else Cd::st(P + dir_opp(i) * np + x, i, si);
+    }
+  });
+  uint32_t nf = smask & kDirBits;
+  if (!nf) return;
   // Elastic wall velocity (Sec. 2.3-2.4): the tube-law expansion dE and the
   // distance dr = dx + dE in FP64; the ratio U_w/u_f = (F + dr - dx)/dr in the
   // compute type (FP64 throughput is low on this GPU and the ratio only
@@ -382,8 +418,8 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
     const IoletDev& io = d.iolets[k];
     double gval = io.u_mean * pr0;
     if (!io.steady) {
-      // time factors u_amp sin(th), u_amp cos(th) of this step, from the host
-      // for the first kMaxTimedInlets iolets, else evaluated here
+      // u_amp sin(th), u_amp cos(th) of this step: from the host for the
+      // first kMaxTimedInlets iolets, else evaluated here
       double as, ac;
       if (k < kMaxTimedInlets) {
         as = p.inlet_sin[k];
@@ -401,44 +437,42 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
     uiy = C(gval * io.axis[1]);
     uiz = C(gval * io.axis[2]);
   }
-  const C uwsq = C(1.5) * (uwx * uwx + uwy * uwy + uwz * uwz);
-  const C uisq = C(1.5) * (uix * uix + uiy * uiy + uiz * uiz);
-
-  // Boundary population for direction J when the opposite link leaves the
-  // fluid through `c`: bounce-back (sopp = f*_opp(J)) or the GZS form
-  // f^eq_J(rho_b, u_b) + (1 - 1/tau) f^neq_J.
-  auto bc = [&](auto Jc, int32_t c, C sopp, C fneqJ) -> C {
-    constexpr int J = decltype(Jc)::value;
-    if (c == -1) {
-      if (!p.elastic) return sopp;
-      return geq<J, C>(m.drho, m.rho, uwx, uwy, uwz, uwsq) + keep * fneqJ;
-    }
-    const IoletDev& io = d.iolets[-2 - c];
-    if (io.kind == LBM_IOLET_VELOCITY)
-      return geq<J, C>(m.drho, m.rho, uix, uiy, uiz, uisq) + keep * fneqJ;
-    return geq<J, C>(C(io.rho - 1.0), C(io.rho), m.ux, m.uy, m.uz, m.usq) + keep * fneqJ;
-  };
-
-  Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
-  unroll<9>([&](auto Pi) {
-    constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
-    const C na = g[a] - geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
-    const C nbq = g[b] - geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
-    const C sa = g[a] - omega * na;
-    const C sb = g[b] - omega * nbq;
-    if (!((smask >> a) & 1u)) {
-      if constexpr (ODD) Cd::st(P + a * np + nb(a), a, sa);
-      else Cd::st(P + b * np + x, a, sa);
+  // Links that leave the fluid: the population of direction j = opp(i) that
+  // the site receives at the next step is rebuilt here and written to its own
+  // slot (x, j) - half-way bounce-back f*_i, or the GZS form
+  // f^eq_j(rho_b, u_b) + (1 - 1/tau) f^neq_j with (rho_b, u_b) = (rho, U_w) at a
+  // wall, (rho, u_in) at a velocity inlet, (rho_out, u) at a density outlet.
+  const int32_t io_code = -2 - (int32_t)((smask & kInletBits) >> kInletShift);
+  while (nf) {
+    const int i = __ffs(nf) - 1;
+    nf &= nf - 1;
+    const int j = dir_opp(i);
+    int32_t c;
+    if (smask & kMultiIolet)
+      c = (ODD && irr) ? nbr_s[(i - 1) * kTile + lane]
+                       : __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
+    else
+      c = ((iom >> i) & 1u) ? io_code : -1;
+    C val;
+    if (c == -1 && !p.elastic) {
+      const C gi = gsm[i * kTile + lane];
+      val = gi + omega * (geq_rt<C>(i, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - gi);
     } else {
-      Cd::st(P + b * np + x, b, bc(std::integral_constant<int, b>{}, nfc(a), sa, nbq));
+      const C fneq = gsm[j * kTile + lane] - geq_rt<C>(j, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
+      C e;
+      if (c == -1) {
+        e = geq_rt<C>(j, m.drho, m.rho, uwx, uwy, uwz, C(1.5) * (uwx * uwx + uwy * uwy + uwz * uwz));
+      } else {
+        const IoletDev& io = d.iolets[-2 - c];
+        if (io.kind == LBM_IOLET_VELOCITY)
+          e = geq_rt<C>(j, m.drho, m.rho, uix, uiy, uiz, C(1.5) * (uix * uix + uiy * uiy + uiz * uiz));
+        else
+          e = geq_rt<C>(j, C(io.rho - 1.0), C(io.rho), m.ux, m.uy, m.uz, m.usq);
+      }
+      val = e + keep * fneq;
     }
-    if (!((smask >> b) & 1u)) {
-      if constexpr (ODD) Cd::st(P + b * np + nb(b), b, sb);
-      else Cd::st(P + a * np + x, b, sb);
-    } else {
-      Cd::st(P + a * np + x, a, bc(std::integral_constant<int, a>{}, nfc(b), sb, na));
-    }
-  });
+    Cd::st(P + j * np + x, j, val);
+  }
 }
 
 #ifndef LBM_BULK_MINB
@@ -448,7 +482,7 @@ constexpr int kBulkWarps = 8;      // k_bulk: tiles (warps) per CTA
 constexpr int kBoundaryWarps = 4;  // k_boundary: tiles (warps) per CTA
 
 // Bulk tile at launch position k (whole warp); dsc: the warp's 20-word area.
-template <class S, bool ODD>
+template <class S, bool ODD, class IX>
 __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams& p, int64_t k,
                                           int32_t* dsc, int lane) {
   if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
@@ -459,166 +493,20 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
   }
   __syncwarp();
   const int64_t x = (int64_t)dsc[19] * kTile + lane;
-  if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p, d.err);
+  if (x >= d.n) return;
+  bulk_update<S, ODD, IX>(static_cast<S*>(d.pop), (IX)d.npad, (IX)x, dsc, p, d.err);
 }
 
-template <class S, bool ODD>
+template <class S, bool ODD, class IX>
 __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK_MINB)
     k_bulk(const DevLattice d, const StepParams p) {
   __shared__ __align__(16) int32_t desc_s[kBulkWarps][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k = d.n_boundary + (int64_t)blockIdx.x * kBulkWarps + w;
   if (k >= d.n_tiles) return;  // warp-uniform
-  bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
+  bulk_tile<S, ODD, IX>(d, p, k, desc_s[w], lane);
 }
 
-#ifndef LBM_BULK2_MINB
-#define LBM_BULK2_MINB 3
-#endif
-#ifndef LBM_BULK_SITES
-#define LBM_BULK_SITES 1
-#endif
-// ------------------------------------------------- packed two-site bulk path
-//
-// On the FP32-compute paths each thread of k_bulk2 updates the same lane of two
-// bulk tiles at once, holding the pair of sites in float2 registers, so the
-// collision runs on Blackwell's packed f32x2 add/mul/fma (one instruction per
-// two sites).  Loads and stores stay per site (the two sites are 32 tiles
-// apart in memory at most, never adjacent).
-
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// a - b as one fused operation: b * (-1) + a, rounded once
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
-
-// c . u of the first direction of pair P (directions 2P-1, 2P), P = 1..9.
-template <int P>
-__device__ __forceinline__ float2 dpair(float2 ux, float2 uy, float2 uz) {
-  if constexpr (P == 1) return ux;
-  else if constexpr (P == 2) return uy;
-  else if constexpr (P == 3) return uz;
-  else if constexpr (P == 4) return add2(ux, uy);
-  else if constexpr (P == 5) return sub2(ux, uy);
-  else if constexpr (P == 6) return add2(ux, uz);
-  else if constexpr (P == 7) return sub2(ux, uz);
-  else if constexpr (P == 8) return add2(uy, uz);
-  else return sub2(uy, uz);
-}
-
-template <class S, bool ODD>
-__global__ void __launch_bounds__(kBulkWarps * 32, LBM_BULK2_MINB)
-    k_bulk2(const DevLattice d, const StepParams p) {
-  using Cd = Codec<S>;
-  __shared__ __align__(16) int32_t desc_s[kBulkWarps][2][20];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ka = d.n_boundary + 2 * ((int64_t)blockIdx.x * kBulkWarps + w);
-  if (ka >= d.n_tiles) return;  // warp-uniform
-  const bool two = ka + 1 < d.n_tiles;
-  int32_t* da = desc_s[w][0];
-  int32_t* db = desc_s[w][1];
-  if (lane < 20) {
-    da[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + ka) + lane);
-    db[lane] = two ? __ldg(reinterpret_cast<const int32_t*>(d.launch + ka + 1) + lane) : 0;
-  }
-  if (p.prefetch > 0 && lane < kQ) {
-    for (int q = 0; q < 2; ++q) {
-      const int64_t kp = ka + q + p.prefetch;
-      if (kp < d.n_tiles) {
-        const int64_t tp = __ldg(&d.launch[kp].tile);
-        bulk_prefetch_l2(static_cast<const S*>(d.pop) + lane * d.npad + tp * kTile,
-                         kTile * sizeof(S));
-      }
-    }
-  }
-  __syncwarp();
-  const int64_t xa = (int64_t)da[19] * kTile + lane;
-  const int64_t xb = (int64_t)db[19] * kTile + lane;
-  const bool va = xa < d.n, vb = two && xb < d.n;
-  S* P = static_cast<S*>(d.pop);
-  const int64_t np = d.npad;
-  float2 g[kQ];
-  unroll<kQ>([&](auto J) {
-    constexpr int j = decltype(J)::value;
-    constexpr int o = dir_opp(j);
-    int64_t ia, ib;
-    if constexpr (!ODD || j == 0) {
-      ia = j * np + xa;
-      ib = j * np + xb;
-    } else {
-      ia = o * np + xa + da[o - 1];
-      ib = o * np + xb + db[o - 1];
-    }
-    g[j].x = va ? Cd::ld(P + ia, j) : 0.f;
-    g[j].y = vb ? Cd::ld(P + ib, j) : 0.f;
-  });
-  // moments (Eqs. Density, Momentum)
-  const float2 a1 = sub2(g[1], g[2]), a3 = sub2(g[3], g[4]), a5 = sub2(g[5], g[6]);
-  const float2 a7 = sub2(g[7], g[8]), a9 = sub2(g[9], g[10]), a11 = sub2(g[11], g[12]);
-  const float2 a13 = sub2(g[13], g[14]), a15 = sub2(g[15], g[16]), a17 = sub2(g[17], g[18]);
-  const float2 drho =
-      add2(add2(add2(g[0], add2(g[1], g[2])), add2(add2(g[3], g[4]), add2(g[5], g[6]))),
-           add2(add2(add2(add2(g[7], g[8]), add2(g[9], g[10])),
-                     add2(add2(g[11], g[12]), add2(g[13], g[14]))),
-                add2(add2(g[15], g[16]), add2(g[17], g[18]))));
-  const float2 jx = add2(add2(add2(a1, a7), add2(a9, a11)), a13);
-  const float2 jy = add2(sub2(add2(a3, a7), sub2(a9, a15)), a17);
-  const float2 jz = sub2(sub2(add2(a5, a11), sub2(a13, a15)), a17);
-  const float2 rho = add2(f2(1.f), drho);
-  if (unstable(rho.x) || (vb && unstable(rho.y))) atomicOr(d.err, kErrUnstable);
-  const float2 inv = make_float2(recip(rho.x), vb ? recip(rho.y) : 0.f);
-  const float2 ux = mul2(jx, inv), uy = mul2(jy, inv), uz = mul2(jz, inv);
-  const float2 usq = mul2(f2(1.5f), fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
-  const float2 om = f2((float)p.omega);
-  // BGK relaxation (Eq. LBE_SRT) with the shifted equilibrium, pairwise:
-  //   s = w (drho + rho (4.5 d^2 - u.u 1.5)), a = 3 w rho d,
-  //   g^eq(2P-1) = s + a, g^eq(2P) = s - a.
-  const float2 r3w_ax = mul2(f2(3.f / 18.f), rho), r3w_dg = mul2(f2(3.f / 36.f), rho);
-  {
-    const float2 e0 = mul2(f2(1.f / 3.f), fma2(rho, sub2(f2(0.f), usq), drho));
-    const float2 s0 = fma2(om, sub2(e0, g[0]), g[0]);
-    if (va) Cd::st(P + xa, 0, s0.x);
-    if (vb) Cd::st(P + xb, 0, s0.y);
-  }
-  unroll<9>([&](auto Pi) {
-    constexpr int pr = decltype(Pi)::value + 1;
-    constexpr int a = 2 * pr - 1, b = a + 1;
-    const float2 wv = f2(pr <= 3 ? 1.f / 18.f : 1.f / 36.f);
-    const float2 r3w = pr <= 3 ? r3w_ax : r3w_dg;
-    const float2 dd = dpair<pr>(ux, uy, uz);
-    const float2 s = mul2(wv, fma2(rho, fma2(f2(4.5f), mul2(dd, dd), sub2(f2(0.f), usq)), drho));
-    const float2 an = mul2(r3w, dd);
-    const float2 sa = fma2(om, sub2(add2(s, an), g[a]), g[a]);
-    const float2 sb = fma2(om, sub2(sub2(s, an), g[b]), g[b]);
-    if constexpr (ODD) {
-      if (va) {
-        Cd::st(P + a * np + xa + da[a - 1], a, sa.x);
-        Cd::st(P + b * np + xa + da[b - 1], b, sb.x);
-      }
-      if (vb) {
-        Cd::st(P + a * np + xb + db[a - 1], a, sa.y);
-        Cd::st(P + b * np + xb + db[b - 1], b, sb.y);
-      }
-    } else {
-      if (va) {
-        Cd::st(P + b * np + xa, a, sa.x);
-        Cd::st(P + a * np + xa, b, sb.x);
-      }
-      if (vb) {
-        Cd::st(P + b * np + xb, a, sa.y);
-        Cd::st(P + a * np + xb, b, sb.y);
-      }
-    }
-  });
-}
-
-#ifndef LBM_MIX_MINB
-#define LBM_MIX_MINB 8
-#endif
-#ifndef LBM_STEP_MIXED
-#define LBM_STEP_MIXED 0
-#endif
 #ifndef LBM_BOUNDARY_MINB
 #define LBM_BOUNDARY_MINB 8
 #endif
@@ -628,7 +516,7 @@ __global__ void __launch_bounds__(kBulkWarps * 32, LBM_BULK2_MINB)
 template <class S, bool ODD>
 __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepParams& p, int64_t k,
                                               int32_t* dsc, int32_t* nbr_s, uint64_t* bar,
-                                              int lane) {
+                                              typename Codec<S>::C* gsm, int lane) {
   using C = typename Codec<S>::C;
   const int64_t slot = k * kTile + lane;  // boundary tiles lead the launch order
   // per-site data and the descriptor, all in one round trip
@@ -676,42 +564,21 @@ __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepPar
   }
   if (!valid) return;
   boundary_update<S, ODD>(d, p, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s, lane,
-                          slot, g);
+                          slot, g, gsm);
 }
 
 template <class S, bool ODD>
 __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_BOUNDARY_MINB)
     k_boundary(const DevLattice d, const StepParams p) {
+  using C = typename Codec<S>::C;
   __shared__ __align__(128) int32_t stage[kBoundaryWarps][18 * kTile];
+  __shared__ __align__(16) C gs[kBoundaryWarps][kQ * kTile];
   __shared__ __align__(16) int32_t desc_s[kBoundaryWarps][20];
   __shared__ uint64_t bars[kBoundaryWarps];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k = (int64_t)blockIdx.x * kBoundaryWarps + w;
   if (k >= d.n_boundary) return;  // warp-uniform
-  boundary_tile<S, ODD>(d, p, k, desc_s[w], stage[w], &bars[w], lane);
-}
-
-// Single-launch step: CTA c is a boundary CTA or a bulk CTA, the boundary CTAs
-// spread evenly over the grid so that their latency-bound work runs beside
-// bandwidth-bound bulk CTAs.  Both roles use kMixWarps tiles per CTA.
-constexpr int kMixWarps = 4;
-template <class S, bool ODD>
-__global__ void __launch_bounds__(kMixWarps * 32, sizeof(S) == 8 ? 4 : LBM_MIX_MINB)
-    k_step_mixed(const DevLattice d, const StepParams p, int64_t nb_ctas, int64_t total_ctas) {
-  __shared__ __align__(128) int32_t stage[kMixWarps][18 * kTile];
-  __shared__ __align__(16) int32_t desc_s[kMixWarps][20];
-  __shared__ uint64_t bars[kMixWarps];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t c = blockIdx.x;
-  const int64_t before = c * nb_ctas / total_ctas;        // boundary CTAs before c
-  const bool bnd = (c + 1) * nb_ctas / total_ctas > before;
-  if (bnd) {
-    const int64_t k = before * kMixWarps + w;
-    if (k < d.n_boundary) boundary_tile<S, ODD>(d, p, k, desc_s[w], stage[w], &bars[w], lane);
-  } else {
-    const int64_t k = d.n_boundary + (c - before) * kMixWarps + w;
-    if (k < d.n_tiles) bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
-  }
+  boundary_tile<S, ODD>(d, p, k, desc_s[w], stage[w], &bars[w], gs[w], lane);
 }
 
 // ------------------------------------------------ state conversion kernels
@@ -910,28 +777,10 @@ __global__ void k_wss(const DevLattice d, int odd, double tau, const int64_t* si
 template <class S>
 int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void* const* ev) {
   cudaStream_t m = (cudaStream_t)ss.main, side = (cudaStream_t)ss.side;
-#if LBM_STEP_MIXED
-  {
-    const int64_t nb = (d.n_boundary + kMixWarps - 1) / kMixWarps;
-    const int64_t nu = (d.n_tiles - d.n_boundary + kMixWarps - 1) / kMixWarps;
-    const int64_t total = nb + nu;
-    if (ev) cudaEventRecord((cudaEvent_t)ev[0], m);
-    if (total) {
-      if (p.step & 1) k_step_mixed<S, true><<<(unsigned)total, kMixWarps * 32, 0, m>>>(d, p, nb, total);
-      else k_step_mixed<S, false><<<(unsigned)total, kMixWarps * 32, 0, m>>>(d, p, nb, total);
-    }
-    if (ev) cudaEventRecord((cudaEvent_t)ev[1], m);
-    if (ev) cudaEventRecord((cudaEvent_t)ev[2], m);
-    (void)side;
-    return (int)cudaGetLastError();
-  }
-#endif
+
   const unsigned nbnd = (unsigned)((d.n_boundary + kBoundaryWarps - 1) / kBoundaryWarps);
   const int64_t nbulk_tiles = d.n_tiles - d.n_boundary;
-  // FP32-compute paths: two tiles per warp (packed f32x2 collision)
-  constexpr bool kTwo = !std::is_same<S, double>::value && LBM_BULK_SITES == 2;
-  const int64_t per_cta = kBulkWarps * (kTwo ? 2 : 1);
-  const unsigned nbulk = (unsigned)((nbulk_tiles + per_cta - 1) / per_cta);
+  const unsigned nbulk = (unsigned)((nbulk_tiles + kBulkWarps - 1) / kBulkWarps);
   const bool odd = p.step & 1;
   if (ev) cudaEventRecord((cudaEvent_t)ev[0], m);
   if (nbnd) {
@@ -941,12 +790,12 @@ int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void
     else k_boundary<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
   }
   if (nbulk) {
-    if constexpr (kTwo) {
-      if (odd) k_bulk2<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
-      else k_bulk2<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+    if (d.idx32) {
+      if (odd) k_bulk<S, true, uint32_t><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+      else k_bulk<S, false, uint32_t><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
     } else {
-      if (odd) k_bulk<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
-      else k_bulk<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+      if (odd) k_bulk<S, true, int64_t><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+      else k_bulk<S, false, int64_t><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
     }
   }
   if (ev) cudaEventRecord((cudaEvent_t)ev[1], m);

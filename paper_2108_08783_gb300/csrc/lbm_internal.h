@@ -124,6 +124,7 @@ struct DevLattice {
   int32_t n_iolets = 0;
   int* err = nullptr;
   int64_t n_boundary = 0;  // boundary tiles = leading entries of the launch order
+  int32_t idx32 = 0;       // 1: 19 * npad < 2^32, element indices fit 32 bits
 };
 
 // Iolets whose inlet time factors are evaluated on the host each step.
