@@ -229,7 +229,6 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   d.npad = ((L.n + 64 + 127) / 128) * 128;
   d.n_tiles = L.n_tiles;
   d.n_boundary = L.n_uniform + L.n_irregular;
-  d.idx32 = (uint64_t)lbm::kQ * (uint64_t)d.npad < (1ull << 32) ? 1 : 0;
   d.slot_stride = L.n_slots;
   d.n_iolets = n_iolets;
   const size_t S = (size_t)L.n_slots;
@@ -360,7 +359,7 @@ int lbm_set_wall_params(lbm_ctx* c, int32_t wall_model, double rho0, const doubl
     if (!std::isfinite(f) || !std::isfinite(k) || f < 0.0 || k < 0.0)
       return fail(c, LBM_EINVAL, "F and kappa must be finite and >= 0");
     hF[c->L.wall_slot[w]] = f;
-    hK[c->L.wall_slot[w]] = k;
+    hK[c->L.wall_slot[w]] = k / 3.0;  // the kernel applies kappa c_s^2 to (rho - rho0)
   }
   cudaError_t e = h2d(c, const_cast<double*>(c->d.slot_F), hF.data(), S);
   if (e == cudaSuccess) e = h2d(c, const_cast<double*>(c->d.slot_kappa), hK.data(), S);

@@ -259,11 +259,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 //     applies the collision and, for each link leaving the fluid, the
 //     boundary rule.
 
-// Branch-free update of a site whose 18 links are fluid.  IX is the element
-// index type: 32-bit whenever 19 * npad < 2^32 (fewer address instructions),
-// else 64-bit.
-template <class S, bool ODD, class IX>
-__device__ __forceinline__ void bulk_update(S* P, IX np, IX x, const int32_t* dsc,
+// Branch-free update of a site whose 18 links are fluid.
+template <class S, bool ODD>
+__device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t* dsc,
                                             const StepParams& p, int* err) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
@@ -271,8 +269,8 @@ __device__ __forceinline__ void bulk_update(S* P, IX np, IX x, const int32_t* ds
   unroll<kQ>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int o = dir_opp(j);
-    if constexpr (!ODD || j == 0) g[j] = Cd::ld(P + (IX)(j * np + x), j);
-    else g[j] = Cd::ld(P + (IX)(o * np + x + (IX)dsc[o - 1]), j);
+    if constexpr (!ODD || j == 0) g[j] = Cd::ld(P + j * np + x, j);
+    else g[j] = Cd::ld(P + o * np + x + dsc[o - 1], j);
   });
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(err, kErrUnstable);
@@ -283,11 +281,11 @@ __device__ __forceinline__ void bulk_update(S* P, IX np, IX x, const int32_t* ds
     const C sa = g[a] + omega * (geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[a]);
     const C sb = g[b] + omega * (geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[b]);
     if constexpr (ODD) {
-      Cd::st(P + (IX)(a * np + x + (IX)dsc[a - 1]), a, sa);
-      Cd::st(P + (IX)(b * np + x + (IX)dsc[b - 1]), b, sb);
+      Cd::st(P + a * np + x + dsc[a - 1], a, sa);
+      Cd::st(P + b * np + x + dsc[b - 1], b, sb);
     } else {
-      Cd::st(P + (IX)(b * np + x), a, sa);
-      Cd::st(P + (IX)(a * np + x), b, sb);
+      Cd::st(P + b * np + x, a, sa);
+      Cd::st(P + a * np + x, b, sb);
     }
   });
 }
@@ -394,18 +392,23 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   // scales an FP32 velocity on the FP32 paths).
   C uwx = C(0), uwy = C(0), uwz = C(0);
   if ((smask & kHasWall) && p.elastic) {
-    const double pr = ((double)m.rho - p.rho0) * (1.0 / 3.0);
-    const double dE = Kw * (pr > 0.0 ? pr : 0.0);
-    const double dr = 1.0 + dE;
+    // Kw holds kappa c_s^2 = kappa / 3, so dE = Kw max(0, rho - rho0)
+    const double dp = (double)m.rho - p.rho0;
+    const double dE = Kw * (dp > 0.0 ? dp : 0.0);
     C sc;
-    if constexpr (std::is_same<C, double>::value) sc = (Fw + dr - 1.0) / dr;
-    else sc = C(Fw + dE) * recip(C(dr));
+    if constexpr (std::is_same<C, double>::value) {
+      const double dr = 1.0 + dE;
+      sc = (Fw + dr - 1.0) / dr;
+    } else {
+      const float e = (float)dE;
+      sc = (float(Fw) + e) * recip(1.0f + e);
+    }
     uwx = sc * m.ux;
     uwy = sc * m.uy;
     uwz = sc * m.uz;
     if (p.write_state) {
       const int64_t ss = d.slot_stride;
-      d.slot_dE[slot] = dE;
+      d.slot_dE[slot] = dE;  // dE of this step; dr = 1 + dE
       d.slot_Uw[slot] = (double)uwx;
       d.slot_Uw[ss + slot] = (double)uwy;
       d.slot_Uw[2 * ss + slot] = (double)uwz;
@@ -482,7 +485,7 @@ constexpr int kBulkWarps = 8;      // k_bulk: tiles (warps) per CTA
 constexpr int kBoundaryWarps = 4;  // k_boundary: tiles (warps) per CTA
 
 // Bulk tile at launch position k (whole warp); dsc: the warp's 20-word area.
-template <class S, bool ODD, class IX>
+template <class S, bool ODD>
 __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams& p, int64_t k,
                                           int32_t* dsc, int lane) {
   if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
@@ -493,18 +496,17 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
   }
   __syncwarp();
   const int64_t x = (int64_t)dsc[19] * kTile + lane;
-  if (x >= d.n) return;
-  bulk_update<S, ODD, IX>(static_cast<S*>(d.pop), (IX)d.npad, (IX)x, dsc, p, d.err);
+  if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p, d.err);
 }
 
-template <class S, bool ODD, class IX>
+template <class S, bool ODD>
 __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK_MINB)
     k_bulk(const DevLattice d, const StepParams p) {
   __shared__ __align__(16) int32_t desc_s[kBulkWarps][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k = d.n_boundary + (int64_t)blockIdx.x * kBulkWarps + w;
   if (k >= d.n_tiles) return;  // warp-uniform
-  bulk_tile<S, ODD, IX>(d, p, k, desc_s[w], lane);
+  bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
 }
 
 #ifndef LBM_BOUNDARY_MINB
@@ -543,7 +545,7 @@ __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepPar
   double Fw = 0.0, Kw = 0.0, pr0 = 0.0, pr1 = 0.0, pr2 = 0.0;
   if (valid && (smask & kHasWall)) {
     Fw = __ldg(d.slot_F + slot);
-    Kw = __ldg(d.slot_kappa + slot);
+    Kw = __ldg(d.slot_kappa + slot);  // kappa / 3
   }
   if (valid && (smask & kHasInlet)) {
     pr0 = __ldg(d.slot_prof + slot);
@@ -790,13 +792,8 @@ int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void
     else k_boundary<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
   }
   if (nbulk) {
-    if (d.idx32) {
-      if (odd) k_bulk<S, true, uint32_t><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
-      else k_bulk<S, false, uint32_t><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
-    } else {
-      if (odd) k_bulk<S, true, int64_t><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
-      else k_bulk<S, false, int64_t><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
-    }
+    if (odd) k_bulk<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+    else k_bulk<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
   }
   if (ev) cudaEventRecord((cudaEvent_t)ev[1], m);
   if (nbnd) {

@@ -116,7 +116,7 @@ struct DevLattice {
   const int32_t* slot_nbr = nullptr;   // [18][slot_stride]
   const double* slot_prof = nullptr;   // [3][slot_stride]
   const double* slot_F = nullptr;
-  const double* slot_kappa = nullptr;
+  const double* slot_kappa = nullptr;  // kappa c_s^2 = kappa / 3 (per slot)
   double* slot_dE = nullptr;
   double* slot_Uw = nullptr;           // [3][slot_stride]
   int64_t slot_stride = 0;
@@ -124,7 +124,6 @@ struct DevLattice {
   int32_t n_iolets = 0;
   int* err = nullptr;
   int64_t n_boundary = 0;  // boundary tiles = leading entries of the launch order
-  int32_t idx32 = 0;       // 1: 19 * npad < 2^32, element indices fit 32 bits
 };
 
 // Iolets whose inlet time factors are evaluated on the host each step.
