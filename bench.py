@@ -19,7 +19,11 @@ needed between steps.
              duration on the main stream, against the measured HBM copy
              bandwidth; "step" gives the same for the whole step (both kernels);
   cpu_baseline  the FP64 CPU oracle on the same workload, a bounded number of
-             steps on all host cores.
+             steps on all host cores;
+  mixed_precision  every storage (FP64/FP32/FP16S/BF16S) run from rest on the
+             same workload: MLUPS, and the rel-L2 error of the wall shear
+             stress and of u against the FP64 path, with the speed-up over
+             FP32 of each storage that meets the WSS error budget.
 
 ``--impl reference`` times the oracle alone (the reference arm of this tier).
 Under torchrun every rank runs its own copy of the workload (independent
@@ -150,6 +154,44 @@ def cpu_oracle(geo, params, seconds=12.0, max_steps=200, min_steps=2):
         steps += 1
     dt = time.perf_counter() - t0
     return orc.n * steps / dt / 1e6, threads, steps, dt
+
+
+def precision_study(args, geo, params, steps, budget=5e-3):
+    """MLUPS and error of each storage against the FP64 path on the same workload
+    (all from rest, `steps` steps): rel-L2 of the wall shear stress at the wall
+    sites and of u.  The FP64 path matches the oracle to 1e-10 (tests)."""
+    import torch
+    import lbm_inputs as I
+    from paper_2108_08783_gb300 import Lattice
+    res, ref = {}, None
+    for st in ("f64", "f32", "f16s", "bf16s"):
+        lat = Lattice(geo.labels, geo.iolets, storage=st, tau=params["tau"])
+        lat.set_wall("elastic", rho0=params["rho0"], F=params["F"], kappa=params["kappa"])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(lat.stream)
+        lat.step(steps)
+        e1.record(lat.stream)
+        torch.cuda.synchronize()
+        lat.sync()
+        ms = e0.elapsed_time(e1)
+        ex = lat.export()
+        s = ex["wall_sites"]
+        wss = lat.wss(s, I.wall_normals(geo, ex["coords"][s]))
+        u = lat.moments()[1]
+        lat.close()
+        if ref is None:
+            ref = (wss, u)
+        res[st] = {"mlups": lat.n * steps / ms / 1e3,
+                   "wss_rel_l2": float(np.linalg.norm(wss - ref[0]) / np.linalg.norm(ref[0])),
+                   "u_rel_l2": float(np.linalg.norm(u - ref[1]) / np.linalg.norm(ref[1]))}
+    f32 = res["f32"]["mlups"]
+    for st in ("f32", "f16s", "bf16s"):
+        res[st]["speedup_vs_f32"] = res[st]["mlups"] / f32
+        res[st]["meets_budget"] = res[st]["wss_rel_l2"] <= budget
+    return {"steps": steps, "reference": "f64 storage (matches the FP64 oracle to 1e-10)",
+            "wss_budget": budget, **res}
 
 
 def dist_init():
@@ -290,6 +332,10 @@ def run_ours(args):
                "h2d_bytes_per_step": (rho_h.numel() + u_h.numel()) * 8 / k,
                "d2h_bytes_per_step": red.numel() * 8 + (rho_o.numel() + u_o.numel()) * 8 / k,
                "steps": k}
+    # ---------------------------------------------------------------- mixed precision
+    prec = None
+    if rank == 0 and not args.no_precision:
+        prec = precision_study(args, geo, params, args.precision_steps)
     # ---------------------------------------------------------------- CPU baseline
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -305,7 +351,7 @@ def run_ours(args):
             "config": {"workload": name, "sites": n, "storage": args.storage,
                        "wall": "elastic GZS", "l2": "populations (%.0f MB) exceed L2; no flush"
                        % (19 * s * n / 1e6), "parallelism": "replicas x%d" % ws},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": prec,
             "gpu_launches": int(n_bulk_l + n_bnd_l),
             "clocks": clk,
         }
@@ -333,6 +379,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--precision-steps", type=int, default=4000)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -6,5 +6,5 @@ seeded initial fields.  It contains none of the lattice Boltzmann method's
 arithmetic, so both the oracle and the product may import it.
 """
 from .geometry import (Geometry, Iolet, tube, duct, closed_box, random_labels, murray_tree,  # noqa: F401
-                       tube_ensemble)
+                       tube_ensemble, rest_radius, wall_normals)
 from .fields import random_fields, gather  # noqa: F401

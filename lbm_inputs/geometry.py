@@ -290,3 +290,33 @@ def tube_ensemble(seed=0, count=256, radius=(6.0, 24.0), length=(64, 512), stiff
     return [dict(radius=float(R[i]), length=int(L[i]), eh_r0=float(Eh[i]), period=float(T[i]),
                  tau=float(taus[i]), kappa=float((1 - sigma ** 2) * R[i] / Eh[i]))
             for i in range(count)]
+
+
+def wall_normals(geom, coords):
+    """Outward unit normals of the vessel surface nearest to the given node coordinates.
+
+    Tubes: the radial direction from the axis; trees: the radial direction from
+    the axis of the segment that owns the node (its axial component removed).
+    Used to evaluate wall shear stress at wall sites.
+    """
+    coords = np.asarray(coords, np.float64)
+    if "segments" not in geom.meta:
+        c = np.array(geom.meta["centre"], np.float64)
+        v = np.zeros_like(coords)
+        v[:, 0] = coords[:, 0] - c[0]
+        v[:, 1] = coords[:, 1] - c[1]
+    else:
+        ic = coords.astype(np.int64)
+        owner = geom.meta["segment_of_voxel"][ic[:, 0], ic[:, 1], ic[:, 2]]
+        lo = geom.meta["origin"]
+        v = np.zeros_like(coords)
+        for k in np.unique(owner):
+            if k == 255:
+                continue
+            p, d, L, r0, r1, lev = geom.meta["segments"][k]
+            m = owner == k
+            rel = coords[m] - (p - lo)
+            v[m] = rel - np.outer(rel @ d, d)
+    nrm = np.linalg.norm(v, axis=1)
+    nrm[nrm == 0] = 1.0
+    return v / nrm[:, None]

@@ -189,11 +189,13 @@ def test_config2_full_size_short_run(storage, tol):
 
 # ------------------------------------------------------------------ reduced precision
 
-@pytest.mark.parametrize("storage,bound", [("f16s", 2e-3), ("bf16s", 6e-2)])
-def test_shifted_half_storage_bound(storage, bound):
-    """Stated bound for 16-bit shifted storage after 1000 steps on config 1:
-    rel-L2 of (rho - 1) and of u against the FP64 oracle.  BF16 keeps 8
-    significant bits, so its bound is looser (measured 3.2e-2 on rho - 1)."""
+@pytest.mark.parametrize("storage,bound,wss_bound", [("f32", 1e-5, 2e-5), ("f16s", 2e-3, 5e-3),
+                                                     ("bf16s", 6e-2, 6e-2)])
+def test_shifted_storage_error_bounds(storage, bound, wss_bound):
+    """Stated bounds for each storage after 1000 steps on config 1 against the
+    FP64 oracle: rel-L2 of (rho - 1), of u and of the wall shear stress at the
+    wall sites.  BF16 keeps 8 significant bits, so its bounds are looser
+    (measured 3.2e-2 on rho - 1)."""
     geo = _config1()
     lat, orc = make_pair(geo, storage, tau=0.8, wall_model=1, F=0.85, kappa=12.0)
     lat.step(1000)
@@ -202,3 +204,26 @@ def test_shifted_half_storage_bound(storage, bound):
     ro, uo = orc.moments()
     assert rel_l2(rl - 1, ro - 1) < bound
     assert rel_l2(ul, uo) < bound
+    ex = lat.export()
+    s = ex["wall_sites"]
+    nrm = I.wall_normals(geo, ex["coords"][s])
+    assert rel_l2(lat.wss(s, nrm), orc.wss(s, nrm)) < wss_bound
+
+
+# ------------------------------------------------------------------ wall shear stress
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-5)])
+def test_wss_matches_oracle(storage, tol):
+    """WSS at the wall sites (deviatoric stress of f^neq, tangential traction
+    for the analytic outward normal) after 600 steps of the config-1 tube."""
+    geo = _config1()
+    lat, orc = make_pair(geo, storage, tau=0.8, wall_model=1, F=0.85, kappa=12.0)
+    lat.step(600)
+    orc.run(600)
+    ex = lat.export()
+    sites = ex["wall_sites"]
+    nrm = I.wall_normals(geo, ex["coords"][sites])
+    wl = lat.wss(sites, nrm)
+    wo = orc.wss(sites, nrm)
+    assert wo.max() > 1e-6  # a developed shear layer
+    assert rel_l2(wl, wo) <= 10 * tol

@@ -387,3 +387,47 @@ def test_f_ratio_limits():
     for alpha in (1.0, 3.0, 8.0):
         assert abs(A.f_ratio(alpha, 1e-9, 0.7) - 1.0) < 1e-6  # F -> 1 as dr -> 0
         assert abs(A.f_ratio(alpha, 0.05, 0.0) - 1.0) < 1e-15  # M = 0
+
+
+# ----------------------------------------------------------- wall shear stress
+
+def test_wss_matches_viscous_stress_of_duct_flow():
+    """The stress read from f^neq at a wall-adjacent node equals mu du/dn of
+    the textbook duct solution there (pins the -(1 - 1/(2 tau)) factor, the
+    second moment of f^neq and the tangential projection)."""
+    tau, n = 1.0, 16
+    nu = A.viscosity(tau)
+    L = 2 * n
+    G0 = 0.01 * nu / (0.0737 * n * n)
+    d = 1.5 * G0 * L
+    g = I.duct(n, n, L, rho_in=1 + d, rho_out=1 - d)
+    o = Oracle(g.labels, g.iolets, tau=tau, wall_model=0)
+    o.run(int(2.5 * n * n / nu))
+    rho, u = o.moments()
+    c = o.coords()
+    zm = L // 2 + 1
+    G = -(rho[c[:, 2] == zm + 1].mean() - rho[c[:, 2] == zm - 1].mean()) / 2.0 / 3.0
+    mu = rho[c[:, 2] == zm].mean() * nu
+    cx = (n + 1) / 2.0
+    sel = np.where((c[:, 2] == zm) & (c[:, 1] == 1) & (np.abs(c[:, 0] - cx) < n / 4))[0]
+    normals = np.tile([0.0, -1.0, 0.0], (sel.size, 1))
+    wss = o.wss(sel, normals)
+    h = 1e-4
+    xs, ys = c[sel, 0] - cx, c[sel, 1] - cx
+    dudy = (duct_velocity(xs, ys + h, n / 2, n / 2, G, mu)
+            - duct_velocity(xs, ys - h, n / 2, n / 2, G, mu)) / (2 * h)
+    np.testing.assert_allclose(wss, mu * np.abs(dudy), rtol=0.03)
+
+
+def test_rigid_wall_shear_exceeds_elastic():
+    """Sec. 3: the elastic wall lowers wall shear stress relative to bounce-back."""
+    g = I.tube(8, 64, u_mean=0.025)
+    out = {}
+    for wm in (0, 1):
+        o = Oracle(g.labels, g.iolets, tau=0.8, wall_model=wm, F=0.85, kappa=12.0)
+        o.run(600)
+        ex = o.export()
+        s = ex["wall_sites"]
+        out[wm] = o.wss(s, I.wall_normals(g, ex["coords"][s]))
+    assert out[0].mean() > 2 * out[1].mean()
+    assert np.mean(out[0] >= out[1]) > 0.9
