@@ -55,6 +55,14 @@ def workload(args):
         geo = I.tube(40, 1024, u_mean=0.03, u_amp=0.02, period=4000.0)
         params = dict(tau=0.6, F=0.85, kappa=0.75 * 40 / 0.5, rho0=1.0)
         name = "long pulsatile tube R=40 L=1024 (~5.15M sites), tau=0.6, Eh/r0=0.5"
+    elif args.config == "tree":
+        geo = I.murray_tree(seed=0, depth=6, root_radius=48.0)
+        geo.iolets[0].u_mean = 0.03
+        geo.iolets[0].u_amp = 0.02
+        geo.iolets[0].period = 4000.0
+        params = dict(tau=0.6, F=0.85, kappa=0.75 * 48.0 / 0.5, rho0=1.0)
+        name = ("seeded Murray tree depth 6, root R=48, 10% taper (%d sites), tau=0.6, Eh/r0=0.5"
+                % geo.n_fluid())
     elif args.config == "tube8":
         geo = I.tube(8, 64, u_mean=0.025)
         params = dict(tau=0.8, F=0.85, kappa=12.0, rho0=1.0)
@@ -374,7 +382,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES))
-    ap.add_argument("--config", default="tube40", choices=["tube40", "tube8"])
+    ap.add_argument("--config", default="tube40", choices=["tube40", "tree", "tube8"])
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")

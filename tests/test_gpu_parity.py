@@ -227,3 +227,27 @@ def test_wss_matches_oracle(storage, tol):
     wo = orc.wss(sites, nrm)
     assert wo.max() > 1e-6  # a developed shear layer
     assert rel_l2(wl, wo) <= 10 * tol
+
+
+# ------------------------------------------------------------------ vessel trees
+
+@pytest.mark.parametrize("storage,tol,steps", [("f64", 1e-10, 200), ("f32", 1e-5, 200)])
+def test_murray_tree_parity(storage, tol, steps):
+    """A seeded bifurcating tree (depth 3, root radius 14): oblique vessels give
+    irregular tiles, leaf outlets and a root inlet; per-wall-site kappa from the
+    local rest radius (Eh/r0 = 0.5), smooth random start."""
+    geo = I.murray_tree(seed=3, depth=3, root_radius=14.0)
+    geo.iolets[0].u_mean = 0.02
+    geo.iolets[0].u_amp = 0.01
+    geo.iolets[0].period = 500.0
+    r0 = np.zeros(geo.shape)
+    fl = np.argwhere(geo.labels == 1)
+    r0[tuple(fl.T)] = I.rest_radius(geo, fl)
+    lat, orc = make_pair(geo, storage, tau=0.7, wall_model=1, F=0.85, kappa_grid=0.75 * r0 / 0.5,
+                         fields=I.random_fields(9, geo.shape, drho=1e-3, umax=0.01))
+    info = lat.info()
+    assert info[6] > 0  # irregular tiles are exercised
+    lat.step(steps)
+    orc.run(steps)
+    _compare(lat, orc, tol, "tree")
+    np.testing.assert_allclose(lat.reduce(), orc.reduce(), rtol=10 * tol, atol=1e-9)
