@@ -61,7 +61,7 @@ def workload(args):
         geo.iolets[0].u_amp = 0.02
         geo.iolets[0].period = 4000.0
         params = dict(tau=0.6, F=0.85, kappa=0.75 * 48.0 / 0.5, rho0=1.0)
-        name = ("seeded Murray tree depth 6, root R=48, 10% taper (%d sites), tau=0.6, Eh/r0=0.5"
+        name = ("seeded Murray tree depth 6, root R=48, 10%% taper (%d sites), tau=0.6, Eh/r0=0.5"
                 % geo.n_fluid())
     elif args.config == "tube8":
         geo = I.tube(8, 64, u_mean=0.025)
