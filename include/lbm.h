@@ -224,6 +224,40 @@ int lbm_checkpoint_load(lbm_ctx *ctx, const void *host_buf, size_t bytes);
  *   sites host int64 [m] canonical ids; normals host [m][3]; out host [m]. */
 int lbm_wss(lbm_ctx *ctx, const int64_t *sites, const double *normals, int64_t m, double *out);
 
+/* ---------------------------------------------------------------- ensembles
+ * An ensemble advances many independent lattices (members) together: each
+ * timestep is one launch of the bulk kernel and one of the boundary kernel
+ * covering the tiles of every member, so that many small vessels with their
+ * own tau, F, kappa, inlet and outlet fill the GPU together.  The paper runs
+ * one geometry at a time; this batching has no counterpart there.
+ *
+ * lbm_ensemble_create - members: [n] contexts built by lbm_build_lattice, all
+ *   with the same storage, on the same device, at the same step; they stay
+ *   owned by the caller and must outlive the ensemble.  The ensemble orders
+ *   its work on members[0]'s stream.  Wall parameters set on a member with
+ *   lbm_set_wall_params are picked up by the next lbm_ensemble_step.
+ * lbm_ensemble_step - enqueue n_steps timesteps of every member and advance
+ *   their step counters.  With LBM_TUNE_GRAPH_STEPS = G > 0 (even), whole
+ *   blocks of G steps replay a CUDA graph captured on first use (the inlet
+ *   time reads a device step counter, so replays stay exact).
+ * lbm_ensemble_sync - wait, then lbm_sync every member (first error wins).
+ * lbm_ensemble_tune - schedule knobs (chosen by an autotuner in the binding):
+ *   LBM_TUNE_PREFETCH    L2 prefetch distance in tiles (>= 0);
+ *   LBM_TUNE_SCHEDULE    0: members in the given order, 1: largest first;
+ *   LBM_TUNE_GRAPH_STEPS steps per captured graph (even, 0 = direct launches).
+ * Before using a member's own calls (moments, wall state, ...) call
+ * lbm_ensemble_sync.  Errors: LBM_EINVAL (bad arguments, mixed storage or
+ * steps), LBM_ESTATE (members drifted apart), LBM_ENOMEM, LBM_ECUDA; the
+ * message is lbm_ensemble_last_error. */
+typedef struct lbm_ensemble lbm_ensemble;
+enum { LBM_TUNE_PREFETCH = 0, LBM_TUNE_SCHEDULE = 1, LBM_TUNE_GRAPH_STEPS = 2 };
+int lbm_ensemble_create(lbm_ctx *const *members, int32_t n, lbm_ensemble **out);
+int lbm_ensemble_step(lbm_ensemble *ens, int64_t n_steps);
+int lbm_ensemble_sync(lbm_ensemble *ens);
+int lbm_ensemble_tune(lbm_ensemble *ens, int32_t knob, int64_t value);
+const char *lbm_ensemble_last_error(const lbm_ensemble *ens);
+void lbm_ensemble_destroy(lbm_ensemble *ens);
+
 /* lbm_set_stream - run subsequent work on another cudaStream_t. */
 int lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
 

@@ -10,7 +10,7 @@ from ._capi import (LBM_BF16S, LBM_F16S, LBM_F32, LBM_F64, LbmError,  # noqa: F4
 
 
 def __getattr__(name):
-    if name == "Lattice":
-        from .lattice import Lattice
-        return Lattice
+    if name in ("Lattice", "Ensemble"):
+        from . import lattice
+        return getattr(lattice, name)
     raise AttributeError(name)

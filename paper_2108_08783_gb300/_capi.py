@@ -24,7 +24,10 @@ EXPORTS = (
     "lbm_get_populations", "lbm_set_populations", "lbm_checkpoint_bytes", "lbm_checkpoint_save",
     "lbm_checkpoint_load", "lbm_wss", "lbm_set_stream", "lbm_last_error", "lbm_status_string",
     "lbm_destroy", "lbm_profile", "lbm_profile_read", "lbm_reduce_noalloc",
+    "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_sync", "lbm_ensemble_tune",
+    "lbm_ensemble_last_error", "lbm_ensemble_destroy",
 )
+LBM_TUNE_PREFETCH, LBM_TUNE_SCHEDULE, LBM_TUNE_GRAPH_STEPS = 0, 1, 2
 
 
 class LbmIolet(C.Structure):
@@ -85,6 +88,12 @@ def lib():
         "lbm_profile": ([P, i32], C.c_int),
         "lbm_profile_read": ([P, P, P], C.c_int),
         "lbm_reduce_noalloc": ([P, P, i32], C.c_int),
+        "lbm_ensemble_create": ([P, i32, C.POINTER(P)], C.c_int),
+        "lbm_ensemble_step": ([P, i64], C.c_int),
+        "lbm_ensemble_sync": ([P], C.c_int),
+        "lbm_ensemble_tune": ([P, i32, i64], C.c_int),
+        "lbm_ensemble_last_error": ([P], C.c_char_p),
+        "lbm_ensemble_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

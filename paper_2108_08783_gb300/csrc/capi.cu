@@ -236,6 +236,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   d.pop = dev_alloc<unsigned char>(c, (size_t)lbm::kQ * d.npad * sz);
   lbm::TileDesc* td = dev_alloc<lbm::TileDesc>(c, L.tiles.size());
   lbm::LaunchDesc* to = dev_alloc<lbm::LaunchDesc>(c, L.launch.size());
+  double* tom = dev_alloc<double>(c, L.launch.size());
   uint32_t* sm = dev_alloc<uint32_t>(c, S);
   uint32_t* sio = dev_alloc<uint32_t>(c, S);
   int32_t* sn = dev_alloc<int32_t>(c, 18 * S);
@@ -250,7 +251,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   c->iolet_sites = dev_alloc<int64_t>(c, L.iolet_sites.size());
   c->partial = dev_alloc<double>(c, lbm::reduce_partials());
   c->red_out = dev_alloc<double>(c, 1 + n_iolets);
-  if (!d.pop || !td || !to || !sm || !sio || !sn || !sp || !sF || !sK || !sdE || !sUw ||
+  if (!d.pop || !td || !to || !tom || !sm || !sio || !sn || !sp || !sF || !sK || !sdE || !sUw ||
       !io || !err || !c->iolet_off || !c->iolet_sites || !c->partial || !c->red_out) {
     g_build_err = "device allocation failed";
     lbm_destroy(c);
@@ -258,6 +259,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   }
   d.tiles = td;
   d.launch = to;
+  d.tile_omega = tom;
   d.slot_mask = sm;
   d.slot_io = sio;
   d.slot_nbr = sn;
@@ -287,6 +289,11 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   chk(h2d(c, td, L.tiles.data(), L.tiles.size()));
   chk(h2d(c, to, L.launch.data(), L.launch.size()));
+  {
+    std::vector<double> om(L.launch.size(), 1.0 / tau);
+    chk(h2d(c, tom, om.data(), om.size()));
+    chk(cudaStreamSynchronize(c->stream));  // om is a temporary
+  }
   chk(h2d(c, sm, L.slot_mask.data(), S));
   chk(h2d(c, sio, L.slot_io.data(), S));
   chk(h2d(c, sn, L.slot_nbr.data(), 18 * S));
@@ -393,22 +400,13 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
   if (!c) return LBM_EINVAL;
   if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps must be >= 0");
   lbm::StepParams p;
-  p.omega = 1.0 / c->tau;
   p.rho0 = c->rho0;
   p.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
   p.prefetch = c->prefetch;
+  p.step_dev = nullptr;
   for (int64_t s = 0; s < n_steps; ++s) {
     p.step = c->step;
     p.write_state = s == n_steps - 1 ? 1 : 0;
-    for (int k = 0; k < lbm::kMaxTimedInlets; ++k) {
-      p.inlet_sin[k] = p.inlet_cos[k] = 0.0;
-      if (k < (int)c->iolets.size() && c->iolets[k].period > 0.0) {
-        const lbm_iolet& io = c->iolets[k];
-        const double th = 2.0 * M_PI * (double)c->step / io.period + io.phase;
-        p.inlet_sin[k] = io.u_amp * std::sin(th);
-        p.inlet_cos[k] = io.u_amp * std::cos(th);
-      }
-    }
     void* ev[3] = {nullptr, nullptr, nullptr};
     if (c->prof) {
       while (c->ev.size() < c->ev_used + 3) {
@@ -715,3 +713,246 @@ extern "C" int lbm_reduce_noalloc(lbm_ctx* c, double* out, int32_t out_is_device
   if (e != cudaSuccess) return cuda_fail(c, e, "lbm_reduce_noalloc copy");
   return sync(c, "lbm_reduce_noalloc");
 }
+
+// ---------------------------------------------------------------------------
+// Ensembles: many independent lattices advanced by one launch of each step
+// kernel per timestep (optionally replayed from a captured CUDA graph).
+
+struct lbm_ensemble {
+  std::vector<lbm_ctx*> members;  // not owned
+  int storage = LBM_F64;
+  cudaStream_t stream = nullptr, side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  std::vector<void*> owned;       // device buffers (member 0's allocator)
+  lbm::MemberDev* mem_d = nullptr;
+  int64_t* prefix_d = nullptr;    // bulk prefix [n+1], then boundary prefix [n+1]
+  int64_t* step_d = nullptr;      // device step counter of captured graphs
+  std::vector<int32_t> order;     // schedule: member order in the launch numbering
+  int64_t prefetch = LBM_DEFAULT_PREFETCH;
+  int64_t graph_steps = 0;        // 0: direct launches
+  cudaGraphExec_t exec = nullptr;
+  int64_t exec_steps = 0;
+  int exec_parity = -1;
+  lbm::EnsembleLaunch launch{};
+  std::string err;
+};
+
+namespace {
+
+int ens_fail(lbm_ensemble* e, int code, const std::string& msg) {
+  if (e) e->err = msg;
+  return code;
+}
+
+int ens_cuda(lbm_ensemble* e, cudaError_t r, const char* what) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(r));
+  return ens_fail(e, LBM_ECUDA, buf);
+}
+
+void ens_drop_graph(lbm_ensemble* e) {
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  e->exec = nullptr;
+  e->exec_steps = 0;
+  e->exec_parity = -1;
+}
+
+// Upload the member table and the prefix tables in schedule order.
+int ens_upload(lbm_ensemble* e) {
+  const int n = (int)e->members.size();
+  std::vector<lbm::MemberDev> tab(n);
+  std::vector<int64_t> pre(2 * (n + 1), 0);
+  for (int q = 0; q < n; ++q) {
+    const lbm_ctx* c = e->members[e->order[q]];
+    lbm::MemberDev& md = tab[q];
+    std::memset(&md, 0, sizeof md);
+    md.d = c->d;
+    md.rho0 = c->rho0;
+    md.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
+    pre[q + 1] = pre[q] + (c->d.n_tiles - c->d.n_boundary);
+    pre[n + 1 + q + 1] = pre[n + 1 + q] + c->d.n_boundary;
+  }
+  cudaError_t r = cudaMemcpyAsync(e->mem_d, tab.data(), n * sizeof(lbm::MemberDev),
+                                  cudaMemcpyHostToDevice, e->stream);
+  if (r == cudaSuccess)
+    r = cudaMemcpyAsync(e->prefix_d, pre.data(), pre.size() * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, e->stream);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);  // tab, pre are temporaries
+  if (r != cudaSuccess) return ens_cuda(e, r, "ensemble upload");
+  e->launch.mem = e->mem_d;
+  e->launch.bulk_prefix = e->prefix_d;
+  e->launch.boundary_prefix = e->prefix_d + (n + 1);
+  e->launch.n_members = n;
+  e->launch.n_bulk_tiles = pre[n];
+  e->launch.n_boundary_tiles = pre[2 * n + 1];
+  ens_drop_graph(e);
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_ensemble_last_error(const lbm_ensemble* e) {
+  return e ? e->err.c_str() : "null ensemble";
+}
+
+void lbm_ensemble_destroy(lbm_ensemble* e) {
+  if (!e) return;
+  if (e->stream) cudaStreamSynchronize(e->stream);
+  if (e->side) cudaStreamSynchronize(e->side);
+  ens_drop_graph(e);
+  if (!e->members.empty())
+    for (void* p : e->owned) dev_free_raw(e->members[0], p);
+  if (e->fork) cudaEventDestroy(e->fork);
+  if (e->join) cudaEventDestroy(e->join);
+  if (e->side) cudaStreamDestroy(e->side);
+  delete e;
+}
+
+int lbm_ensemble_create(lbm_ctx* const* members, int32_t n, lbm_ensemble** out) {
+  if (!out || !members || n <= 0) return LBM_EINVAL;
+  *out = nullptr;
+  for (int q = 0; q < n; ++q)
+    if (!members[q] || members[q]->storage != members[0]->storage ||
+        members[q]->step != members[0]->step)
+      return LBM_EINVAL;
+  lbm_ensemble* e = new (std::nothrow) lbm_ensemble();
+  if (!e) return LBM_ENOMEM;
+  e->members.assign(members, members + n);
+  e->storage = members[0]->storage;
+  e->stream = members[0]->stream;
+  e->order.resize(n);
+  for (int q = 0; q < n; ++q) e->order[q] = q;
+  int lo = 0, hi = 0;
+  cudaError_t r = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (r == cudaSuccess) r = cudaStreamCreateWithPriority(&e->side, cudaStreamNonBlocking, hi);
+  if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+  if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->join, cudaEventDisableTiming);
+  if (r != cudaSuccess) {
+    lbm_ensemble_destroy(e);
+    return LBM_ECUDA;
+  }
+  lbm_ctx* c0 = members[0];
+  auto alloc = [&](size_t bytes) {
+    void* p = dev_alloc_raw(c0, bytes);
+    if (p) e->owned.push_back(p);
+    return p;
+  };
+  e->mem_d = static_cast<lbm::MemberDev*>(alloc(n * sizeof(lbm::MemberDev)));
+  e->prefix_d = static_cast<int64_t*>(alloc(2 * (n + 1) * sizeof(int64_t)));
+  e->step_d = static_cast<int64_t*>(alloc(sizeof(int64_t)));
+  if (!e->mem_d || !e->prefix_d || !e->step_d) {
+    lbm_ensemble_destroy(e);
+    return LBM_ENOMEM;
+  }
+  if (ens_upload(e) != LBM_OK) {
+    lbm_ensemble_destroy(e);
+    return LBM_ECUDA;
+  }
+  *out = e;
+  return LBM_OK;
+}
+
+int lbm_ensemble_tune(lbm_ensemble* e, int32_t knob, int64_t value) {
+  if (!e) return LBM_EINVAL;
+  e->err.clear();
+  switch (knob) {
+    case LBM_TUNE_PREFETCH:
+      if (value < 0) return ens_fail(e, LBM_EINVAL, "prefetch distance must be >= 0");
+      e->prefetch = value;
+      ens_drop_graph(e);
+      return LBM_OK;
+    case LBM_TUNE_SCHEDULE: {
+      const int n = (int)e->members.size();
+      for (int q = 0; q < n; ++q) e->order[q] = q;
+      if (value == 1) {  // largest members first
+        std::stable_sort(e->order.begin(), e->order.end(), [&](int a, int b) {
+          return e->members[a]->d.n_tiles > e->members[b]->d.n_tiles;
+        });
+      } else if (value != 0) {
+        return ens_fail(e, LBM_EINVAL, "schedule must be 0 (given order) or 1 (largest first)");
+      }
+      return ens_upload(e);
+    }
+    case LBM_TUNE_GRAPH_STEPS:
+      if (value < 0 || (value & 1)) return ens_fail(e, LBM_EINVAL, "graph steps must be even");
+      e->graph_steps = value;
+      ens_drop_graph(e);
+      return LBM_OK;
+  }
+  return ens_fail(e, LBM_EINVAL, "unknown tuning knob");
+}
+
+int lbm_ensemble_step(lbm_ensemble* e, int64_t n_steps) {
+  if (!e || n_steps < 0) return LBM_EINVAL;
+  e->err.clear();
+  const int64_t step0 = e->members[0]->step;
+  for (lbm_ctx* c : e->members)
+    if (c->step != step0) return ens_fail(e, LBM_ESTATE, "members are at different steps");
+  int rc = ens_upload(e);  // wall models or rho0 may have changed since the last call
+  if (rc != LBM_OK) return rc;
+  const lbm::StepStreams ss{e->stream, e->side, e->fork, e->join};
+  lbm::StepParams p{};
+  p.prefetch = e->prefetch;
+  int64_t done = 0;
+  const int64_t G = e->graph_steps;
+  if (G > 0 && n_steps >= G) {
+    const int parity = (int)(step0 & 1);
+    if (!e->exec || e->exec_steps != G || e->exec_parity != parity) {
+      ens_drop_graph(e);
+      cudaGraph_t graph = nullptr;
+      cudaError_t r = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
+      for (int64_t s = 0; s < G && r == cudaSuccess; ++s) {
+        p.step = parity + s;  // offset; the step is *step_d + offset - parity
+        p.step_dev = e->step_d;
+        p.write_state = s == G - 1 ? 1 : 0;
+        const int lr = lbm::launch_ensemble_step(e->storage, e->launch, p, ss);
+        if (lr != 0) r = (cudaError_t)lr;
+      }
+      if (r == cudaSuccess) r = (cudaError_t)lbm::launch_advance(e->step_d, G, e->stream);
+      cudaError_t r2 = cudaStreamEndCapture(e->stream, &graph);
+      if (r == cudaSuccess) r = r2;
+      if (r == cudaSuccess) r = cudaGraphInstantiate(&e->exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (r != cudaSuccess) {
+        e->exec = nullptr;
+        return ens_cuda(e, r, "ensemble graph capture");
+      }
+      e->exec_steps = G;
+      e->exec_parity = parity;
+    }
+    // the captured kernels add `parity` back: store step - parity on the device
+    const int64_t base = step0 - parity;
+    cudaError_t r = cudaMemcpyAsync(e->step_d, &base, sizeof base, cudaMemcpyHostToDevice,
+                                    e->stream);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);
+    while (r == cudaSuccess && n_steps - done >= G) {
+      r = cudaGraphLaunch(e->exec, e->stream);
+      done += G;
+    }
+    if (r != cudaSuccess) return ens_cuda(e, r, "ensemble graph launch");
+  }
+  p.step_dev = nullptr;
+  for (int64_t s = done; s < n_steps; ++s) {
+    p.step = step0 + s;
+    p.write_state = s == n_steps - 1 ? 1 : 0;
+    const int lr = lbm::launch_ensemble_step(e->storage, e->launch, p, ss);
+    if (lr != 0) return ens_cuda(e, (cudaError_t)lr, "ensemble step kernels");
+  }
+  for (lbm_ctx* c : e->members) c->step = step0 + n_steps;
+  return LBM_OK;
+}
+
+int lbm_ensemble_sync(lbm_ensemble* e) {
+  if (!e) return LBM_EINVAL;
+  cudaError_t r = cudaStreamSynchronize(e->stream);
+  if (r != cudaSuccess) return ens_cuda(e, r, "lbm_ensemble_sync");
+  for (lbm_ctx* c : e->members) {
+    const int rc = lbm_sync(c);
+    if (rc != LBM_OK) return ens_fail(e, rc, c->err);
+  }
+  return LBM_OK;
+}
+
+}  // extern "C"

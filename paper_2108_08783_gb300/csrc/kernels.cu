@@ -262,7 +262,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Branch-free update of a site whose 18 links are fluid.
 template <class S, bool ODD>
 __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t* dsc,
-                                            const StepParams& p, int* err) {
+                                            double omega_t, int* err) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
   C g[kQ];
@@ -274,7 +274,7 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
   });
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(err, kErrUnstable);
-  const C omega = C(p.omega);
+  const C omega = C(omega_t);
   Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
   unroll<9>([&](auto Pi) {
     constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
@@ -352,7 +352,8 @@ __device__ __forceinline__ C geq_rt(int j, C drho, C rho, C ux, C uy, C uz, C us
 // per-site neighbour rows (irregular tiles on odd steps); gsm: the warp's
 // [19][32] shared-memory area where g is parked for the boundary rule.
 template <class S, bool ODD>
-__device__ __forceinline__ void boundary_update(const DevLattice& d, const StepParams& p, S* P,
+__device__ __forceinline__ void boundary_update(const DevLattice& d, const StepParams& p,
+                                                double omega_t, S* P,
                                                 int64_t x, const int32_t* dsc, bool irr,
                                                 uint32_t smask, uint32_t iom, double Fw, double Kw,
                                                 double pr0, double pr1, double pr2,
@@ -364,7 +365,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   const int64_t np = d.npad;
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
-  const C omega = C(p.omega);
+  const C omega = C(omega_t);
   const C keep = C(1) - omega;  // (1 - 1/tau)
   unroll<kQ>([&](auto J) {
     constexpr int j = decltype(J)::value;
@@ -417,24 +418,26 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   // Inlet velocity (Sec. 3): u_in = a (u_mean p0 + u_amp (ps sin th + pc cos th)).
   C uix = C(0), uiy = C(0), uiz = C(0);
   if (smask & kHasInlet) {
-    const int k = (int)((smask & kInletBits) >> kInletShift);
+    const int k = (int)((iom & kIoletIdBits) >> kIoletShift);
     const IoletDev& io = d.iolets[k];
     double gval = io.u_mean * pr0;
     if (!io.steady) {
-      // u_amp sin(th), u_amp cos(th) of this step: from the host for the
-      // first kMaxTimedInlets iolets, else evaluated here
-      double as, ac;
-      if (k < kMaxTimedInlets) {
-        as = p.inlet_sin[k];
-        ac = p.inlet_cos[k];
+      // th = 2 pi n / T + phase.  FP64 paths take sin/cos in FP64 (as the
+      // oracle); FP32 paths reduce the phase to one period in FP64 and take
+      // sinpi/cospi in FP32 (error ~1e-7 of u_amp).
+      double sn, cs;
+      const int64_t step = p.step + (p.step_dev ? *p.step_dev : 0);
+      if constexpr (std::is_same<C, double>::value) {
+        sincos(2.0 * M_PI * (double)step / io.period + io.phase, &sn, &cs);
       } else {
-        const double th = 2.0 * M_PI * (double)p.step / io.period + io.phase;
-        double sn, cs;
-        sincos(th, &sn, &cs);
-        as = io.u_amp * sn;
-        ac = io.u_amp * cs;
+        double t = (double)step / io.period + io.phase * (0.5 / M_PI);
+        t -= floor(t);
+        float sf, cf;
+        sincospif(2.0f * (float)t, &sf, &cf);
+        sn = sf;
+        cs = cf;
       }
-      gval += pr1 * as + pr2 * ac;
+      gval += io.u_amp * (pr1 * sn + pr2 * cs);
     }
     uix = C(gval * io.axis[0]);
     uiy = C(gval * io.axis[1]);
@@ -445,7 +448,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   // slot (x, j) - half-way bounce-back f*_i, or the GZS form
   // f^eq_j(rho_b, u_b) + (1 - 1/tau) f^neq_j with (rho_b, u_b) = (rho, U_w) at a
   // wall, (rho, u_in) at a velocity inlet, (rho_out, u) at a density outlet.
-  const int32_t io_code = -2 - (int32_t)((smask & kInletBits) >> kInletShift);
+  const int32_t io_code = -2 - (int32_t)((iom & kIoletIdBits) >> kIoletShift);
   while (nf) {
     const int i = __ffs(nf) - 1;
     nf &= nf - 1;
@@ -494,9 +497,10 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
     bulk_prefetch_l2(static_cast<const S*>(d.pop) + lane * d.npad + tp * kTile,
                      kTile * sizeof(S));
   }
+  const double omega = __ldg(d.tile_omega + k);
   __syncwarp();
   const int64_t x = (int64_t)dsc[19] * kTile + lane;
-  if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p, d.err);
+  if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, omega, d.err);
 }
 
 template <class S, bool ODD>
@@ -524,6 +528,7 @@ __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepPar
   // per-site data and the descriptor, all in one round trip
   const uint32_t smask = __ldg(d.slot_mask + slot);
   const uint32_t iom = __ldg(d.slot_io + slot);
+  const double omega = __ldg(d.tile_omega + k);
   if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
   __syncwarp();
   const uint32_t tmask = (uint32_t)dsc[18];
@@ -565,8 +570,8 @@ __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepPar
     if (valid) boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, true, nbr_s, lane, g);
   }
   if (!valid) return;
-  boundary_update<S, ODD>(d, p, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s, lane,
-                          slot, g, gsm);
+  boundary_update<S, ODD>(d, p, omega, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s,
+                          lane, slot, g, gsm);
 }
 
 template <class S, bool ODD>
@@ -582,6 +587,54 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
   if (k >= d.n_boundary) return;  // warp-uniform
   boundary_tile<S, ODD>(d, p, k, desc_s[w], stage[w], &bars[w], gs[w], lane);
 }
+
+// -------------------------------------------------------------- ensembles
+// One launch of each step kernel covers every member of an ensemble: global
+// tile g belongs to the member m with prefix[m] <= g < prefix[m + 1].
+
+__device__ __forceinline__ int find_member(const int64_t* prefix, int32_t nm, int64_t g) {
+  int lo = 0, hi = nm;  // prefix[lo] <= g < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(prefix + mid) <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK_MINB)
+    k_bulk_ens(const EnsembleLaunch e, const StepParams p) {
+  __shared__ __align__(16) int32_t desc_s[kBulkWarps][20];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * kBulkWarps + w;
+  if (g >= e.n_bulk_tiles) return;  // warp-uniform
+  const int m = find_member(e.bulk_prefix, e.n_members, g);
+  const DevLattice& d = e.mem[m].d;
+  bulk_tile<S, ODD>(d, p, d.n_boundary + (g - __ldg(e.bulk_prefix + m)), desc_s[w], lane);
+}
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_BOUNDARY_MINB)
+    k_boundary_ens(const EnsembleLaunch e, const StepParams p) {
+  using C = typename Codec<S>::C;
+  __shared__ __align__(128) int32_t stage[kBoundaryWarps][18 * kTile];
+  __shared__ __align__(16) C gs[kBoundaryWarps][kQ * kTile];
+  __shared__ __align__(16) int32_t desc_s[kBoundaryWarps][20];
+  __shared__ uint64_t bars[kBoundaryWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * kBoundaryWarps + w;
+  if (g >= e.n_boundary_tiles) return;  // warp-uniform
+  const int m = find_member(e.boundary_prefix, e.n_members, g);
+  const MemberDev& md = e.mem[m];
+  StepParams pm = p;
+  pm.rho0 = md.rho0;
+  pm.elastic = md.elastic;
+  boundary_tile<S, ODD>(md.d, pm, g - __ldg(e.boundary_prefix + m), desc_s[w], stage[w], &bars[w],
+                        gs[w], lane);
+}
+
+__global__ void k_advance(int64_t* step, int64_t by) { *step += by; }
 
 // ------------------------------------------------ state conversion kernels
 
@@ -835,6 +888,42 @@ int launch_step(int storage, const DevLattice& d, const StepParams& p, const Ste
     using S = std::remove_pointer_t<decltype(tag)>;
     return step_t<S>(d, p, ss, events);
   });
+}
+
+template <class S>
+int ensemble_step_t(const EnsembleLaunch& e, const StepParams& p, const StepStreams& ss) {
+  cudaStream_t m = (cudaStream_t)ss.main, side = (cudaStream_t)ss.side;
+  const unsigned nbnd = (unsigned)((e.n_boundary_tiles + kBoundaryWarps - 1) / kBoundaryWarps);
+  const unsigned nbulk = (unsigned)((e.n_bulk_tiles + kBulkWarps - 1) / kBulkWarps);
+  const bool odd = p.step & 1;  // every member is at the same step; graphs keep the parity
+  if (nbnd) {
+    cudaEventRecord((cudaEvent_t)ss.fork, m);
+    cudaStreamWaitEvent(side, (cudaEvent_t)ss.fork, 0);
+    if (odd) k_boundary_ens<S, true><<<nbnd, kBoundaryWarps * 32, 0, side>>>(e, p);
+    else k_boundary_ens<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(e, p);
+  }
+  if (nbulk) {
+    if (odd) k_bulk_ens<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(e, p);
+    else k_bulk_ens<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(e, p);
+  }
+  if (nbnd) {
+    cudaEventRecord((cudaEvent_t)ss.join, side);
+    cudaStreamWaitEvent(m, (cudaEvent_t)ss.join, 0);
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_ensemble_step(int storage, const EnsembleLaunch& e, const StepParams& p,
+                         const StepStreams& ss) {
+  return dispatch(storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    return ensemble_step_t<S>(e, p, ss);
+  });
+}
+
+int launch_advance(int64_t* step_dev, int64_t by, void* stream) {
+  k_advance<<<1, 1, 0, (cudaStream_t)stream>>>(step_dev, by);
+  return (int)cudaGetLastError();
 }
 
 int launch_init(int storage, const DevLattice& d, const double* rho, const double* u,

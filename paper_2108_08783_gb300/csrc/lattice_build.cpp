@@ -177,7 +177,7 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
       }
     }
     const int id = site_inlet[s] >= 0 ? site_inlet[s] : first_io;
-    if (id >= 0) m |= (uint32_t)id << kInletShift;
+    if (id >= 0) io |= (uint32_t)id << kIoletShift;
     site_mask[s] = m;
     site_io[s] = io;
     if (walls) L.wall_sites.push_back(s);

@@ -24,9 +24,12 @@ constexpr int kWarpsPerCta = LBM_WARPS_PER_CTA;  // step kernel: tiles (warps) p
 constexpr uint32_t kDirBits = 0x7FFFEu;
 constexpr uint32_t kMultiIolet = 1u << 19; // site links into two or more iolets: the
                                            // per-link codes of the neighbour table decide
-constexpr int kInletShift = 20;            // slot masks: bits 20..27 = iolet id (the
-constexpr uint32_t kInletBits = 0xFFu << kInletShift;  // velocity inlet if any)
 constexpr uint32_t kValid = 1u << 28;      // slot holds a site (slot masks only)
+// Iolet-link words (slot_io): bits 1..18 = the non-fluid link is an iolet link;
+// bits 20..31 = the site's iolet id (its velocity inlet if it has one).
+constexpr int kIoletShift = 20;
+constexpr uint32_t kIoletIdBits = 0xFFFu << kIoletShift;
+constexpr int kMaxIolets = 4095;
 constexpr uint32_t kHasInlet = 1u << 29;   // a velocity-inlet link is present
 constexpr uint32_t kHasWall = 1u << 30;    // a wall link is present
 constexpr uint32_t kIrregular = 1u << 31;  // tile: fluid-link offsets differ between lanes
@@ -88,7 +91,7 @@ struct HostLattice {
   // boundary slots (32 per boundary tile, in tile order)
   int64_t n_slots = 0;
   std::vector<uint32_t> slot_mask;   // [n_slots]
-  std::vector<uint32_t> slot_io;     // [n_slots] bits 1..18: the non-fluid link is an iolet link
+  std::vector<uint32_t> slot_io;     // [n_slots] iolet-link word (see kIoletShift)
   std::vector<int32_t> slot_nbr;     // [18][n_slots] absolute neighbour or non-fluid code
   std::vector<double> slot_prof;     // [3][n_slots] inlet shape p0, ps, pc
   std::vector<int64_t> wall_slot;    // [n_wall_sites] slot of each wall site
@@ -110,6 +113,7 @@ struct DevLattice {
   int64_t n = 0;
   const TileDesc* tiles = nullptr;
   const LaunchDesc* launch = nullptr;  // boundary tiles (ascending), then bulk tiles
+  const double* tile_omega = nullptr;  // [n_tiles] 1/tau of each tile, launch order
   int64_t n_tiles = 0;
   const uint32_t* slot_mask = nullptr;
   const uint32_t* slot_io = nullptr;
@@ -126,20 +130,24 @@ struct DevLattice {
   int64_t n_boundary = 0;  // boundary tiles = leading entries of the launch order
 };
 
-// Iolets whose inlet time factors are evaluated on the host each step.
-constexpr int kMaxTimedInlets = 8;
-
 struct StepParams {
-  double omega;      // 1 / tau
   double rho0;
   int32_t elastic;   // 1: elastic GZS wall, 0: bounce-back
   int32_t write_state;
-  int64_t step;
+  int64_t step;      // step index (plus *step_dev when step_dev is set)
   int64_t prefetch;  // L2 prefetch distance in tiles of launch order (0: off)
-  // u_amp sin(th_k), u_amp cos(th_k), th_k = 2 pi step / period_k + phase_k
-  double inlet_sin[kMaxTimedInlets];
-  double inlet_cos[kMaxTimedInlets];
+  const int64_t* step_dev;  // device step counter (captured graphs), or NULL
 };
+
+// One member of an ensemble: its device view and its wall constants.
+struct MemberDev {
+  DevLattice d;
+  double rho0;
+  int32_t elastic;
+  int32_t pad;
+};
+
+
 
 // Kernel launchers (kernels.cu); storage is LBM_F64 ... LBM_BF16S.
 // All return cudaError_t values cast to int.
@@ -155,6 +163,19 @@ struct StepStreams {
 // fork, after the bulk kernel and after the join.
 int launch_step(int storage, const DevLattice& d, const StepParams& p, const StepStreams& ss,
                 void* const* events);
+
+// Ensemble launch: the members' bulk (boundary) tiles are numbered in
+// schedule order; prefix[m] is the number of tiles of members before m.
+struct EnsembleLaunch {
+  const MemberDev* mem;
+  const int64_t* bulk_prefix;      // [n_members + 1]
+  const int64_t* boundary_prefix;  // [n_members + 1]
+  int32_t n_members;
+  int64_t n_bulk_tiles, n_boundary_tiles;
+};
+int launch_ensemble_step(int storage, const EnsembleLaunch& e, const StepParams& p,
+                         const StepStreams& ss);
+int launch_advance(int64_t* step_dev, int64_t by, void* stream);
 int launch_init(int storage, const DevLattice& d, const double* rho, const double* u,
                 void* stream);
 int launch_gather(int storage, const DevLattice& d, int odd_layout, double* f_out, void* stream);

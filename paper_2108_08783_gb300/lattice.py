@@ -224,3 +224,90 @@ class Lattice:
         out = np.zeros(sites.size)
         self._check(self._lib.lbm_wss(self.h, _ptr(sites), _ptr(normals), sites.size, _ptr(out)))
         return out
+
+
+class Ensemble:
+    """Many independent lattices advanced by one launch of each step kernel per
+    timestep (wraps ``lbm_ensemble_create``).  The member Lattices stay owned
+    by the caller and must outlive the ensemble; call :meth:`sync` before
+    using a member's own methods."""
+
+    def __init__(self, lattices):
+        self._lib = A.lib()
+        self.members = list(lattices)
+        arr = (C.c_void_p * len(self.members))(*[m.h.value for m in self.members])
+        h = C.c_void_p()
+        rc = self._lib.lbm_ensemble_create(arr, len(self.members), C.byref(h))
+        if rc != A.LBM_OK:
+            raise A.LbmError(rc, "lbm_ensemble_create failed")
+        self.h = h
+        self.stream = self.members[0].stream
+        self.n = sum(m.n for m in self.members)
+        self.settings = {"prefetch": None, "schedule": 0, "graph_steps": 0}
+
+    def _check(self, rc):
+        if rc != A.LBM_OK:
+            raise A.LbmError(rc, self._lib.lbm_ensemble_last_error(self.h).decode())
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_ensemble_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(self._lib.lbm_ensemble_sync(self.h))
+
+    def tune(self, prefetch=None, schedule=None, graph_steps=None):
+        if prefetch is not None:
+            self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_PREFETCH, int(prefetch)))
+            self.settings["prefetch"] = int(prefetch)
+        if schedule is not None:
+            self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_SCHEDULE, int(schedule)))
+            self.settings["schedule"] = int(schedule)
+        if graph_steps is not None:
+            self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_GRAPH_STEPS,
+                                                    int(graph_steps)))
+            self.settings["graph_steps"] = int(graph_steps)
+
+    def time_steps(self, n):
+        """Device ms of n steps (CUDA events on the ensemble's stream)."""
+        import torch
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        self.sync()
+        e0.record(self.stream)
+        self.step(n)
+        e1.record(self.stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def autotune(self, prefetch=(0, 1024, 2048, 4096, 8192), schedule=(0, 1),
+                 graph_steps=(0, 20), trial_steps=40):
+        """Choose the schedule knobs by timing each candidate on this ensemble
+        (coordinate search, one knob at a time).  Every trial advances the
+        members by ``trial_steps`` steps."""
+        results = []
+        best = dict(prefetch=prefetch[0], schedule=schedule[0], graph_steps=graph_steps[0])
+        for knob, cands in (("schedule", schedule), ("prefetch", prefetch),
+                            ("graph_steps", graph_steps)):
+            times = {}
+            for v in cands:
+                cfg = dict(best)
+                cfg[knob] = v
+                self.tune(**cfg)
+                self.time_steps(trial_steps)  # warm (and capture a graph if any)
+                times[v] = self.time_steps(trial_steps)
+                results.append((dict(cfg), times[v]))
+            best[knob] = min(times, key=times.get)
+        self.tune(**best)
+        return best, results
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h is not None:
+            self._lib.lbm_ensemble_destroy(h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
