@@ -233,8 +233,9 @@ int lbm_wss(lbm_ctx *ctx, const int64_t *sites, const double *normals, int64_t m
  *
  * lbm_ensemble_create - members: [n] contexts built by lbm_build_lattice, all
  *   with the same storage, on the same device, at the same step; they stay
- *   owned by the caller and must outlive the ensemble.  The ensemble orders
- *   its work on members[0]'s stream.  Wall parameters set on a member with
+ *   owned by the caller and must outlive the ensemble.  The ensemble runs on
+ *   private streams, ordered after the work already queued on the members'
+ *   streams and before their later work.  Wall parameters set on a member with
  *   lbm_set_wall_params are picked up by the next lbm_ensemble_step.
  * lbm_ensemble_step - enqueue n_steps timesteps of every member and advance
  *   their step counters.  With LBM_TUNE_GRAPH_STEPS = G > 0 (even), whole

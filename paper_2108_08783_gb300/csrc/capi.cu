@@ -721,8 +721,10 @@ extern "C" int lbm_reduce_noalloc(lbm_ctx* c, double* out, int32_t out_is_device
 struct lbm_ensemble {
   std::vector<lbm_ctx*> members;  // not owned
   int storage = LBM_F64;
+  // private streams (capturable), ordered after / before the members' streams
   cudaStream_t stream = nullptr, side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, order = nullptr;
+  std::vector<cudaStream_t> member_streams;  // distinct streams of the members
   std::vector<void*> owned;       // device buffers (member 0's allocator)
   lbm::MemberDev* mem_d = nullptr;
   int64_t* prefix_d = nullptr;    // bulk prefix [n+1], then boundary prefix [n+1]
@@ -806,7 +808,9 @@ void lbm_ensemble_destroy(lbm_ensemble* e) {
     for (void* p : e->owned) dev_free_raw(e->members[0], p);
   if (e->fork) cudaEventDestroy(e->fork);
   if (e->join) cudaEventDestroy(e->join);
+  if (e->order) cudaEventDestroy(e->order);
   if (e->side) cudaStreamDestroy(e->side);
+  if (e->stream) cudaStreamDestroy(e->stream);
   delete e;
 }
 
@@ -821,14 +825,19 @@ int lbm_ensemble_create(lbm_ctx* const* members, int32_t n, lbm_ensemble** out) 
   if (!e) return LBM_ENOMEM;
   e->members.assign(members, members + n);
   e->storage = members[0]->storage;
-  e->stream = members[0]->stream;
+  for (lbm_ctx* c : e->members)
+    if (std::find(e->member_streams.begin(), e->member_streams.end(), c->stream) ==
+        e->member_streams.end())
+      e->member_streams.push_back(c->stream);
   e->order.resize(n);
   for (int q = 0; q < n; ++q) e->order[q] = q;
   int lo = 0, hi = 0;
   cudaError_t r = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (r == cudaSuccess) r = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
   if (r == cudaSuccess) r = cudaStreamCreateWithPriority(&e->side, cudaStreamNonBlocking, hi);
   if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
   if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->join, cudaEventDisableTiming);
+  if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->order, cudaEventDisableTiming);
   if (r != cudaSuccess) {
     lbm_ensemble_destroy(e);
     return LBM_ECUDA;
@@ -892,6 +901,12 @@ int lbm_ensemble_step(lbm_ensemble* e, int64_t n_steps) {
     if (c->step != step0) return ens_fail(e, LBM_ESTATE, "members are at different steps");
   int rc = ens_upload(e);  // wall models or rho0 may have changed since the last call
   if (rc != LBM_OK) return rc;
+  // start after the members' pending work
+  for (cudaStream_t ms : e->member_streams) {
+    cudaError_t r = cudaEventRecord(e->order, ms);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(e->stream, e->order, 0);
+    if (r != cudaSuccess) return ens_cuda(e, r, "ensemble ordering");
+  }
   const lbm::StepStreams ss{e->stream, e->side, e->fork, e->join};
   lbm::StepParams p{};
   p.prefetch = e->prefetch;
@@ -941,6 +956,11 @@ int lbm_ensemble_step(lbm_ensemble* e, int64_t n_steps) {
     if (lr != 0) return ens_cuda(e, (cudaError_t)lr, "ensemble step kernels");
   }
   for (lbm_ctx* c : e->members) c->step = step0 + n_steps;
+  // the members' later work comes after the ensemble's
+  cudaError_t r = cudaEventRecord(e->order, e->stream);
+  for (cudaStream_t ms : e->member_streams)
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(ms, e->order, 0);
+  if (r != cudaSuccess) return ens_cuda(e, r, "ensemble ordering");
   return LBM_OK;
 }
 

@@ -241,7 +241,7 @@ class Ensemble:
         if rc != A.LBM_OK:
             raise A.LbmError(rc, "lbm_ensemble_create failed")
         self.h = h
-        self.stream = self.members[0].stream
+        self.stream = self.members[0].stream  # the ensemble's work is ordered with it
         self.n = sum(m.n for m in self.members)
         self.settings = {"prefetch": None, "schedule": 0, "graph_steps": 0}
 
