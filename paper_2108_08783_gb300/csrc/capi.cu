@@ -723,7 +723,7 @@ struct lbm_ensemble {
   int storage = LBM_F64;
   // private streams (capturable), ordered after / before the members' streams
   cudaStream_t stream = nullptr, side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr, order = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, ord_ev = nullptr;
   std::vector<cudaStream_t> member_streams;  // distinct streams of the members
   std::vector<void*> owned;       // device buffers (member 0's allocator)
   lbm::MemberDev* mem_d = nullptr;
@@ -808,7 +808,7 @@ void lbm_ensemble_destroy(lbm_ensemble* e) {
     for (void* p : e->owned) dev_free_raw(e->members[0], p);
   if (e->fork) cudaEventDestroy(e->fork);
   if (e->join) cudaEventDestroy(e->join);
-  if (e->order) cudaEventDestroy(e->order);
+  if (e->ord_ev) cudaEventDestroy(e->ord_ev);
   if (e->side) cudaStreamDestroy(e->side);
   if (e->stream) cudaStreamDestroy(e->stream);
   delete e;
@@ -837,7 +837,7 @@ int lbm_ensemble_create(lbm_ctx* const* members, int32_t n, lbm_ensemble** out) 
   if (r == cudaSuccess) r = cudaStreamCreateWithPriority(&e->side, cudaStreamNonBlocking, hi);
   if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
   if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->join, cudaEventDisableTiming);
-  if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->order, cudaEventDisableTiming);
+  if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->ord_ev, cudaEventDisableTiming);
   if (r != cudaSuccess) {
     lbm_ensemble_destroy(e);
     return LBM_ECUDA;
@@ -903,8 +903,8 @@ int lbm_ensemble_step(lbm_ensemble* e, int64_t n_steps) {
   if (rc != LBM_OK) return rc;
   // start after the members' pending work
   for (cudaStream_t ms : e->member_streams) {
-    cudaError_t r = cudaEventRecord(e->order, ms);
-    if (r == cudaSuccess) r = cudaStreamWaitEvent(e->stream, e->order, 0);
+    cudaError_t r = cudaEventRecord(e->ord_ev, ms);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(e->stream, e->ord_ev, 0);
     if (r != cudaSuccess) return ens_cuda(e, r, "ensemble ordering");
   }
   const lbm::StepStreams ss{e->stream, e->side, e->fork, e->join};
@@ -957,9 +957,9 @@ int lbm_ensemble_step(lbm_ensemble* e, int64_t n_steps) {
   }
   for (lbm_ctx* c : e->members) c->step = step0 + n_steps;
   // the members' later work comes after the ensemble's
-  cudaError_t r = cudaEventRecord(e->order, e->stream);
+  cudaError_t r = cudaEventRecord(e->ord_ev, e->stream);
   for (cudaStream_t ms : e->member_streams)
-    if (r == cudaSuccess) r = cudaStreamWaitEvent(ms, e->order, 0);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(ms, e->ord_ev, 0);
   if (r != cudaSuccess) return ens_cuda(e, r, "ensemble ordering");
   return LBM_OK;
 }
