@@ -232,6 +232,74 @@ def max_over_ranks(ws, v):
     return float(t.item())
 
 
+def ensemble_members(seed=0, count=256):
+    """Config-4 family: radius U(6,24), length U(64,512), Eh/r0 log-U(0.05,5),
+    inlet period U(1000,5000), tau U(0.55,1.0); F = 0.85, parabolic pulsatile
+    inlet 0.02 + 0.01 sin(2 pi n / T)."""
+    import lbm_inputs as I
+    out = []
+    for prm in I.tube_ensemble(seed=seed, count=count):
+        geo = I.tube(prm["radius"], prm["length"], u_mean=0.02, u_amp=0.01, period=prm["period"])
+        out.append((geo, prm["tau"], prm["kappa"]))
+    return out
+
+
+def run_ensemble(args):
+    """Batched ensemble (256 uneven tubes): one launch per step kernel for all
+    members, autotuned schedule, FP16S storage; compared with the same tubes
+    in FP32, batched and stepped one lattice at a time."""
+    import torch
+    from paper_2108_08783_gb300 import Ensemble, Lattice
+    members = ensemble_members()
+
+    def build(storage):
+        lats = []
+        for geo, tau, kappa in members:
+            lat = Lattice(geo.labels, geo.iolets, storage=storage, tau=tau)
+            lat.set_wall("elastic", rho0=1.0, F=0.85, kappa=kappa)
+            lats.append(lat)
+        return lats
+
+    def timed(fn, stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    out = {}
+    for storage in ("f16s", "f32"):
+        lats = build(storage)
+        n = sum(l.n for l in lats)
+        ens = Ensemble(lats)
+        best, trials = ens.autotune()
+        ens.step(args.warmup)
+        ms = timed(lambda: ens.step(args.steps), ens.stream)
+        ens.sync()
+        out[storage] = {"batched_mlups": n * args.steps / ms / 1e3, "autotuned": best,
+                        "ms_per_step": ms / args.steps}
+        ens.close()
+        if storage == "f32":
+            k = max(4, args.steps // 50)
+            ms1 = timed(lambda: [l.step(1) for _ in range(k) for l in lats], lats[0].stream)
+            out["f32"]["one_at_a_time_mlups"] = n * k / ms1 / 1e3
+        for l in lats:
+            l.close()
+    line = {
+        "metric": METRIC, "value": out["f16s"]["batched_mlups"], "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": out["f16s"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ensemble of 256 seeded elastic tubes (%d sites), FP16S storage"
+                   % n, "sites": n},
+        "ensemble": out,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -384,7 +452,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES))
-    ap.add_argument("--config", default="tube40", choices=["tube40", "tree", "tube8"])
+    ap.add_argument("--config", default="tube40", choices=["tube40", "tree", "tube8", "ensemble"])
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -396,6 +464,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "ensemble":
+        run_ensemble(args)
     else:
         run_ours(args)
 
