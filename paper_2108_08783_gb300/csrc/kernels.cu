@@ -339,13 +339,6 @@ __device__ __forceinline__ C dir_tab(int row, int i) {
   else return c_dir_f[row][i];
 }
 
-// Shifted equilibrium of direction j (run time), as geq<j>.
-template <class C>
-__device__ __forceinline__ C geq_rt(int j, C drho, C rho, C ux, C uy, C uz, C usq) {
-  const C cu = dir_tab<C>(0, j) * ux + dir_tab<C>(1, j) * uy + dir_tab<C>(2, j) * uz;
-  return dir_tab<C>(3, j) * (drho + rho * (C(3) * cu + C(4.5) * cu * cu - usq));
-}
-
 // Collision, boundary rule and stores of a boundary site with pre-collision
 // populations g.  smask, iom: the site's link masks; Fw, Kw: its wall
 // parameters; pr0..pr2: its inlet profile (p0, ps, pc); nbr_s: the staged
@@ -387,32 +380,28 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   });
   uint32_t nf = smask & kDirBits;
   if (!nf) return;
-  // Elastic wall velocity (Sec. 2.3-2.4): the tube-law expansion dE and the
-  // distance dr = dx + dE in FP64; the ratio U_w/u_f = (F + dr - dx)/dr in the
-  // compute type (FP64 throughput is low on this GPU and the ratio only
-  // scales an FP32 velocity on the FP32 paths).
-  C uwx = C(0), uwy = C(0), uwz = C(0);
+  // Elastic wall (Sec. 2.3-2.4): the tube-law expansion dE in FP64, and the
+  // ratio sw = U_w/u_f = (F + dr - dx)/dr with dr = dx + dE in the compute
+  // type (FP64 throughput is low on this GPU and the ratio only scales an FP32
+  // velocity on the FP32 paths).  U_w = sw u.
+  C sw = C(0);
   if ((smask & kHasWall) && p.elastic) {
     // Kw holds kappa c_s^2 = kappa / 3, so dE = Kw max(0, rho - rho0)
     const double dp = (double)m.rho - p.rho0;
     const double dE = Kw * (dp > 0.0 ? dp : 0.0);
-    C sc;
     if constexpr (std::is_same<C, double>::value) {
       const double dr = 1.0 + dE;
-      sc = (Fw + dr - 1.0) / dr;
+      sw = (Fw + dr - 1.0) / dr;
     } else {
       const float e = (float)dE;
-      sc = (float(Fw) + e) * recip(1.0f + e);
+      sw = (float(Fw) + e) * recip(1.0f + e);
     }
-    uwx = sc * m.ux;
-    uwy = sc * m.uy;
-    uwz = sc * m.uz;
     if (p.write_state) {
       const int64_t ss = d.slot_stride;
       d.slot_dE[slot] = dE;  // dE of this step; dr = 1 + dE
-      d.slot_Uw[slot] = (double)uwx;
-      d.slot_Uw[ss + slot] = (double)uwy;
-      d.slot_Uw[2 * ss + slot] = (double)uwz;
+      d.slot_Uw[slot] = (double)(sw * m.ux);
+      d.slot_Uw[ss + slot] = (double)(sw * m.uy);
+      d.slot_Uw[2 * ss + slot] = (double)(sw * m.uz);
     }
   }
   // Inlet velocity (Sec. 3): u_in = a (u_mean p0 + u_amp (ps sin th + pc cos th)).
@@ -443,6 +432,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
     uiy = C(gval * io.axis[1]);
     uiz = C(gval * io.axis[2]);
   }
+  const C uisq = C(1.5) * (uix * uix + uiy * uiy + uiz * uiz);
   // Links that leave the fluid: the population of direction j = opp(i) that
   // the site receives at the next step is rebuilt here and written to its own
   // slot (x, j) - half-way bounce-back f*_i, or the GZS form
@@ -459,21 +449,31 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
                        : __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
     else
       c = ((iom >> i) & 1u) ? io_code : -1;
+    // c_j . u and the shifted equilibria share one read of the direction table
+    const C cx = dir_tab<C>(0, j), cy = dir_tab<C>(1, j), cz = dir_tab<C>(2, j);
+    const C wj = dir_tab<C>(3, j);
+    const C cu = cx * m.ux + cy * m.uy + cz * m.uz;
+    const C quad = C(4.5) * cu * cu - m.usq;
     C val;
     if (c == -1 && !p.elastic) {
+      // f*_i, with c_i = -c_j
       const C gi = gsm[i * kTile + lane];
-      val = gi + omega * (geq_rt<C>(i, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - gi);
+      val = gi + omega * (wj * (m.drho + m.rho * (quad - C(3) * cu)) - gi);
     } else {
-      const C fneq = gsm[j * kTile + lane] - geq_rt<C>(j, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
+      const C fneq = gsm[j * kTile + lane] - wj * (m.drho + m.rho * (quad + C(3) * cu));
       C e;
       if (c == -1) {
-        e = geq_rt<C>(j, m.drho, m.rho, uwx, uwy, uwz, C(1.5) * (uwx * uwx + uwy * uwy + uwz * uwz));
+        const C cw = sw * cu;  // c_j . U_w
+        e = wj * (m.drho + m.rho * (C(3) * cw + sw * sw * quad));
       } else {
         const IoletDev& io = d.iolets[-2 - c];
-        if (io.kind == LBM_IOLET_VELOCITY)
-          e = geq_rt<C>(j, m.drho, m.rho, uix, uiy, uiz, C(1.5) * (uix * uix + uiy * uiy + uiz * uiz));
-        else
-          e = geq_rt<C>(j, C(io.rho - 1.0), C(io.rho), m.ux, m.uy, m.uz, m.usq);
+        if (io.kind == LBM_IOLET_VELOCITY) {
+          const C ci = cx * uix + cy * uiy + cz * uiz;
+          e = wj * (m.drho + m.rho * (C(3) * ci + C(4.5) * ci * ci - uisq));
+        } else {
+          const C rb = C(io.rho);
+          e = wj * (C(io.rho - 1.0) + rb * (quad + C(3) * cu));
+        }
       }
       val = e + keep * fneq;
     }
