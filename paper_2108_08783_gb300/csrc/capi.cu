@@ -236,7 +236,6 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   d.pop = dev_alloc<unsigned char>(c, (size_t)lbm::kQ * d.npad * sz);
   lbm::TileDesc* td = dev_alloc<lbm::TileDesc>(c, L.tiles.size());
   lbm::LaunchDesc* to = dev_alloc<lbm::LaunchDesc>(c, L.launch.size());
-  double* tom = dev_alloc<double>(c, L.launch.size());
   uint32_t* sm = dev_alloc<uint32_t>(c, S);
   uint32_t* sio = dev_alloc<uint32_t>(c, S);
   int32_t* sn = dev_alloc<int32_t>(c, 18 * S);
@@ -251,7 +250,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   c->iolet_sites = dev_alloc<int64_t>(c, L.iolet_sites.size());
   c->partial = dev_alloc<double>(c, lbm::reduce_partials());
   c->red_out = dev_alloc<double>(c, 1 + n_iolets);
-  if (!d.pop || !td || !to || !tom || !sm || !sio || !sn || !sp || !sF || !sK || !sdE || !sUw ||
+  if (!d.pop || !td || !to || !sm || !sio || !sn || !sp || !sF || !sK || !sdE || !sUw ||
       !io || !err || !c->iolet_off || !c->iolet_sites || !c->partial || !c->red_out) {
     g_build_err = "device allocation failed";
     lbm_destroy(c);
@@ -259,7 +258,6 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   }
   d.tiles = td;
   d.launch = to;
-  d.tile_omega = tom;
   d.slot_mask = sm;
   d.slot_io = sio;
   d.slot_nbr = sn;
@@ -289,11 +287,6 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   chk(h2d(c, td, L.tiles.data(), L.tiles.size()));
   chk(h2d(c, to, L.launch.data(), L.launch.size()));
-  {
-    std::vector<double> om(L.launch.size(), 1.0 / tau);
-    chk(h2d(c, tom, om.data(), om.size()));
-    chk(cudaStreamSynchronize(c->stream));  // om is a temporary
-  }
   chk(h2d(c, sm, L.slot_mask.data(), S));
   chk(h2d(c, sio, L.slot_io.data(), S));
   chk(h2d(c, sn, L.slot_nbr.data(), 18 * S));
@@ -401,6 +394,7 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
   if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps must be >= 0");
   lbm::StepParams p;
   p.rho0 = c->rho0;
+  p.omega = 1.0 / c->tau;
   p.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
   p.prefetch = c->prefetch;
   p.step_dev = nullptr;
@@ -769,6 +763,7 @@ int ens_upload(lbm_ensemble* e) {
     lbm::MemberDev& md = tab[q];
     std::memset(&md, 0, sizeof md);
     md.d = c->d;
+    md.omega = 1.0 / c->tau;
     md.rho0 = c->rho0;
     md.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
     pre[q + 1] = pre[q] + (c->d.n_tiles - c->d.n_boundary);

@@ -497,10 +497,9 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
     bulk_prefetch_l2(static_cast<const S*>(d.pop) + lane * d.npad + tp * kTile,
                      kTile * sizeof(S));
   }
-  const double omega = __ldg(d.tile_omega + k);
   __syncwarp();
   const int64_t x = (int64_t)dsc[19] * kTile + lane;
-  if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, omega, d.err);
+  if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p.omega, d.err);
 }
 
 template <class S, bool ODD>
@@ -528,7 +527,6 @@ __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepPar
   // per-site data and the descriptor, all in one round trip
   const uint32_t smask = __ldg(d.slot_mask + slot);
   const uint32_t iom = __ldg(d.slot_io + slot);
-  const double omega = __ldg(d.tile_omega + k);
   if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
   __syncwarp();
   const uint32_t tmask = (uint32_t)dsc[18];
@@ -570,7 +568,7 @@ __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepPar
     if (valid) boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, true, nbr_s, lane, g);
   }
   if (!valid) return;
-  boundary_update<S, ODD>(d, p, omega, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s,
+  boundary_update<S, ODD>(d, p, p.omega, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s,
                           lane, slot, g, gsm);
 }
 
@@ -610,8 +608,10 @@ __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK
   const int64_t g = (int64_t)blockIdx.x * kBulkWarps + w;
   if (g >= e.n_bulk_tiles) return;  // warp-uniform
   const int m = find_member(e.bulk_prefix, e.n_members, g);
-  const DevLattice& d = e.mem[m].d;
-  bulk_tile<S, ODD>(d, p, d.n_boundary + (g - __ldg(e.bulk_prefix + m)), desc_s[w], lane);
+  const MemberDev& md = e.mem[m];
+  StepParams pm = p;
+  pm.omega = md.omega;
+  bulk_tile<S, ODD>(md.d, pm, md.d.n_boundary + (g - __ldg(e.bulk_prefix + m)), desc_s[w], lane);
 }
 
 template <class S, bool ODD>
@@ -628,6 +628,7 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
   const int m = find_member(e.boundary_prefix, e.n_members, g);
   const MemberDev& md = e.mem[m];
   StepParams pm = p;
+  pm.omega = md.omega;
   pm.rho0 = md.rho0;
   pm.elastic = md.elastic;
   boundary_tile<S, ODD>(md.d, pm, g - __ldg(e.boundary_prefix + m), desc_s[w], stage[w], &bars[w],

@@ -113,7 +113,6 @@ struct DevLattice {
   int64_t n = 0;
   const TileDesc* tiles = nullptr;
   const LaunchDesc* launch = nullptr;  // boundary tiles (ascending), then bulk tiles
-  const double* tile_omega = nullptr;  // [n_tiles] 1/tau of each tile, launch order
   int64_t n_tiles = 0;
   const uint32_t* slot_mask = nullptr;
   const uint32_t* slot_io = nullptr;
@@ -131,6 +130,7 @@ struct DevLattice {
 };
 
 struct StepParams {
+  double omega;      // 1 / tau
   double rho0;
   int32_t elastic;   // 1: elastic GZS wall, 0: bounce-back
   int32_t write_state;
@@ -142,6 +142,7 @@ struct StepParams {
 // One member of an ensemble: its device view and its wall constants.
 struct MemberDev {
   DevLattice d;
+  double omega;
   double rho0;
   int32_t elastic;
   int32_t pad;
