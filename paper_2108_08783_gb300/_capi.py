@@ -17,7 +17,7 @@ LBM_WALL_BOUNCEBACK, LBM_WALL_ELASTIC_GZS = 0, 1
 LBM_IOLET_VELOCITY, LBM_IOLET_DENSITY = 0, 1
 LBM_PROFILE_PARABOLIC, LBM_PROFILE_WOMERSLEY, LBM_PROFILE_PLUG = 0, 1, 2
 
-# Every symbol include/lbm.h declares.
+# Every symbol include/lbm.h and include/lbm_mlp.h declare.
 EXPORTS = (
     "lbm_build_lattice", "lbm_set_wall_params", "lbm_init_fields", "lbm_step", "lbm_moments",
     "lbm_sync", "lbm_info", "lbm_export_lattice", "lbm_wall_state", "lbm_reduce",
@@ -26,6 +26,10 @@ EXPORTS = (
     "lbm_destroy", "lbm_profile", "lbm_profile_read", "lbm_reduce_noalloc",
     "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_sync", "lbm_ensemble_tune",
     "lbm_ensemble_last_error", "lbm_ensemble_destroy",
+    # include/lbm_mlp.h
+    "lbm_mlp_create", "lbm_mlp_param_count", "lbm_mlp_set_params", "lbm_mlp_get_params",
+    "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train_step", "lbm_mlp_sync",
+    "lbm_mlp_last_error", "lbm_mlp_destroy", "lbm_warm_features", "lbm_warm_start",
 )
 LBM_TUNE_PREFETCH, LBM_TUNE_SCHEDULE, LBM_TUNE_GRAPH_STEPS = 0, 1, 2
 
@@ -43,6 +47,21 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 class LbmAllocator(C.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+LBM_WARM_MAX_GLOBAL = 14
+
+
+class LbmAdam(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("eps", C.c_double)]
+
+
+class LbmWarmFrame(C.Structure):
+    _fields_ = [("centre", C.c_double * 3), ("axis", C.c_double * 3), ("z0", C.c_double),
+                ("length", C.c_double), ("radius", C.c_double), ("rho_scale", C.c_double),
+                ("u_scale", C.c_double), ("n_global", C.c_int32),
+                ("global_", C.c_float * LBM_WARM_MAX_GLOBAL)]
 
 
 class LbmError(RuntimeError):
@@ -94,6 +113,18 @@ def lib():
         "lbm_ensemble_tune": ([P, i32, i64], C.c_int),
         "lbm_ensemble_last_error": ([P], C.c_char_p),
         "lbm_ensemble_destroy": ([P], None),
+        "lbm_mlp_create": ([i32, i32, i32, i32, i64, P, P, C.POINTER(P)], C.c_int),
+        "lbm_mlp_param_count": ([P, P], C.c_int),
+        "lbm_mlp_set_params": ([P, P, i32], C.c_int),
+        "lbm_mlp_get_params": ([P, P, i32], C.c_int),
+        "lbm_mlp_forward": ([P, P, i64, P], C.c_int),
+        "lbm_mlp_loss_grad": ([P, P, P, i64, P, P, i32], C.c_int),
+        "lbm_mlp_train_step": ([P, P, P, i64, P, P], C.c_int),
+        "lbm_mlp_sync": ([P], C.c_int),
+        "lbm_mlp_last_error": ([P], C.c_char_p),
+        "lbm_mlp_destroy": ([P], None),
+        "lbm_warm_features": ([P, P, P, P], C.c_int),
+        "lbm_warm_start": ([P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -1,6 +1,6 @@
 """Build ``liblbm.so`` (the C-ABI library of ``include/lbm.h``) in place for sm_103a.
 
-The three translation units are compiled in parallel with nvcc (one
+The four translation units are compiled in parallel with nvcc (one
 ``-gencode`` for sm_103a, ``-lineinfo`` for profiling) and linked into a
 shared object next to this file, with the CUDA runtime linked statically.
 """
@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblbm.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["lattice_build.cpp", "kernels.cu", "capi.cu"]
+SOURCES = ["lattice_build.cpp", "kernels.cu", "capi.cu", "mlp.cu"]
 HEADERS = ["lbm_internal.h", "d3q19.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -22,6 +22,7 @@ NVCC = os.environ.get("NVCC", "nvcc")
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES + HEADERS]
     files.append(os.path.join(HERE, "..", "include", "lbm.h"))
+    files.append(os.path.join(HERE, "..", "include", "lbm_mlp.h"))
     files.append(os.path.abspath(__file__))
     return files
 

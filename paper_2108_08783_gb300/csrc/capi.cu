@@ -51,6 +51,7 @@ struct lbm_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   size_t ev_used = 0;
+  int32_t* coords_dev = nullptr;  // [n][3] voxel coordinates, uploaded on first use (warm start)
 };
 
 namespace {
@@ -968,6 +969,108 @@ int lbm_ensemble_sync(lbm_ensemble* e) {
     if (rc != LBM_OK) return ens_fail(e, rc, c->err);
   }
   return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- warm start
+// Learned initial fields (include/lbm_mlp.h); no counterpart in the paper.
+
+namespace {
+
+int warm_frame(lbm_ctx* c, const lbm_warm_frame* f, lbm_warm_frame* out) {
+  if (!f) return fail(c, LBM_EINVAL, "warm start: NULL frame");
+  const double a = std::sqrt(f->axis[0] * f->axis[0] + f->axis[1] * f->axis[1] +
+                             f->axis[2] * f->axis[2]);
+  if (!(a > 0.0) || !(f->length > 0.0) || !(f->radius > 0.0) || f->n_global < 0 ||
+      f->n_global > LBM_WARM_MAX_GLOBAL || !(f->rho_scale != 0.0) || !(f->u_scale != 0.0) ||
+      !std::isfinite(f->rho_scale) || !std::isfinite(f->u_scale))
+    return fail(c, LBM_EINVAL, "warm start: invalid frame");
+  *out = *f;
+  for (int k = 0; k < 3; ++k) out->axis[k] = f->axis[k] / a;
+  return LBM_OK;
+}
+
+int warm_coords(lbm_ctx* c) {
+  if (c->coords_dev) return LBM_OK;
+  int32_t* p = dev_alloc<int32_t>(c, c->L.coords.size());
+  if (!p) return fail(c, LBM_ENOMEM, "warm start: coordinate allocation");
+  cudaError_t e = h2d(c, p, c->L.coords.data(), c->L.coords.size());
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "warm start: coordinate copy");
+  c->coords_dev = p;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_warm_features(lbm_ctx* c, const lbm_warm_frame* frame, float* x, float* t) {
+  if (!c) return LBM_EINVAL;
+  c->err.clear();
+  lbm_warm_frame f;
+  int rc = warm_frame(c, frame, &f);
+  if (rc != LBM_OK) return rc;
+  if (!x) return fail(c, LBM_EINVAL, "lbm_warm_features: NULL x");
+  if ((rc = warm_coords(c)) != LBM_OK) return rc;
+  const size_t n = (size_t)c->L.n;
+  Temp tr(c, t ? n * sizeof(double) : 0), tu(c, t ? 3 * n * sizeof(double) : 0);
+  if (t && (!tr.p || !tu.p)) return fail(c, LBM_ENOMEM, "lbm_warm_features: allocation");
+  if (t) {
+    rc = check_launch(c, lbm::launch_moments(c->storage, c->d, odd_layout(c), (double*)tr.p,
+                                             (double*)tu.p, c->stream),
+                      "moments kernel");
+    if (rc != LBM_OK) return rc;
+  }
+  rc = check_launch(c, lbm::launch_warm_features(c->coords_dev, (int64_t)n, f, (double*)tr.p,
+                                                 (double*)tu.p, x, t, c->stream),
+                    "warm feature kernel");
+  if (rc == LBM_OK) rc = sync(c, "lbm_warm_features");
+  return rc;
+}
+
+int lbm_warm_start(lbm_ctx* c, lbm_mlp* net, const lbm_warm_frame* frame) {
+  if (!c) return LBM_EINVAL;
+  c->err.clear();
+  if (!net) return fail(c, LBM_EINVAL, "lbm_warm_start: NULL network");
+  lbm_warm_frame f;
+  int rc = warm_frame(c, frame, &f);
+  if (rc != LBM_OK) return rc;
+  int n_in = 0, n_out = 0;
+  void* ns = nullptr;
+  lbm::mlp_shape(net, &n_in, &n_out, &ns);
+  if (n_in != f.n_global + 2 || n_out != 3)
+    return fail(c, LBM_EINVAL, "lbm_warm_start: network needs n_in = n_global + 2, n_out = 3");
+  if ((rc = warm_coords(c)) != LBM_OK) return rc;
+  // The network's buffers are used on this context's stream: let its own
+  // queued work finish first.
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(ns));
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_warm_start: network stream");
+  const size_t n = (size_t)c->L.n;
+  Temp tx(c, n * n_in * sizeof(float)), ty(c, n * 3 * sizeof(float));
+  Temp tr(c, n * sizeof(double)), tu(c, 3 * n * sizeof(double));
+  if (!tx.p || !ty.p || !tr.p || !tu.p) return fail(c, LBM_ENOMEM, "lbm_warm_start: allocation");
+  rc = check_launch(c, lbm::launch_warm_features(c->coords_dev, (int64_t)n, f, nullptr, nullptr,
+                                                 (float*)tx.p, nullptr, c->stream),
+                    "warm feature kernel");
+  if (rc == LBM_OK)
+    rc = check_launch(c, lbm::mlp_forward_on(net, (const float*)tx.p, (int64_t)n, (float*)ty.p,
+                                             c->stream),
+                      "network forward");
+  if (rc == LBM_OK)
+    rc = check_launch(c, lbm::launch_warm_fields(c->coords_dev, (int64_t)n, f,
+                                                 (const float*)ty.p, (double*)tr.p,
+                                                 (double*)tu.p, c->stream),
+                      "warm field kernel");
+  if (rc == LBM_OK)
+    rc = check_launch(c, lbm::launch_init(c->storage, c->d, (double*)tr.p, (double*)tu.p,
+                                          c->stream),
+                      "init kernel");
+  const int rs = sync(c, "lbm_warm_start");
+  if (rc == LBM_OK) rc = rs;
+  if (rc == LBM_OK) c->step = 0;
+  return rc;
 }
 
 }  // extern "C"

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "../../include/lbm_mlp.h"
 
 namespace lbm {
 
@@ -191,6 +192,16 @@ int launch_wss(int storage, const DevLattice& d, int odd_layout, double tau,
                const int64_t* sites, const double* normals, int64_t m, double* out,
                void* stream);
 size_t storage_bytes(int storage);
+
+// Learned warm start (mlp.cu): the network's forward pass on a given stream
+// (n rows in chunks of its batch size, using its activation buffers), its
+// shape and stream, and the per-site feature / field kernels.
+int mlp_forward_on(lbm_mlp* net, const float* x, int64_t n, float* y, void* stream);
+void mlp_shape(const lbm_mlp* net, int* n_in, int* n_out, void** stream);
+int launch_warm_features(const int32_t* coords, int64_t n, const lbm_warm_frame& f,
+                         const double* rho, const double* u, float* x, float* t, void* stream);
+int launch_warm_fields(const int32_t* coords, int64_t n, const lbm_warm_frame& f, const float* y,
+                       double* rho, double* u, void* stream);
 
 int reduce_partials();
 

@@ -164,6 +164,21 @@ class Lattice:
         self._check(self._lib.lbm_moments(self.h, C.c_void_p(rho.data_ptr()),
                                           C.c_void_p(u.data_ptr()), 1))
 
+    def warm_features(self, frame, targets=True):
+        """Per-site features x [n][n_global + 2] and (optionally) targets t [n][3]
+        from the current fields, as device tensors (``lbm_warm_features``)."""
+        import torch
+        x = torch.empty((self.n, frame.n_global + 2), dtype=torch.float32, device=self.device)
+        t = torch.empty((self.n, 3), dtype=torch.float32, device=self.device) if targets else None
+        self._check(self._lib.lbm_warm_features(self.h, C.byref(frame), C.c_void_p(x.data_ptr()),
+                                                C.c_void_p(t.data_ptr()) if targets else None))
+        return x, t
+
+    def warm_start(self, net, frame):
+        """Initial fields proposed by the network ``net`` (an MLP) for this
+        lattice, f = f^eq(rho, u) (``lbm_warm_start``)."""
+        self._check(self._lib.lbm_warm_start(self.h, net.h, C.byref(frame)))
+
     def export(self):
         coords = np.zeros((self.n, 3), np.int32)
         nbr = np.zeros((self.n, 18), np.int32)

@@ -26,9 +26,12 @@ def capi():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for h in ("lbm.h", "lbm_mlp.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_north_star_calls():
