@@ -259,6 +259,21 @@ int lbm_ensemble_tune(lbm_ensemble *ens, int32_t knob, int64_t value);
 const char *lbm_ensemble_last_error(const lbm_ensemble *ens);
 void lbm_ensemble_destroy(lbm_ensemble *ens);
 
+/* lbm_fmap - host precompute of the wall-velocity ratio F of Sec. 2.3 (Eq. F),
+ * the ratio of the oscillating axial velocity of elastic-tube Womersley flow
+ * (Sec. 2.2) at the displaced wall r = R to that at the fluid node
+ * r = R - dr:
+ *   F(alpha, dr/R) = (1 - M) / (1 - M J0(Lambda (1 - dr/R)) / J0(Lambda)),
+ *   Lambda = i^(3/2) alpha,
+ * with the elastic-tube coefficient M = M_re + i M_im supplied by the caller
+ * (the paper does not fix it).  out [n_alpha][n_dr][2] host: (Re F, Im F) for
+ * every alpha[a] in [0, 25] and dr_over_R[b] in [0, 1); the magnitude |F| is
+ * the real ratio a caller passes to lbm_set_wall_params.  A pair whose
+ * denominator vanishes (dr = 0 with M = 1) gives NaN.  LBM_EINVAL for
+ * arguments out of range.  Runs on the host; no context, no GPU. */
+int lbm_fmap(const double *alpha, int64_t n_alpha, const double *dr_over_R, int64_t n_dr,
+             double M_re, double M_im, double *out);
+
 /* lbm_set_stream - run subsequent work on another cudaStream_t. */
 int lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
 

@@ -26,9 +26,9 @@
 
 namespace lbm {
 
-namespace {
-
 using cplx = std::complex<double>;
+
+namespace {
 
 // Bessel J0 and J1 of complex argument from their integral representations
 //   J0(z) = (1/pi) int_0^pi cos(z sin t) dt,  J1(z) = (1/pi) int_0^pi cos(t - z sin t) dt,
@@ -313,3 +313,35 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
 }
 
 }  // namespace lbm
+
+// --------------------------------------------------------------- F map
+// Host precompute of F (Sec. 2.3, Eq. F) over a grid of (alpha, dr/R).
+
+extern "C" int lbm_fmap(const double* alpha, int64_t n_alpha, const double* dr_over_R,
+                        int64_t n_dr, double M_re, double M_im, double* out) {
+  using lbm::cplx;
+  if (n_alpha < 0 || n_dr < 0 || ((n_alpha > 0 && n_dr > 0) && (!alpha || !dr_over_R || !out)) ||
+      !std::isfinite(M_re) || !std::isfinite(M_im))
+    return LBM_EINVAL;
+  for (int64_t a = 0; a < n_alpha; ++a)
+    if (!(alpha[a] >= 0.0 && alpha[a] <= 25.0)) return LBM_EINVAL;
+  for (int64_t b = 0; b < n_dr; ++b)
+    if (!(dr_over_R[b] >= 0.0 && dr_over_R[b] < 1.0)) return LBM_EINVAL;
+  const cplx M(M_re, M_im);
+  for (int64_t a = 0; a < n_alpha; ++a) {
+    const cplx lam = alpha[a] * std::exp(cplx(0.0, 0.75 * M_PI));
+    cplx j0L, j1L;
+    lbm::bessel01(lam, j0L, j1L);
+    for (int64_t b = 0; b < n_dr; ++b) {
+      cplx j0r, j1r;
+      lbm::bessel01(lam * (1.0 - dr_over_R[b]), j0r, j1r);
+      const cplx den = 1.0 - M * j0r / j0L;
+      cplx F;
+      if (std::abs(den) == 0.0) F = cplx(NAN, NAN);
+      else F = (1.0 - M) / den;
+      out[2 * (a * n_dr + b)] = F.real();
+      out[2 * (a * n_dr + b) + 1] = F.imag();
+    }
+  }
+  return LBM_OK;
+}
