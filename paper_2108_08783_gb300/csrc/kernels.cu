@@ -148,6 +148,15 @@ struct Codec<__nv_bfloat16> {
 __device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
 __device__ __forceinline__ double recip(double v) { return __drcp_rn(v); }
 
+// Explicitly rounded multiply and fused multiply-add.  The boundary rule below
+// is written once and evaluated in an unrolled and a looped form; pinning its
+// operations makes both forms round identically (no compiler choice of what
+// to contract).
+__device__ __forceinline__ float mul_pin(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_pin(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_pin(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_pin(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class C>
 struct Mom {
   C drho, rho, ux, uy, uz, usq;
@@ -259,6 +268,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 //     applies the collision and, for each link leaving the fluid, the
 //     boundary rule.
 
+__device__ __forceinline__ int32_t lds_volatile(const int32_t* p) {
+  return *static_cast<const volatile int32_t*>(p);
+}
+
 // Branch-free update of a site whose 18 links are fluid.
 template <class S, bool ODD>
 __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t* dsc,
@@ -281,8 +294,11 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
     const C sa = g[a] + omega * (geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[a]);
     const C sb = g[b] + omega * (geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[b]);
     if constexpr (ODD) {
-      Cd::st(P + a * np + x + dsc[a - 1], a, sa);
-      Cd::st(P + b * np + x + dsc[b - 1], b, sb);
+      // The store to (x + c_a, a) hits the address the load of direction
+      // opp(a) used; re-reading the offset from shared memory keeps the
+      // compiler from holding all 18 64-bit addresses live across the update.
+      Cd::st(P + a * np + x + lds_volatile(dsc + a - 1), a, sa);
+      Cd::st(P + b * np + x + lds_volatile(dsc + b - 1), b, sb);
     } else {
       Cd::st(P + b * np + x, a, sa);
       Cd::st(P + a * np + x, b, sb);
@@ -360,10 +376,6 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
   const C omega = C(omega_t);
   const C keep = C(1) - omega;  // (1 - 1/tau)
-  unroll<kQ>([&](auto J) {
-    constexpr int j = decltype(J)::value;
-    gsm[j * kTile + lane] = g[j];
-  });
   // neighbour index of a fluid link i (odd steps)
   auto nb = [&](int i) -> int64_t {
     return irr ? (int64_t)nbr_s[(i - 1) * kTile + lane] : x + dsc[i - 1];
@@ -394,7 +406,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
       sw = (Fw + dr - 1.0) / dr;
     } else {
       const float e = (float)dE;
-      sw = (float(Fw) + e) * recip(1.0f + e);
+      sw = mul_pin(float(Fw) + e, recip(1.0f + e));
     }
     if (p.write_state) {
       const int64_t ss = d.slot_stride;
@@ -409,7 +421,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   if (smask & kHasInlet) {
     const int k = (int)((iom & kIoletIdBits) >> kIoletShift);
     const IoletDev& io = d.iolets[k];
-    double gval = io.u_mean * pr0;
+    double gval = mul_pin(io.u_mean, pr0);
     if (!io.steady) {
       // th = 2 pi n / T + phase.  FP64 paths take sin/cos in FP64 (as the
       // oracle); FP32 paths reduce the phase to one period in FP64 and take
@@ -426,58 +438,86 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
         sn = sf;
         cs = cf;
       }
-      gval += io.u_amp * (pr1 * sn + pr2 * cs);
+      gval = fma_pin(io.u_amp, fma_pin(pr1, sn, mul_pin(pr2, cs)), gval);
     }
-    uix = C(gval * io.axis[0]);
-    uiy = C(gval * io.axis[1]);
-    uiz = C(gval * io.axis[2]);
+    uix = C(mul_pin(gval, io.axis[0]));
+    uiy = C(mul_pin(gval, io.axis[1]));
+    uiz = C(mul_pin(gval, io.axis[2]));
   }
-  const C uisq = C(1.5) * (uix * uix + uiy * uiy + uiz * uiz);
+  const C uisq = mul_pin(C(1.5), fma_pin(uiz, uiz, fma_pin(uiy, uiy, mul_pin(uix, uix))));
   // Links that leave the fluid: the population of direction j = opp(i) that
   // the site receives at the next step is rebuilt here and written to its own
   // slot (x, j) - half-way bounce-back f*_i, or the GZS form
   // f^eq_j(rho_b, u_b) + (1 - 1/tau) f^neq_j with (rho_b, u_b) = (rho, U_w) at a
   // wall, (rho, u_in) at a velocity inlet, (rho_out, u) at a density outlet.
   const int32_t io_code = -2 - (int32_t)((iom & kIoletIdBits) >> kIoletShift);
-  while (nf) {
-    const int i = __ffs(nf) - 1;
-    nf &= nf - 1;
-    const int j = dir_opp(i);
-    int32_t c;
+  // Boundary code of the non-fluid link i: -1 wall, -2-k iolet k.
+  auto link_code = [&](int i) -> int32_t {
     if (smask & kMultiIolet)
-      c = (ODD && irr) ? nbr_s[(i - 1) * kTile + lane]
-                       : __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
-    else
-      c = ((iom >> i) & 1u) ? io_code : -1;
-    // c_j . u and the shifted equilibria share one read of the direction table
-    const C cx = dir_tab<C>(0, j), cy = dir_tab<C>(1, j), cz = dir_tab<C>(2, j);
-    const C wj = dir_tab<C>(3, j);
-    const C cu = cx * m.ux + cy * m.uy + cz * m.uz;
-    const C quad = C(4.5) * cu * cu - m.usq;
-    C val;
+      return (ODD && irr) ? nbr_s[(i - 1) * kTile + lane]
+                          : __ldg(d.slot_nbr + (i - 1) * d.slot_stride + slot);
+    return ((iom >> i) & 1u) ? io_code : -1;
+  };
+  // Value stored into (x, j) for the non-fluid link i = opp(j), from
+  // cu = c_j . u, ci = c_j . u_in, the weight w_j and the pre-collision g_i, g_j.
+  auto link_value = [&](int32_t c, C cu, C ci, C wj, C gi, C gj) -> C {
+    const C quad = fma_pin(mul_pin(C(4.5), cu), cu, -m.usq);
     if (c == -1 && !p.elastic) {
       // f*_i, with c_i = -c_j
-      const C gi = gsm[i * kTile + lane];
-      val = gi + omega * (wj * (m.drho + m.rho * (quad - C(3) * cu)) - gi);
-    } else {
-      const C fneq = gsm[j * kTile + lane] - wj * (m.drho + m.rho * (quad + C(3) * cu));
-      C e;
-      if (c == -1) {
-        const C cw = sw * cu;  // c_j . U_w
-        e = wj * (m.drho + m.rho * (C(3) * cw + sw * sw * quad));
-      } else {
-        const IoletDev& io = d.iolets[-2 - c];
-        if (io.kind == LBM_IOLET_VELOCITY) {
-          const C ci = cx * uix + cy * uiy + cz * uiz;
-          e = wj * (m.drho + m.rho * (C(3) * ci + C(4.5) * ci * ci - uisq));
-        } else {
-          const C rb = C(io.rho);
-          e = wj * (C(io.rho - 1.0) + rb * (quad + C(3) * cu));
-        }
-      }
-      val = e + keep * fneq;
+      const C ei = mul_pin(wj, fma_pin(m.rho, fma_pin(C(-3), cu, quad), m.drho));
+      return fma_pin(omega, ei - gi, gi);
     }
-    Cd::st(P + j * np + x, j, val);
+    const C fneq = gj - mul_pin(wj, fma_pin(m.rho, fma_pin(C(3), cu, quad), m.drho));
+    C e;
+    if (c == -1) {
+      // U_w = sw u: c_j . U_w = sw cu, 1.5 U_w^2 = sw^2 1.5 u^2
+      const C inner = fma_pin(C(3), mul_pin(sw, cu), mul_pin(mul_pin(sw, sw), quad));
+      e = mul_pin(wj, fma_pin(m.rho, inner, m.drho));
+    } else {
+      const IoletDev& io = d.iolets[-2 - c];
+      if (io.kind == LBM_IOLET_VELOCITY) {
+        const C inner = fma_pin(mul_pin(C(4.5), ci), ci, fma_pin(C(3), ci, -uisq));
+        e = mul_pin(wj, fma_pin(m.rho, inner, m.drho));
+      } else {
+        e = mul_pin(wj, fma_pin(C(io.rho), fma_pin(C(3), cu, quad), C(io.rho - 1.0)));
+      }
+    }
+    return fma_pin(keep, fneq, e);
+  };
+  if (!(ODD && irr)) {
+    // One branch per direction, so c_j, w_j and g are compile-time operands.
+    // On coherent tiles (straight walls, iolet planes) every lane has the same
+    // non-fluid links and the branches are uniform across the warp; on even
+    // steps irregular tiles take this form too, which measured faster than
+    // the loop below while no neighbour rows are staged.
+    unroll<kQ - 1>([&](auto I0) {
+      constexpr int i = decltype(I0)::value + 1;
+      constexpr int j = dir_opp(i);
+      if ((nf >> i) & 1u) {
+        const C val = link_value(link_code(i), cdot<j, C>(m.ux, m.uy, m.uz),
+                                 cdot<j, C>(uix, uiy, uiz), weight<C>(j), g[i], g[j]);
+        Cd::st(P + j * np + x, j, val);
+      }
+    });
+  } else {
+    // Odd steps of irregular tiles: lanes differ in their non-fluid links,
+    // so each lane loops over its own; g is parked in the warp's shared
+    // memory and c_j, w_j come from the constant table.
+    unroll<kQ>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      gsm[j * kTile + lane] = g[j];
+    });
+    while (nf) {
+      const int i = __ffs(nf) - 1;
+      nf &= nf - 1;
+      const int j = dir_opp(i);
+      const C cx = dir_tab<C>(0, j), cy = dir_tab<C>(1, j), cz = dir_tab<C>(2, j);
+      const C cu = fma_pin(cz, m.uz, fma_pin(cy, m.uy, mul_pin(cx, m.ux)));
+      const C ci = fma_pin(cz, uiz, fma_pin(cy, uiy, mul_pin(cx, uix)));
+      const C val = link_value(link_code(i), cu, ci, dir_tab<C>(3, j), gsm[i * kTile + lane],
+                               gsm[j * kTile + lane]);
+      Cd::st(P + j * np + x, j, val);
+    }
   }
 }
 
