@@ -233,14 +233,23 @@ def max_over_ranks(ws, v):
     return float(t.item())
 
 
+ENSEMBLE_STEPS = 2000  # timed steps of the ensemble workload (at most)
+
+
 def ensemble_members(seed=0, count=256):
     """Config-4 family: radius U(6,24), length U(64,512), Eh/r0 log-U(0.05,5),
     inlet period U(1000,5000), tau U(0.55,1.0); F = 0.85, parabolic pulsatile
-    inlet 0.02 + 0.01 sin(2 pi n / T)."""
+    inlet of mean 0.01 + 0.005 sin(2 pi n / T).
+
+    Some soft, low-tau members of this family are unstable under the elastic
+    wall: member 97 (tau 0.56, R 23.5) diverges after ~3,750 steps, in the
+    FP64 oracle as on the GPU; at twice this inflow member 252 (tau 0.554,
+    R 23.9) diverges after ~2,700 steps.  ENSEMBLE_STEPS keeps the whole
+    ensemble run (autotuning included) below that."""
     import lbm_inputs as I
     out = []
     for prm in I.tube_ensemble(seed=seed, count=count):
-        geo = I.tube(prm["radius"], prm["length"], u_mean=0.02, u_amp=0.01, period=prm["period"])
+        geo = I.tube(prm["radius"], prm["length"], u_mean=0.01, u_amp=0.005, period=prm["period"])
         out.append((geo, prm["tau"], prm["kappa"]))
     return out
 
@@ -272,16 +281,17 @@ def run_ensemble(args):
         return e0.elapsed_time(e1)
 
     out = {}
+    k_steps = min(args.steps, ENSEMBLE_STEPS)
     for storage in ("f16s", "f32"):
         lats = build(storage)
         n = sum(l.n for l in lats)
         ens = Ensemble(lats)
-        best, trials = ens.autotune()
+        best, trials = ens.autotune(trial_steps=20)
         ens.step(args.warmup)
-        ms = timed(lambda: ens.step(args.steps), ens.stream)
+        ms = timed(lambda: ens.step(k_steps), ens.stream)
         ens.sync()
-        out[storage] = {"batched_mlups": n * args.steps / ms / 1e3, "autotuned": best,
-                        "ms_per_step": ms / args.steps}
+        out[storage] = {"batched_mlups": n * k_steps / ms / 1e3, "autotuned": best,
+                        "ms_per_step": ms / k_steps}
         ens.close()
         if storage == "f32":
             k = max(4, args.steps // 50)
@@ -291,7 +301,7 @@ def run_ensemble(args):
             l.close()
     line = {
         "metric": METRIC, "value": out["f16s"]["batched_mlups"], "unit": "MLUPS", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup,
+        "steps": k_steps, "warmup": args.warmup,
         "ms_per_step": out["f16s"]["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "ensemble of 256 seeded elastic tubes (%d sites), FP16S storage"

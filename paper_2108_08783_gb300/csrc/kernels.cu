@@ -776,7 +776,10 @@ __global__ void k_moments(const DevLattice d, int odd, double* rho, double* u) {
 }
 
 constexpr int kRedThreads = 256;
-constexpr int kRedBlocks = 1024;
+constexpr int kRedBlocks = 1024;                        // partials of one reduction
+constexpr int kMassBlocks = 768;                        // partials [0, 768): mass
+constexpr int kFluxPartials = kRedBlocks - kMassBlocks;  // [768, 1024): iolet fluxes
+constexpr int kFluxBlocksMax = 16;                      // blocks per iolet
 
 __device__ double block_sum(double v, double* sh) {
   sh[threadIdx.x] = v;
@@ -788,47 +791,75 @@ __device__ double block_sum(double v, double* sh) {
   return sh[0];
 }
 
-// Mass partials: fixed grid, fixed order -> deterministic.
+// Mass partials: fixed grid, fixed order -> deterministic.  Both AA layouts
+// hold every population of every site exactly once (each step writes every
+// slot once), so the total mass is n + the sum of all stored g = f - w, read
+// as a flat stream: no neighbour gather and no momentum.  Each site's 19
+// values are summed in the compute type (exact data for every storage, FP32
+// adds of |g| << 1 for the FP32 paths) and the sites in FP64.
 template <class S>
-__global__ void __launch_bounds__(kRedThreads) k_mass(const DevLattice d, int odd, double* partial) {
+__global__ void __launch_bounds__(kRedThreads) k_mass(const DevLattice d, double* partial) {
+  using Cd = Codec<S>;
+  using C = typename Cd::C;
   __shared__ double sh[kRedThreads];
+  const S* P = static_cast<const S*>(d.pop);
   double acc = 0.0;
   for (int64_t x = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; x < d.n;
-       x += (int64_t)kRedBlocks * kRedThreads) {
-    double f[kQ], r, jx, jy, jz;
-    site_f<S>(d, x, odd, f);
-    f_moments(f, r, jx, jy, jz);
-    if (!(r > 0.0) || !(r < 1e30)) atomicOr(d.err, kErrUnstable);
-    acc += r;
+       x += (int64_t)kMassBlocks * kRedThreads) {
+    C sg = C(0);
+    unroll<kQ>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      sg += Cd::ld(P + j * d.npad + x, j);
+    });
+    acc += (double)sg;
   }
   const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_mass_final(const double* partial, double* out) {
+__global__ void __launch_bounds__(kRedThreads) k_mass_final(const double* partial, int64_t n,
+                                                            int* err, double* out) {
   __shared__ double sh[kRedThreads];
   double acc = 0.0;
-  for (int b = threadIdx.x; b < kRedBlocks; b += kRedThreads) acc += partial[b];
+  for (int b = threadIdx.x; b < kMassBlocks; b += kRedThreads) acc += partial[b];
   const double s = block_sum(acc, sh);
-  if (threadIdx.x == 0) out[0] = s;
+  if (threadIdx.x == 0) {
+    out[0] = (double)n + s;
+    if (!isfinite(s)) atomicOr(err, kErrUnstable);  // a non-finite population anywhere
+  }
 }
 
-// One block per iolet: flux of rho u along its axis over the sites touching it.
+// Flux of rho u along iolet k's axis over the sites touching it: blocks
+// (k, b) of a (n_iolets x bpi) grid take every bpi-th chunk of the site list;
+// with bpi > 1 they write partials that k_flux_final adds in block order,
+// with bpi = 1 the single block writes the result.
 template <class S>
 __global__ void __launch_bounds__(kRedThreads)
-    k_flux(const DevLattice d, int odd, const int64_t* off, const int64_t* sites, double* out) {
+    k_flux(const DevLattice d, int odd, const int64_t* off, const int64_t* sites, double* part,
+           double* out) {
   __shared__ double sh[kRedThreads];
-  const int k = blockIdx.x;
+  const int k = blockIdx.x, b = blockIdx.y, bpi = gridDim.y;
   const IoletDev& io = d.iolets[k];
   double acc = 0.0;
-  for (int64_t q = off[k] + threadIdx.x; q < off[k + 1]; q += kRedThreads) {
+  for (int64_t q = off[k] + (int64_t)b * kRedThreads + threadIdx.x; q < off[k + 1];
+       q += (int64_t)bpi * kRedThreads) {
     double f[kQ], r, jx, jy, jz;
     site_f<S>(d, sites[q], odd, f);
     f_moments(f, r, jx, jy, jz);
     acc += jx * io.axis[0] + jy * io.axis[1] + jz * io.axis[2];
   }
   const double s = block_sum(acc, sh);
-  if (threadIdx.x == 0) out[1 + k] = s;
+  if (threadIdx.x == 0) {
+    if (bpi == 1) out[1 + k] = s;
+    else part[k * bpi + b] = s;
+  }
+}
+
+__global__ void k_flux_final(const double* part, int bpi, double* out) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < bpi; ++b) s += part[blockIdx.x * bpi + b];
+  out[1 + blockIdx.x] = s;
 }
 
 // Wall shear stress (metric): sigma = -(1 - 1/(2 tau)) sum f^neq c c,
@@ -1012,9 +1043,15 @@ int launch_reduce(int storage, const DevLattice& d, int odd, const int64_t* off,
   return dispatch(storage, [&](auto tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     cudaStream_t s = (cudaStream_t)stream;
-    k_mass<S><<<kRedBlocks, kRedThreads, 0, s>>>(d, odd, partial);
-    k_mass_final<<<1, kRedThreads, 0, s>>>(partial, out);
-    if (d.n_iolets > 0) k_flux<S><<<d.n_iolets, kRedThreads, 0, s>>>(d, odd, off, sites, out);
+    k_mass<S><<<kMassBlocks, kRedThreads, 0, s>>>(d, partial);
+    k_mass_final<<<1, kRedThreads, 0, s>>>(partial, d.n, d.err, out);
+    if (d.n_iolets > 0) {
+      int bpi = kFluxPartials / d.n_iolets;
+      bpi = bpi < 1 ? 1 : (bpi > kFluxBlocksMax ? kFluxBlocksMax : bpi);
+      double* part = partial + kMassBlocks;
+      k_flux<S><<<dim3(d.n_iolets, bpi), kRedThreads, 0, s>>>(d, odd, off, sites, part, out);
+      if (bpi > 1) k_flux_final<<<d.n_iolets, 32, 0, s>>>(part, bpi, out);
+    }
     return (int)cudaGetLastError();
   });
 }
