@@ -77,7 +77,9 @@ enum {
   LBM_ECUDA = -3,     /* a CUDA runtime call failed; see lbm_last_error */
   LBM_EUNSTABLE = -4, /* a kernel saw a non-finite or non-positive density */
   LBM_ETIMEOUT = -5,  /* a bounded device wait gave up */
-  LBM_ESTATE = -6     /* call not valid in the context's current state */
+  LBM_ESTATE = -6,    /* call not valid in the context's current state */
+  LBM_ECHECK = -7     /* checked builds only (-DLBM_CHECKED): a neighbour or slot index out of
+                         range, or a population slot not written exactly once in a step */
 };
 
 /* Population storage.  Every variant stores f_i - w_i (the deviation from the

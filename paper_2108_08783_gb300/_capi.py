@@ -8,10 +8,12 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblbm.so")
+# LBM_LIBRARY selects another build of the same ABI (e.g. the checked build,
+# compiled with -DLBM_CHECKED); default: the package's liblbm.so.
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(HERE, "liblbm.so")
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = (
-    0, -1, -2, -3, -4, -5, -6)
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_ECHECK = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
 LBM_WALL_BOUNCEBACK, LBM_WALL_ELASTIC_GZS = 0, 1
 LBM_IOLET_VELOCITY, LBM_IOLET_DENSITY = 0, 1

@@ -142,6 +142,7 @@ const char* lbm_status_string(int s) {
     case LBM_EUNSTABLE: return "LBM_EUNSTABLE";
     case LBM_ETIMEOUT: return "LBM_ETIMEOUT";
     case LBM_ESTATE: return "LBM_ESTATE";
+    case LBM_ECHECK: return "LBM_ECHECK";
   }
   return "LBM_E?";
 }
@@ -269,6 +270,20 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   d.slot_Uw = sUw;
   d.iolets = io;
   d.err = err;
+#ifdef LBM_CHECKED
+  // checked builds: per-slot store counts of the current step
+  d.chk = dev_alloc<int>(c, (size_t)lbm::kQ * d.npad);
+  if (!d.chk) {
+    g_build_err = "device allocation failed";
+    lbm_destroy(c);
+    return LBM_ENOMEM;
+  }
+  if (cudaMemsetAsync(d.chk, 0, (size_t)lbm::kQ * d.npad * sizeof(int), c->stream) != cudaSuccess) {
+    g_build_err = "checked build: count reset failed";
+    lbm_destroy(c);
+    return LBM_ECUDA;
+  }
+#endif
   std::vector<lbm::IoletDev> hio(n_iolets);
   for (int k = 0; k < n_iolets; ++k) {
     const lbm_iolet& s = iolets[k];
@@ -416,6 +431,10 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
     const lbm::StepStreams ss{c->stream, c->side, c->fork, c->join};
     int rc = lbm::launch_step(c->storage, c->d, p, ss, c->prof ? ev : nullptr);
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "step kernels");
+#ifdef LBM_CHECKED
+    rc = lbm::launch_check_counts(c->d, c->stream);
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "checked build: count kernel");
+#endif
     ++c->step;
   }
   return LBM_OK;
@@ -434,6 +453,8 @@ int lbm_sync(lbm_ctx* c) {
     cudaStreamSynchronize(c->stream);
     if (flag & lbm::kErrTimeout)
       return fail(c, LBM_ETIMEOUT, "a bounded device wait gave up");
+    if (flag & lbm::kErrCheck)
+      return fail(c, LBM_ECHECK, "checked build: index out of range or a slot not written once");
     return fail(c, LBM_EUNSTABLE, "non-finite or non-positive density");
   }
   return LBM_OK;
@@ -764,6 +785,7 @@ int ens_upload(lbm_ensemble* e) {
     lbm::MemberDev& md = tab[q];
     std::memset(&md, 0, sizeof md);
     md.d = c->d;
+    md.d.chk = nullptr;  // store counting covers single-lattice steps only
     md.omega = 1.0 / c->tau;
     md.rho0 = c->rho0;
     md.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;

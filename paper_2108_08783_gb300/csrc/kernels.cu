@@ -272,10 +272,38 @@ __device__ __forceinline__ int32_t lds_volatile(const int32_t* p) {
   return *static_cast<const volatile int32_t*>(p);
 }
 
+// Checked builds (-DLBM_CHECKED): every population store of a step kernel is
+// counted per slot (a separate kernel then requires exactly one per slot), and
+// neighbour indices are range-checked; a violation sets kErrCheck and skips
+// the access instead of trapping.
+#ifdef LBM_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+template <class S>
+__device__ __forceinline__ void chk_count(int* chk, const S* P0, const S* p, int64_t lim, int* err) {
+  if constexpr (kChecked) {
+    if (!chk) return;
+    const int64_t i = p - P0;
+    if (i < 0 || i >= lim) atomicOr(err, kErrCheck);
+    else atomicAdd(chk + i, 1);
+  }
+}
+__device__ __forceinline__ bool chk_site(int64_t y, int64_t n, int* err) {
+  if constexpr (kChecked) {
+    if (y < 0 || y >= n) {
+      atomicOr(err, kErrCheck);
+      return false;
+    }
+  }
+  return true;
+}
+
 // Branch-free update of a site whose 18 links are fluid.
 template <class S, bool ODD>
 __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t* dsc,
-                                            double omega_t, int* err) {
+                                            double omega_t, int* err, int* chk) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
   C g[kQ];
@@ -289,6 +317,7 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
   if (unstable(m.rho)) atomicOr(err, kErrUnstable);
   const C omega = C(omega_t);
   Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
+  chk_count(chk, P, P + x, kQ * np, err);
   unroll<9>([&](auto Pi) {
     constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
     const C sa = g[a] + omega * (geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[a]);
@@ -297,11 +326,17 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
       // The store to (x + c_a, a) hits the address the load of direction
       // opp(a) used; re-reading the offset from shared memory keeps the
       // compiler from holding all 18 64-bit addresses live across the update.
-      Cd::st(P + a * np + x + lds_volatile(dsc + a - 1), a, sa);
-      Cd::st(P + b * np + x + lds_volatile(dsc + b - 1), b, sb);
+      S* pa = P + a * np + x + lds_volatile(dsc + a - 1);
+      S* pb = P + b * np + x + lds_volatile(dsc + b - 1);
+      Cd::st(pa, a, sa);
+      Cd::st(pb, b, sb);
+      chk_count(chk, P, pa, kQ * np, err);
+      chk_count(chk, P, pb, kQ * np, err);
     } else {
       Cd::st(P + b * np + x, a, sa);
       Cd::st(P + a * np + x, b, sb);
+      chk_count(chk, P, P + b * np + x, kQ * np, err);
+      chk_count(chk, P, P + a * np + x, kQ * np, err);
     }
   });
 }
@@ -314,7 +349,8 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
 template <class S, bool ODD>
 __device__ __forceinline__ void boundary_load(const S* P, int64_t np, int64_t x, uint32_t nf,
                                               const int32_t* dsc, bool irr, const int32_t* nbr_s,
-                                              int lane, typename Codec<S>::C (&g)[kQ]) {
+                                              int lane, typename Codec<S>::C (&g)[kQ],
+                                              int64_t n, int* err) {
   using Cd = Codec<S>;
   unroll<kQ>([&](auto J) {
     constexpr int j = decltype(J)::value;
@@ -325,7 +361,8 @@ __device__ __forceinline__ void boundary_load(const S* P, int64_t np, int64_t x,
       if ((nf >> o) & 1u) {
         g[j] = Cd::ld(P + j * np + x, j);
       } else {
-        const int64_t y = irr ? (int64_t)nbr_s[(o - 1) * kTile + lane] : x + dsc[o - 1];
+        int64_t y = irr ? (int64_t)nbr_s[(o - 1) * kTile + lane] : x + dsc[o - 1];
+        if (!chk_site(y, n, err)) y = x;  // checked builds: flagged, read a safe slot
         g[j] = Cd::ld(P + o * np + y, j);
       }
     }
@@ -382,12 +419,21 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   };
   // Rest population and the links that stay in the fluid: stream f*.
   Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
+  chk_count(d.chk, P, P + x, kQ * np, d.err);
   unroll<kQ - 1>([&](auto I0) {
     constexpr int i = decltype(I0)::value + 1;
     if (!((smask >> i) & 1u)) {
       const C si = g[i] + omega * (geq<i, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[i]);
-      if constexpr (ODD) Cd::st(P + i * np + nb(i), i, si);
-      else Cd::st(P + dir_opp(i) * np + x, i, si);
+      S* pi;
+      if constexpr (ODD) {
+        const int64_t y = nb(i);
+        if (!chk_site(y, d.n, d.err)) return;
+        pi = P + i * np + y;
+      } else {
+        pi = P + dir_opp(i) * np + x;
+      }
+      Cd::st(pi, i, si);
+      chk_count(d.chk, P, pi, kQ * np, d.err);
     }
   });
   uint32_t nf = smask & kDirBits;
@@ -497,6 +543,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
         const C val = link_value(link_code(i), cdot<j, C>(m.ux, m.uy, m.uz),
                                  cdot<j, C>(uix, uiy, uiz), weight<C>(j), g[i], g[j]);
         Cd::st(P + j * np + x, j, val);
+        chk_count(d.chk, P, P + j * np + x, kQ * np, d.err);
       }
     });
   } else {
@@ -517,6 +564,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
       const C val = link_value(link_code(i), cu, ci, dir_tab<C>(3, j), gsm[i * kTile + lane],
                                gsm[j * kTile + lane]);
       Cd::st(P + j * np + x, j, val);
+      chk_count(d.chk, P, P + j * np + x, kQ * np, d.err);
     }
   }
 }
@@ -539,7 +587,13 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
   }
   __syncwarp();
   const int64_t x = (int64_t)dsc[19] * kTile + lane;
-  if (x < d.n) bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p.omega, d.err);
+  if (x >= d.n) return;
+  if constexpr (kChecked && ODD) {
+    bool ok = true;
+    for (int o = 0; o < 18; ++o) ok = chk_site(x + dsc[o], d.n, d.err) && ok;
+    if (!ok) return;
+  }
+  bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p.omega, d.err, d.chk);
 }
 
 template <class S, bool ODD>
@@ -598,14 +652,15 @@ __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepPar
   C g[kQ];
   S* P = static_cast<S*>(d.pop);
   if (!stage && valid)
-    boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g);
+    boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g, d.n, d.err);
   if (stage) {
     if (!mbar_wait_bounded(bar, 0)) {
       if (lane == 0) atomicOr(d.err, kErrTimeout);
       mbar_wait_bounded(bar, 0);  // a second bounded chance for copies still in flight
       return;
     }
-    if (valid) boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, true, nbr_s, lane, g);
+    if (valid)
+      boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, true, nbr_s, lane, g, d.n, d.err);
   }
   if (!valid) return;
   boundary_update<S, ODD>(d, p, p.omega, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s,
@@ -789,6 +844,17 @@ __device__ double block_sum(double v, double* sh) {
     __syncthreads();
   }
   return sh[0];
+}
+
+// Checked builds: every slot of a valid site stored exactly once since the
+// last check, padding slots never; the counts are cleared for the next step.
+__global__ void k_check_counts(int* chk, int64_t total, int64_t npad, int64_t n, int* err) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int want = (q % npad) < n ? 1 : 0;
+    if (chk[q] != want) atomicOr(err, kErrCheck);
+    chk[q] = 0;
+  }
 }
 
 // Mass partials: fixed grid, fixed order -> deterministic.  Both AA layouts
@@ -995,6 +1061,14 @@ int launch_ensemble_step(int storage, const EnsembleLaunch& e, const StepParams&
 
 int launch_advance(int64_t* step_dev, int64_t by, void* stream) {
   k_advance<<<1, 1, 0, (cudaStream_t)stream>>>(step_dev, by);
+  return (int)cudaGetLastError();
+}
+
+int launch_check_counts(const DevLattice& d, void* stream) {
+  if (!d.chk) return 0;
+  const int64_t total = (int64_t)kQ * d.npad;
+  k_check_counts<<<blocks_for(total, 256) < 4096 ? blocks_for(total, 256) : 4096, 256, 0,
+                   (cudaStream_t)stream>>>(d.chk, total, d.npad, d.n, d.err);
   return (int)cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ constexpr uint32_t kIrregular = 1u << 31;  // tile: fluid-link offsets differ be
 // Sticky device error bits (ctx->err).
 constexpr int kErrUnstable = 1;
 constexpr int kErrTimeout = 2;
+constexpr int kErrCheck = 4;  // checked builds: index out of range / slot not written once
 
 // One tile of 32 consecutive sites, 80 bytes, read by one warp (lanes 0..19).
 //  bulk tile: mask == 0 and code[i-1] = nbr(x, i) - x, the same for every
@@ -128,6 +129,7 @@ struct DevLattice {
   int32_t n_iolets = 0;
   int* err = nullptr;
   int64_t n_boundary = 0;  // boundary tiles = leading entries of the launch order
+  int* chk = nullptr;      // checked builds: stores per population slot this step, [19][npad]
 };
 
 struct StepParams {
@@ -192,6 +194,9 @@ int launch_wss(int storage, const DevLattice& d, int odd_layout, double tau,
                const int64_t* sites, const double* normals, int64_t m, double* out,
                void* stream);
 size_t storage_bytes(int storage);
+// Checked builds: flag every population slot not stored exactly once since the
+// last call (padding slots: never), then clear the counts.
+int launch_check_counts(const DevLattice& d, void* stream);
 
 // Learned warm start (mlp.cu): the network's forward pass on a given stream
 // (n rows in chunks of its batch size, using its activation buffers), its
