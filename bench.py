@@ -149,11 +149,12 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_oracle(geo, params, seconds=12.0, max_steps=200, min_steps=2):
-    """MLUPS of the FP64 oracle on all host cores over a time-bounded sample."""
+def cpu_oracle(geo, params, seconds=12.0, max_steps=200, min_steps=2, threads=None):
+    """MLUPS of the FP64 oracle over a time-bounded sample (all host cores by
+    default)."""
     from oracle import Oracle
     from oracle.oracle import default_threads
-    threads = default_threads()
+    threads = threads or default_threads()
     orc = Oracle(geo.labels, geo.iolets, tau=params["tau"], wall_model=1, F=params["F"],
                  kappa=params["kappa"], rho0=params["rho0"], threads=threads)
     orc.run(1)  # page in
@@ -163,6 +164,31 @@ def cpu_oracle(geo, params, seconds=12.0, max_steps=200, min_steps=2):
         steps += 1
     dt = time.perf_counter() - t0
     return orc.n * steps / dt / 1e6, threads, steps, dt
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "CPU part", "Model"):
+                    return v.strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_config1_full_run():
+    """Wall seconds of the oracle's full config-1 run (R = 8, L = 64 tube, 2000
+    steps from rest, all host cores)."""
+    from oracle import Oracle
+    import lbm_inputs as I
+    geo = I.tube(8, 64, u_mean=0.025)
+    orc = Oracle(geo.labels, geo.iolets, tau=0.8, wall_model=1, F=0.85, kappa=12.0, rho0=1.0)
+    t0 = time.perf_counter()
+    orc.run(2000)
+    return time.perf_counter() - t0, orc.n
 
 
 def precision_study(args, geo, params, steps, budget=5e-3):
@@ -428,8 +454,15 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         mlups, threads, steps, dt = cpu_oracle(geo, params, seconds=args.cpu_seconds)
+        m1, _, steps1, dt1 = cpu_oracle(geo, params, seconds=3.0, max_steps=50, threads=1)
+        c1_s, c1_n = cpu_config1_full_run()
         cpu = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-               "sample": "%d FP64 oracle steps of the same workload (%.1f s)" % (steps, dt)}
+               "sample": "%d FP64 oracle steps of the same workload (%.1f s)" % (steps, dt),
+               "single_thread_mlups": m1,
+               "single_thread_sample": "%d steps (%.1f s)" % (steps1, dt1),
+               "cpu_model": cpu_model(),
+               "config1_full_run_s": c1_s,
+               "config1": "R=8 L=64 tube (%d sites), 2000 steps from rest, all cores" % c1_n}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,

@@ -62,3 +62,31 @@ def wss_agreement(geo, tau, F, kappa, steps, storage="f32", rho0=1.0):
         lat.close()
     return out["elastic"], out["bounceback"], limits_of_agreement(out["elastic"],
                                                                   out["bounceback"])
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    import lbm_inputs as I
+    ap = argparse.ArgumentParser(description="F map and rigid vs elastic WSS agreement")
+    ap.add_argument("--M", type=complex, default=complex(0.9, 0.0),
+                    help="elastic-tube coefficient M of Eq. F (not fixed by the paper)")
+    ap.add_argument("--steps", type=int, default=2400, help="steps from rest before the WSS snapshot")
+    ap.add_argument("--depth", type=int, default=6)
+    ap.add_argument("--storage", default="f32")
+    a = ap.parse_args()
+    alpha = [0.5, 1.0, 2.0, 3.0, 4.0, 6.0, 8.0, 10.0]
+    drs = [0.01, 0.02, 0.05, 0.1]
+    F = np.abs(fmap(alpha, drs, a.M))
+    print("|F| for M = %s (rows alpha %s, columns dr/R %s)" % (a.M, alpha, drs))
+    for al, row in zip(alpha, F):
+        print("  alpha %5.1f: %s" % (al, " ".join("%.4f" % v for v in row)))
+    geo = I.murray_tree(seed=0, depth=a.depth, root_radius=48.0)
+    geo.iolets[0].u_mean = 0.03
+    geo.iolets[0].u_amp = 0.02
+    geo.iolets[0].period = 4000.0
+    e, r, s = wss_agreement(geo, tau=0.6, F=0.85, kappa=0.75 * 48.0 / 0.5, steps=a.steps,
+                            storage=a.storage)
+    s["tree"] = "Murray tree depth %d, root R 48 (%d sites), %d steps from rest, pulsatile " \
+                "inflow 0.03 + 0.02 sin(2 pi n / 4000)" % (a.depth, geo.n_fluid(), a.steps)
+    print(json.dumps(s))
