@@ -3,12 +3,14 @@
 // kernels that connect it to a lattice.  No counterpart in the paper.
 //
 // Every contraction (forward z = h W^T, input error d W, weight gradient
-// d^T h) runs through one tensor-core GEMM kernel: bfloat16 operands staged
-// in shared memory, mma.sync m16n8k16 with FP32 accumulation, and a fused
-// epilogue (bias + tanh + bfloat16 store; bias + FP32 store; tanh derivative
-// + bfloat16 store; FP32 atomic accumulation for split-batch weight
-// gradients).  The network is narrow (a few hundred columns), so the
-// operands live in L2 and a GEMM launch lasts microseconds.
+// d^T h) runs through one GEMM kernel on the fifth-generation tensor cores:
+// bfloat16 operands staged in shared memory in the canonical K-major layout,
+// tcgen05.mma (kind::f16, 128 x 128 x 16) accumulating in FP32 in tensor
+// memory, completion tracked by an mbarrier (bounded wait), and a fused
+// epilogue read back with tcgen05.ld (bias + tanh + bfloat16 store; bias +
+// FP32 store; tanh derivative + bfloat16 store; FP32 atomic accumulation for
+// split-batch weight gradients).  The network is narrow (a few hundred
+// columns), so the operands live in L2 and a GEMM launch lasts microseconds.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -41,117 +43,266 @@ struct GemmArgs {
   bf16* o16;           // [M][ldo]       (kEpiTanh, kEpiDTanh)
   float* o32;          // [M][ldo]       (kEpiLinear, kEpiAccum)
   int64_t ldo;
+  int* err;            // set if a bounded wait for the tensor cores gives up
 };
 
 enum { kEpiTanh = 0, kEpiLinear = 1, kEpiDTanh = 2, kEpiAccum = 3 };
-constexpr int kBM = 64, kBN = 64, kBK = 32, kPad = 8, kGemmThreads = 128;
 
-__device__ __forceinline__ uint32_t ld32(const bf16* p) {
-  return *reinterpret_cast<const uint32_t*>(p);
+// Tile of one CTA: a 128 x 128 block of C, K staged 64 at a time; the UMMA
+// shape is M = 128, N = 128, K = 16 (kind::f16, bf16 in, FP32 accumulate).
+constexpr int kTM = 128, kTN = 128, kTK = 64, kTcThreads = 128;
+constexpr uint32_t kTmemCols = 128;  // FP32 accumulator columns (= kTN)
+constexpr int kTcSmemPad = 15 * 1024;
+
+// Shared-memory tiles in the canonical K-major layout without swizzling: a
+// core matrix is 8 rows x 16 bytes (8 bf16 along K) stored contiguously;
+// core matrices adjacent along K are kLBO bytes apart, 8-row groups kSBO.
+constexpr uint32_t kLBO = 128, kSBO = (kTK / 8) * 128;
+
+__device__ __forceinline__ int canon(int r, int k) {  // bf16 index of element (r, k)
+  return (r >> 3) * (int)(kSBO / 2) + (k >> 3) * (int)(kLBO / 2) + (r & 7) * 8 + (k & 7);
 }
 
-// D += A B on one 16x8x16 tile: A row-major bf16 pairs, B column-major pairs.
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4],
-                                         const uint32_t (&b)[2]) {
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (M/N) byte offsets, each >> 4; bits 46-48 = 0b001; no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(kLBO >> 4) << 16) |
+         ((uint64_t)(kSBO >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                            ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: each try_wait suspends for a hardware-chosen interval, so the
+// limit is reached only if the tensor-core work never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (mbar_try(bar, parity)) return true;
+  return false;
 }
 
-// 4 warps per 64x64 block tile, each warp a 32x32 quadrant (2 x 4 mma tiles).
-template <int EPI>
-__global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
-  __shared__ __align__(16) bf16 As[kBM][kBK + kPad];  // [m][k]
-  __shared__ __align__(16) bf16 Bs[kBN][kBK + kPad];  // [n][k]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int grp = lane >> 2, tq = lane & 3;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int64_t m0 = (int64_t)blockIdx.x * kBM, n0 = (int64_t)blockIdx.y * kBN;
-  const int64_t kb = (int64_t)blockIdx.z * g.kchunk;
-  const int64_t ke = g.K < kb + g.kchunk ? g.K : kb + g.kchunk;
+// Stage rows [row0, row0 + rows) x k [k0, k0 + kTK) of an operand whose
+// element (row, k) is src[row s_row + k s_k] into T in the canonical layout,
+// zero outside row < row_lim, k < ke.  16-byte loads when the operand is
+// contiguous along k (one core-matrix row per load) or along rows (8 rows of
+// one k per load), else element by element.
+__device__ __forceinline__ void stage_tile(bf16* T, const bf16* src, int64_t s_row, int64_t s_k,
+                                           int64_t row0, int64_t row_lim, int64_t k0, int64_t ke,
+                                           int rows, int tid) {
   const bf16 zero = __float2bfloat16_rn(0.0f);
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-
-  for (int64_t k0 = kb; k0 < ke; k0 += kBK) {
-    // Stage the tiles; the index order follows the operand's unit stride.
-    for (int e = tid; e < kBM * kBK; e += kGemmThreads) {
-      int r, c;
-      if (g.sak == 1) { r = e / kBK; c = e % kBK; }
-      else { c = e / kBM; r = e % kBM; }
-      const int64_t m = m0 + r, k = k0 + c;
-      As[r][c] = (m < g.M && k < ke) ? g.A[m * g.sam + k * g.sak] : zero;
-    }
-    for (int e = tid; e < kBN * kBK; e += kGemmThreads) {
-      int r, c;
-      if (g.sbk == 1) { r = e / kBK; c = e % kBK; }
-      else { c = e / kBN; r = e % kBN; }
-      const int64_t n = n0 + r, k = k0 + c;
-      Bs[r][c] = (n < g.N && k < ke) ? g.B[k * g.sbk + n * g.sbn] : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + grp;
-        af[i][0] = ld32(&As[r][kk + 2 * tq]);
-        af[i][1] = ld32(&As[r + 8][kk + 2 * tq]);
-        af[i][2] = ld32(&As[r][kk + 2 * tq + 8]);
-        af[i][3] = ld32(&As[r + 8][kk + 2 * tq + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int cn = wn + j * 8 + grp;
-        bfr[j][0] = ld32(&Bs[cn][kk + 2 * tq]);
-        bfr[j][1] = ld32(&Bs[cn][kk + 2 * tq + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma16816(acc[i][j], af[i], bfr[j]);
-    }
-    __syncthreads();
-  }
-
-  // Accumulator q of tile (i, j): row grp + 8 (q >> 1), column 2 tq + (q & 1).
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t m = m0 + wm + i * 16 + grp + 8 * (q >> 1);
-        const int64_t n = n0 + wn + j * 8 + 2 * tq + (q & 1);
-        if (m >= g.M || n >= g.N) continue;
-        const float v = acc[i][j][q];
-        if constexpr (EPI == kEpiTanh) {
-          g.o16[m * g.ldo + n] = __float2bfloat16_rn(tanhf(v + g.bias[n]));
-        } else if constexpr (EPI == kEpiLinear) {
-          g.o32[m * g.ldo + n] = v + g.bias[n];
-        } else if constexpr (EPI == kEpiDTanh) {
-          const float h = __bfloat162float(g.hprev[m * g.ldh + n]);
-          g.o16[m * g.ldo + n] = __float2bfloat16_rn(v * (1.0f - h * h));
+  const bool al = ((uintptr_t)src & 15u) == 0;
+  if (al && s_k == 1 && (s_row & 7) == 0) {
+    for (int e = tid; e < rows * (kTK / 8); e += kTcThreads) {
+      const int r = e / (kTK / 8), c = (e % (kTK / 8)) * 8;
+      const int64_t row = row0 + r, k = k0 + c;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (row < row_lim) {
+        const bf16* p = src + row * s_row + k;
+        if (k + 8 <= ke) {
+          v = __ldg(reinterpret_cast<const uint4*>(p));
         } else {
-          atomicAdd(g.o32 + m * g.ldo + n, v);
+          bf16 t[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) t[i] = (k + i < ke) ? p[i] : zero;
+          v = *reinterpret_cast<const uint4*>(t);
         }
       }
+      *reinterpret_cast<uint4*>(T + canon(r, c)) = v;
+    }
+  } else if (al && s_row == 1 && (s_k & 7) == 0 && (rows & 7) == 0) {
+    for (int e = tid; e < (rows / 8) * kTK; e += kTcThreads) {
+      const int r = (e % (rows / 8)) * 8, c = e / (rows / 8);
+      const int64_t row = row0 + r, k = k0 + c;
+      bf16 t[8];
+      if (k < ke && row + 8 <= row_lim) {
+        *reinterpret_cast<uint4*>(t) = __ldg(reinterpret_cast<const uint4*>(src + k * s_k + row));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = (k < ke && row + i < row_lim) ? src[k * s_k + row + i] : zero;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) T[canon(r + i, c)] = t[i];
+    }
+  } else {
+    for (int e = tid; e < rows * kTK; e += kTcThreads) {
+      int r, c;
+      if (s_k == 1) { r = e / kTK; c = e % kTK; }
+      else { c = e / rows; r = e % rows; }
+      const int64_t row = row0 + r, k = k0 + c;
+      T[canon(r, c)] = (row < row_lim && k < ke) ? src[row * s_row + k * s_k] : zero;
+    }
+  }
+}
+
+// C = A B with A (M x K) and B (K x N) in bf16, FP32 accumulation in tensor
+// memory (tcgen05), fused epilogue.  One CTA per 128 x 128 tile of C (and per
+// K chunk, blockIdx.z): all 128 threads stage A and B into shared memory in
+// the canonical layout (any global strides); one thread issues the four
+// K = 16 MMAs of a stage and commits them to an mbarrier; after the last
+// stage each warp reads its 32 accumulator rows from tensor memory.
+template <int EPI>
+__global__ void __launch_bounds__(kTcThreads) k_gemm(const GemmArgs g) {
+  __shared__ __align__(128) bf16 As[kTM * kTK];
+  __shared__ __align__(128) bf16 Bs[kTN * kTK];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * kTM, n0 = (int64_t)blockIdx.y * kTN;
+  const int64_t kb = (int64_t)blockIdx.z * g.kchunk;
+  const int64_t ke = g.K < kb + g.kchunk ? g.K : kb + g.kchunk;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(&tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) mbar_init1(&bar);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int64_t k0 = kb; k0 < ke; k0 += kTK) {
+    stage_tile(As, g.A, g.sam, g.sak, m0, g.M, k0, ke, kTM, tid);
+    stage_tile(Bs, g.B, g.sbn, g.sbk, n0, g.N, k0, ke, kTN, tid);
+    // make the generic-proxy stores visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < kTK / 16; ++kk) {
+        // K = 16 is two core matrices along K: advance the start by 2 LBO
+        const uint64_t ad = smem_desc(saddr(As) + kk * 2 * kLBO);
+        const uint64_t bd = smem_desc(saddr(Bs) + kk * 2 * kLBO);
+        const uint32_t acc = (k0 > kb || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              saddr(&bar))
+          : "memory");
+    }
+    // every thread takes the same branch (the tensor-memory loads below are
+    // warp-collective)
+    if (!__syncthreads_and(mbar_wait(&bar, phase) ? 1 : 0)) {
+      if (tid == 0) atomicOr(g.err, 1);
+      mbar_wait(&bar, phase);  // a second bounded chance for the MMAs in flight
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  if (ok && kb < ke) {
+    const int64_t m = m0 + warp * 32 + lane;  // accumulator row = tensor-memory lane
+#pragma unroll 1
+    for (int c0 = 0; c0 < kTN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+          "%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m >= g.M) continue;
+      const int64_t nb = n0 + c0;
+      float x[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) x[j] = __uint_as_float(v[j]);
+      // Each thread owns 16 consecutive outputs of one row: whole 16-byte
+      // vectors when the row segment is full and aligned, else element-wise.
+      if constexpr (EPI == kEpiTanh || EPI == kEpiDTanh) {
+        bf16* o = g.o16 + m * g.ldo + nb;
+        if (nb + 16 <= g.N && ((uintptr_t)o & 15u) == 0 &&
+            (EPI == kEpiTanh || ((uintptr_t)(g.hprev + m * g.ldh + nb) & 15u) == 0)) {
+          __align__(16) bf16 t[16];
+          if constexpr (EPI == kEpiDTanh) {
+            __align__(16) bf16 h[16];
+            *reinterpret_cast<uint4*>(h) = *reinterpret_cast<const uint4*>(g.hprev + m * g.ldh + nb);
+            *reinterpret_cast<uint4*>(h + 8) =
+                *reinterpret_cast<const uint4*>(g.hprev + m * g.ldh + nb + 8);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float hv = __bfloat162float(h[j]);
+              t[j] = __float2bfloat16_rn(x[j] * (1.0f - hv * hv));
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) t[j] = __float2bfloat16_rn(tanhf(x[j] + g.bias[nb + j]));
+          }
+          reinterpret_cast<uint4*>(o)[0] = reinterpret_cast<const uint4*>(t)[0];
+          reinterpret_cast<uint4*>(o)[1] = reinterpret_cast<const uint4*>(t)[1];
+          continue;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int64_t n = nb + j;
+        if (n >= g.N) break;
+        if constexpr (EPI == kEpiTanh) {
+          g.o16[m * g.ldo + n] = __float2bfloat16_rn(tanhf(x[j] + g.bias[n]));
+        } else if constexpr (EPI == kEpiLinear) {
+          g.o32[m * g.ldo + n] = x[j] + g.bias[n];
+        } else if constexpr (EPI == kEpiDTanh) {
+          const float h = __bfloat162float(g.hprev[m * g.ldh + n]);
+          g.o16[m * g.ldo + n] = __float2bfloat16_rn(x[j] * (1.0f - h * h));
+        } else {
+          atomicAdd(g.o32 + m * g.ldo + n, x[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
 }
 
 template <int EPI>
 int gemm(const GemmArgs& g, int64_t splits, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return 0;
-  dim3 grid((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + kBN - 1) / kBN),
+  dim3 grid((unsigned)((g.M + kTM - 1) / kTM), (unsigned)((g.N + kTN - 1) / kTN),
             (unsigned)splits);
-  k_gemm<EPI><<<grid, kGemmThreads, 0, s>>>(g);
+  // 15 KB of (unused) dynamic shared memory on top of the 32 KB of tiles caps
+  // an SM at 4 CTAs, so their 4 x 128 accumulator columns always fit in the
+  // 512 columns of tensor memory and no allocation ever waits.
+  k_gemm<EPI><<<grid, kTcThreads, kTcSmemPad, s>>>(g);
   return (int)cudaGetLastError();
 }
 
@@ -291,6 +442,7 @@ struct lbm_mlp {
   float* y = nullptr;      // [max_batch][n_out]
   bf16* d[2] = {nullptr, nullptr};  // errors, [max_batch][max(width, n_out)]
   double* loss = nullptr;
+  int* dflag = nullptr;    // device flag: a bounded tensor-core wait gave up
   int64_t t = 0;           // Adam steps taken
   std::string err;
 };
@@ -332,6 +484,7 @@ int forward_rows(lbm_mlp* net, const float* x, int64_t n, float* y, cudaStream_t
   if ((e = (int)cudaGetLastError())) return e;
   for (int l = 0; l < net->n_layers; ++l) {
     GemmArgs g{};
+    g.err = net->dflag;
     g.A = layer_in(net, l);
     g.sam = net->cols[l];
     g.sak = 1;
@@ -376,6 +529,7 @@ int loss_grad_rows(lbm_mlp* net, const float* x, const float* t, int64_t n, cuda
     const bf16* dl = net->d[cur];
     // dW_l = d_l^T h_l: [rows][cols], contraction over the n rows.
     GemmArgs gw{};
+    gw.err = net->dflag;
     gw.A = dl;
     gw.sam = 1;
     gw.sak = ldd;
@@ -398,6 +552,7 @@ int loss_grad_rows(lbm_mlp* net, const float* x, const float* t, int64_t n, cuda
     if (l == 0) break;
     // d_{l-1} = (d_l W_l) * (1 - h_l^2): [n][cols_l].
     GemmArgs gd{};
+    gd.err = net->dflag;
     gd.A = dl;
     gd.sam = ldd;
     gd.sak = 1;
@@ -520,7 +675,8 @@ int lbm_mlp_create(int32_t n_in, int32_t width, int32_t n_layers, int32_t n_out,
   net->d[0] = b16(max_batch * dw);
   net->d[1] = b16(max_batch * dw);
   net->loss = static_cast<double*>(malloc_dev(net, sizeof(double)));
-  ok = ok && net->loss;
+  net->dflag = static_cast<int*>(malloc_dev(net, sizeof(int)));
+  ok = ok && net->loss && net->dflag;
   if (!ok) {
     lbm_mlp_destroy(net);
     return LBM_ENOMEM;
@@ -530,6 +686,7 @@ int lbm_mlp_create(int32_t n_in, int32_t width, int32_t n_layers, int32_t n_out,
   for (void* p : {(void*)net->theta, (void*)net->grad, (void*)net->m, (void*)net->v})
     if (!e) e = (int)cudaMemsetAsync(p, 0, o * sizeof(float), s);
   if (!e) e = (int)cudaMemsetAsync(net->w16, 0, o * sizeof(bf16), s);
+  if (!e) e = (int)cudaMemsetAsync(net->dflag, 0, sizeof(int), s);
   if (!e) e = (int)cudaStreamSynchronize(s);
   if (e) {
     lbm_mlp_destroy(net);
@@ -619,7 +776,18 @@ int lbm_mlp_train_step(lbm_mlp* net, const float* x, const float* t, int64_t n,
 
 int lbm_mlp_sync(lbm_mlp* net) {
   if (!net) return LBM_EINVAL;
-  return mcuda(net, (int)cudaStreamSynchronize(net->stream), "lbm_mlp_sync");
+  int rc = mcuda(net, (int)cudaStreamSynchronize(net->stream), "lbm_mlp_sync");
+  if (rc != LBM_OK) return rc;
+  int flag = 0;
+  int e = (int)cudaMemcpyAsync(&flag, net->dflag, sizeof(int), cudaMemcpyDeviceToHost, net->stream);
+  if (!e) e = (int)cudaStreamSynchronize(net->stream);
+  if (e) return mcuda(net, e, "lbm_mlp_sync flag");
+  if (flag) {
+    cudaMemsetAsync(net->dflag, 0, sizeof(int), net->stream);
+    cudaStreamSynchronize(net->stream);
+    return mfail(net, LBM_ETIMEOUT, "a bounded wait for the tensor cores gave up");
+  }
+  return LBM_OK;
 }
 
 const char* lbm_mlp_last_error(const lbm_mlp* net) { return net ? net->err.c_str() : ""; }
