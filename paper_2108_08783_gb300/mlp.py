@@ -120,3 +120,42 @@ def warm_frame(centre, axis, z0, length, radius, features, rho_scale, u_scale):
     for k, v in enumerate(feats):
         f.global_[k] = float(v)
     return f
+
+
+def _throughput(rows=65536, train_rows=16384, reps=20):
+    """CUDA-event timing of the warm-start network's forward pass and
+    training step (seeded Glorot weights, uniform random inputs)."""
+    import torch
+    import lbm_inputs as I
+    net = MLP(7, 256, 4, 3, max_batch=rows)
+    net.set_params(I.mlp_init(0, 7, 256, 4, 3))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand(rows, 7, device="cuda", generator=g)
+    t = torch.rand(rows, 3, device="cuda", generator=g)
+    for _ in range(3):
+        net.forward(x)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(net.stream)
+    for _ in range(reps):
+        net.forward(x)
+    e1.record(net.stream)
+    e1.synchronize()
+    fwd = e0.elapsed_time(e1) / reps
+    flop = 2 * (7 * 256 + 2 * 256 * 256 + 256 * 3)
+    e0.record(net.stream)
+    for _ in range(reps):
+        net.train_step(x[:train_rows], t[:train_rows], lr=1e-4)
+    e1.record(net.stream)
+    e1.synchronize()
+    trn = e0.elapsed_time(e1) / reps
+    net.sync()
+    return {"forward_rows": rows, "forward_ms": fwd, "forward_tflops": rows * flop / fwd / 1e9,
+            "train_rows": train_rows, "train_step_ms": trn,
+            "train_tflops": 3 * train_rows * flop / trn / 1e9}
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    print(json.dumps(_throughput(int(sys.argv[1]) if len(sys.argv) > 1 else 65536)))
