@@ -247,13 +247,28 @@ int lbm_wss(lbm_ctx *ctx, const int64_t *sites, const double *normals, int64_t m
  * lbm_ensemble_tune - schedule knobs (chosen by an autotuner in the binding):
  *   LBM_TUNE_PREFETCH    L2 prefetch distance in tiles (>= 0);
  *   LBM_TUNE_SCHEDULE    0: members in the given order, 1: largest first;
- *   LBM_TUNE_GRAPH_STEPS steps per captured graph (even, 0 = direct launches).
+ *   LBM_TUNE_GRAPH_STEPS steps per captured graph (even, 0 = direct launches);
+ *   LBM_TUNE_PERSISTENT  1: each lbm_ensemble_step is one cooperative launch of a
+ *                        persistent kernel whose CTAs take chunks of tiles from a
+ *                        device counter and meet at a grid barrier after every
+ *                        step (graphs are not used then); a barrier that does not
+ *                        complete within ~1 s makes every CTA return and
+ *                        lbm_ensemble_sync report LBM_ETIMEOUT;
+ *   LBM_TUNE_BARRIER_EXTRA fault injection for tests: the grid barrier waits for
+ *                        this many arrivals that never come (default 0), so a
+ *                        persistent step times out instead of completing.
  * Before using a member's own calls (moments, wall state, ...) call
  * lbm_ensemble_sync.  Errors: LBM_EINVAL (bad arguments, mixed storage or
  * steps), LBM_ESTATE (members drifted apart), LBM_ENOMEM, LBM_ECUDA; the
  * message is lbm_ensemble_last_error. */
 typedef struct lbm_ensemble lbm_ensemble;
-enum { LBM_TUNE_PREFETCH = 0, LBM_TUNE_SCHEDULE = 1, LBM_TUNE_GRAPH_STEPS = 2 };
+enum {
+  LBM_TUNE_PREFETCH = 0,
+  LBM_TUNE_SCHEDULE = 1,
+  LBM_TUNE_GRAPH_STEPS = 2,
+  LBM_TUNE_PERSISTENT = 3,
+  LBM_TUNE_BARRIER_EXTRA = 4
+};
 int lbm_ensemble_create(lbm_ctx *const *members, int32_t n, lbm_ensemble **out);
 int lbm_ensemble_step(lbm_ensemble *ens, int64_t n_steps);
 int lbm_ensemble_sync(lbm_ensemble *ens);

@@ -748,6 +748,9 @@ struct lbm_ensemble {
   std::vector<int32_t> order;     // schedule: member order in the launch numbering
   int64_t prefetch = LBM_DEFAULT_PREFETCH;
   int64_t graph_steps = 0;        // 0: direct launches
+  int persistent = 0;             // 1: one cooperative launch per lbm_ensemble_step
+  int barrier_extra = 0;          // fault injection: arrivals the grid barrier waits for in vain
+  lbm::GridSync* sync_d = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t exec_steps = 0;
   int exec_parity = -1;
@@ -869,7 +872,8 @@ int lbm_ensemble_create(lbm_ctx* const* members, int32_t n, lbm_ensemble** out) 
   e->mem_d = static_cast<lbm::MemberDev*>(alloc(n * sizeof(lbm::MemberDev)));
   e->prefix_d = static_cast<int64_t*>(alloc(2 * (n + 1) * sizeof(int64_t)));
   e->step_d = static_cast<int64_t*>(alloc(sizeof(int64_t)));
-  if (!e->mem_d || !e->prefix_d || !e->step_d) {
+  e->sync_d = static_cast<lbm::GridSync*>(alloc(sizeof(lbm::GridSync)));
+  if (!e->mem_d || !e->prefix_d || !e->step_d || !e->sync_d) {
     lbm_ensemble_destroy(e);
     return LBM_ENOMEM;
   }
@@ -907,6 +911,14 @@ int lbm_ensemble_tune(lbm_ensemble* e, int32_t knob, int64_t value) {
       e->graph_steps = value;
       ens_drop_graph(e);
       return LBM_OK;
+    case LBM_TUNE_PERSISTENT:
+      if (value != 0 && value != 1) return ens_fail(e, LBM_EINVAL, "persistent must be 0 or 1");
+      e->persistent = (int)value;
+      return LBM_OK;
+    case LBM_TUNE_BARRIER_EXTRA:
+      if (value < 0 || value > 1024) return ens_fail(e, LBM_EINVAL, "barrier extra out of range");
+      e->barrier_extra = (int)value;
+      return LBM_OK;
   }
   return ens_fail(e, LBM_EINVAL, "unknown tuning knob");
 }
@@ -929,7 +941,15 @@ int lbm_ensemble_step(lbm_ensemble* e, int64_t n_steps) {
   lbm::StepParams p{};
   p.prefetch = e->prefetch;
   int64_t done = 0;
-  const int64_t G = e->graph_steps;
+  if (e->persistent && n_steps > 0) {
+    p.step = step0;
+    p.step_dev = nullptr;
+    const int lr = lbm::launch_ensemble_persistent(e->storage, e->launch, p, n_steps, e->sync_d,
+                                                   e->barrier_extra, e->stream);
+    if (lr != 0) return ens_cuda(e, (cudaError_t)lr, "persistent ensemble launch");
+    done = n_steps;
+  }
+  const int64_t G = e->persistent ? 0 : e->graph_steps;
   if (G > 0 && n_steps >= G) {
     const int parity = (int)(step0 & 1);
     if (!e->exec || e->exec_steps != G || e->exec_parity != parity) {

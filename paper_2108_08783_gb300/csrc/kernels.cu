@@ -613,9 +613,10 @@ __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK
 // staging area (18 rows of per-site neighbours) and mbarrier; dsc: its
 // 20-word descriptor area.
 template <class S, bool ODD>
-__device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepParams& p, int64_t k,
+__device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepParams& p, int64_t k,
                                               int32_t* dsc, int32_t* nbr_s, uint64_t* bar,
-                                              typename Codec<S>::C* gsm, int lane) {
+                                              typename Codec<S>::C* gsm, int lane,
+                                              uint32_t* bar_phase = nullptr) {
   using C = typename Codec<S>::C;
   const int64_t slot = k * kTile + lane;  // boundary tiles lead the launch order
   // per-site data and the descriptor, all in one round trip
@@ -629,8 +630,10 @@ __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepPar
   // odd steps of an irregular tile: stage the per-site neighbour rows
   // (cp.async.bulk into shared memory, completing on the warp's mbarrier)
   const bool stage = ODD && irr;
+  // bar_phase: a warp that stages repeatedly (persistent kernel) keeps one
+  // initialised mbarrier and tracks its phase; otherwise it is set up here.
   if (stage) {
-    if (lane == 0) mbar_init(bar, 1);
+    if (lane == 0 && !bar_phase) mbar_init(bar, 1);
     __syncwarp();
     if (lane == 0) {
       mbar_expect_tx(bar, 18u * kTile * 4u);
@@ -654,17 +657,20 @@ __device__ __forceinline__ void boundary_tile(const DevLattice& d, const StepPar
   if (!stage && valid)
     boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g, d.n, d.err);
   if (stage) {
-    if (!mbar_wait_bounded(bar, 0)) {
+    const uint32_t ph = bar_phase ? *bar_phase : 0u;
+    if (!mbar_wait_bounded(bar, ph)) {
       if (lane == 0) atomicOr(d.err, kErrTimeout);
-      mbar_wait_bounded(bar, 0);  // a second bounded chance for copies still in flight
-      return;
+      mbar_wait_bounded(bar, ph);  // a second bounded chance for copies still in flight
+      return false;
     }
+    if (bar_phase) *bar_phase = ph ^ 1u;
     if (valid)
       boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, true, nbr_s, lane, g, d.n, d.err);
   }
-  if (!valid) return;
+  if (!valid) return true;
   boundary_update<S, ODD>(d, p, p.omega, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s,
                           lane, slot, g, gsm);
+  return true;
 }
 
 template <class S, bool ODD>
@@ -728,6 +734,146 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
   pm.elastic = md.elastic;
   boundary_tile<S, ODD>(md.d, pm, g - __ldg(e.boundary_prefix + m), desc_s[w], stage[w], &bars[w],
                         gs[w], lane);
+}
+
+// ------------------------------------------------- persistent ensemble kernel
+// Every CTA stays resident for the whole launch (cooperative launch) and
+// loops over the steps: its warps take chunks of kPersistChunk tiles from a
+// per-step device counter - boundary tiles of all members first, then bulk
+// tiles - and the grid meets at a barrier between steps.
+
+constexpr int kPersistWarps = 8;
+constexpr int kPersistChunk = 16;
+constexpr long long kBarrierCycles = 1ll << 31;  // ~1 s at the GB300 SM clock
+
+// Grid barrier: bounded spin; false (every thread of the CTA) on timeout.
+__device__ bool grid_sync(GridSync* gs, unsigned expected, unsigned& gen, int next_slot, int* err) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&gs->arrive, 1u) == expected - 1u) {
+      atomicExch(&gs->arrive, 0u);
+      atomicExch(&gs->work[next_slot], 0ull);
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*static_cast<volatile unsigned*>(&gs->gen) == gen) {
+        if (clock64() - t0 > kBarrierCycles) {
+          atomicOr(err, kErrTimeout);
+          atomicExch(&gs->abort, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+    if (*static_cast<volatile unsigned*>(&gs->abort)) ok = 0;
+  }
+  ok = __syncthreads_and(ok);
+  ++gen;
+  return ok != 0;
+}
+
+// The four tile bodies as separate functions, so that each keeps the
+// register allocation it has in its own kernel.
+template <class S, bool ODD>
+__device__ __noinline__ bool persist_boundary(const DevLattice& d, const StepParams& p, int64_t k,
+                                              int32_t* dsc, int32_t* nbr_s, uint64_t* bar,
+                                              typename Codec<S>::C* gsm, int lane,
+                                              uint32_t* phase) {
+  return boundary_tile<S, ODD>(d, p, k, dsc, nbr_s, bar, gsm, lane, phase);
+}
+template <class S, bool ODD>
+__device__ __noinline__ void persist_bulk(const DevLattice& d, const StepParams& p, int64_t k,
+                                          int32_t* dsc, int lane) {
+  bulk_tile<S, ODD>(d, p, k, dsc, lane);
+}
+
+template <class S>
+__global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
+    k_ensemble_persistent(const EnsembleLaunch e, const StepParams p, int64_t n_steps,
+                          GridSync* gs, unsigned expected) {
+  using C = typename Codec<S>::C;
+  __shared__ __align__(128) int32_t stage[kPersistWarps][18 * kTile];
+  __shared__ __align__(16) C gsm[kPersistWarps][kQ * kTile];
+  __shared__ __align__(16) int32_t desc_s[kPersistWarps][20];
+  __shared__ uint64_t bars[kPersistWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) mbar_init(&bars[w], 1);
+  __syncwarp();
+  uint32_t phase = 0;
+  unsigned gen = 0;  // the launcher clears the barrier state
+  int* err0 = e.mem[0].d.err;
+  const int64_t total = e.n_boundary_tiles + e.n_bulk_tiles;
+  for (int64_t s = 0; s < n_steps; ++s) {
+    StepParams q = p;
+    q.step = p.step + s;
+    q.write_state = s == n_steps - 1 ? 1 : 0;
+    const bool odd = q.step & 1;
+    const int slot = (int)(q.step & 1);
+    for (;;) {
+      unsigned long long t0 = 0;
+      if (lane == 0) {
+        t0 = *static_cast<volatile unsigned*>(&gs->abort) ? (unsigned long long)total
+                                                          : atomicAdd(&gs->work[slot],
+                                                                      (unsigned long long)kPersistChunk);
+      }
+      t0 = __shfl_sync(0xffffffffu, t0, 0);
+      if ((int64_t)t0 >= total) break;
+      const int64_t t1 = (int64_t)t0 + kPersistChunk < total ? (int64_t)t0 + kPersistChunk : total;
+      for (int64_t t = (int64_t)t0; t < t1; ++t) {
+        if (t < e.n_boundary_tiles) {
+          const int m = find_member(e.boundary_prefix, e.n_members, t);
+          const MemberDev& md = e.mem[m];
+          StepParams pm = q;
+          pm.omega = md.omega;
+          pm.rho0 = md.rho0;
+          pm.elastic = md.elastic;
+          const int64_t k = t - __ldg(e.boundary_prefix + m);
+          const bool ok = odd ? persist_boundary<S, true>(md.d, pm, k, desc_s[w], stage[w],
+                                                          &bars[w], gsm[w], lane, &phase)
+                              : persist_boundary<S, false>(md.d, pm, k, desc_s[w], stage[w],
+                                                           &bars[w], gsm[w], lane, &phase);
+          if (!ok && lane == 0) atomicExch(&gs->abort, 1u);
+        } else {
+          const int64_t tb = t - e.n_boundary_tiles;
+          const int m = find_member(e.bulk_prefix, e.n_members, tb);
+          const MemberDev& md = e.mem[m];
+          StepParams pm = q;
+          pm.omega = md.omega;
+          const int64_t k = md.d.n_boundary + (tb - __ldg(e.bulk_prefix + m));
+          if (odd) persist_bulk<S, true>(md.d, pm, k, desc_s[w], lane);
+          else persist_bulk<S, false>(md.d, pm, k, desc_s[w], lane);
+        }
+        __syncwarp();
+      }
+    }
+    if (!grid_sync(gs, expected, gen, slot ^ 1, err0)) return;
+  }
+}
+
+template <class S>
+int ensemble_persistent_t(const EnsembleLaunch& e, const StepParams& p, int64_t n_steps,
+                          GridSync* gs, int extra, cudaStream_t s) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t r = cudaGetDevice(&dev);
+  if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (r == cudaSuccess)
+    r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ensemble_persistent<S>,
+                                                      kPersistWarps * 32, 0);
+  if (r != cudaSuccess) return (int)r;
+  if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+  const unsigned blocks = (unsigned)(per_sm * sms);
+  r = cudaMemsetAsync(gs, 0, sizeof(GridSync), s);
+  if (r != cudaSuccess) return (int)r;
+  unsigned expected = blocks + (unsigned)(extra > 0 ? extra : 0);
+  void* args[] = {(void*)&e, (void*)&p, (void*)&n_steps, (void*)&gs, (void*)&expected};
+  r = cudaLaunchCooperativeKernel((const void*)k_ensemble_persistent<S>, dim3(blocks),
+                                  dim3(kPersistWarps * 32), args, 0, s);
+  return (int)r;
 }
 
 __global__ void k_advance(int64_t* step, int64_t by) { *step += by; }
@@ -1056,6 +1202,15 @@ int launch_ensemble_step(int storage, const EnsembleLaunch& e, const StepParams&
   return dispatch(storage, [&](auto tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     return ensemble_step_t<S>(e, p, ss);
+  });
+}
+
+int launch_ensemble_persistent(int storage, const EnsembleLaunch& e, const StepParams& p,
+                               int64_t n_steps, GridSync* gs, int extra_arrivals, void* stream) {
+  if (n_steps <= 0) return 0;
+  return dispatch(storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    return ensemble_persistent_t<S>(e, p, n_steps, gs, extra_arrivals, (cudaStream_t)stream);
   });
 }
 

@@ -179,6 +179,23 @@ struct EnsembleLaunch {
 };
 int launch_ensemble_step(int storage, const EnsembleLaunch& e, const StepParams& p,
                          const StepStreams& ss);
+
+// Persistent ensemble kernel: one cooperative launch advances every member by
+// n_steps, CTAs taking chunks of tiles from a device counter and meeting at a
+// grid barrier after each step (bounded spin: a barrier that does not complete
+// sets kErrTimeout in member 0's flag and every CTA returns).  `sync` is
+// device memory the launcher clears; `extra_arrivals` > 0 makes every barrier
+// wait for arrivals that never come (fault-injection hook for tests).
+struct GridSync {
+  unsigned int arrive;
+  unsigned int gen;
+  unsigned int abort;
+  unsigned int pad;
+  unsigned long long work[2];
+};
+int launch_ensemble_persistent(int storage, const EnsembleLaunch& e, const StepParams& p,
+                               int64_t n_steps, GridSync* sync, int extra_arrivals,
+                               void* stream);
 int launch_advance(int64_t* step_dev, int64_t by, void* stream);
 int launch_init(int storage, const DevLattice& d, const double* rho, const double* u,
                 void* stream);

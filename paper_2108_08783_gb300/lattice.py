@@ -258,7 +258,7 @@ class Ensemble:
         self.h = h
         self.stream = self.members[0].stream  # the ensemble's work is ordered with it
         self.n = sum(m.n for m in self.members)
-        self.settings = {"prefetch": None, "schedule": 0, "graph_steps": 0}
+        self.settings = {"prefetch": None, "schedule": 0, "graph_steps": 0, "persistent": 0}
 
     def _check(self, rc):
         if rc != A.LBM_OK:
@@ -270,7 +270,8 @@ class Ensemble:
     def sync(self):
         self._check(self._lib.lbm_ensemble_sync(self.h))
 
-    def tune(self, prefetch=None, schedule=None, graph_steps=None):
+    def tune(self, prefetch=None, schedule=None, graph_steps=None, persistent=None,
+             barrier_extra=None):
         if prefetch is not None:
             self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_PREFETCH, int(prefetch)))
             self.settings["prefetch"] = int(prefetch)
@@ -281,6 +282,13 @@ class Ensemble:
             self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_GRAPH_STEPS,
                                                     int(graph_steps)))
             self.settings["graph_steps"] = int(graph_steps)
+        if persistent is not None:
+            self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_PERSISTENT,
+                                                    int(persistent)))
+            self.settings["persistent"] = int(persistent)
+        if barrier_extra is not None:
+            self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_BARRIER_EXTRA,
+                                                    int(barrier_extra)))
 
     def time_steps(self, n):
         """Device ms of n steps (CUDA events on the ensemble's stream)."""
@@ -295,14 +303,15 @@ class Ensemble:
         return e0.elapsed_time(e1)
 
     def autotune(self, prefetch=(0, 1024, 2048, 4096, 8192), schedule=(0, 1),
-                 graph_steps=(0, 20), trial_steps=40):
+                 graph_steps=(0, 20), persistent=(0, 1), trial_steps=40):
         """Choose the schedule knobs by timing each candidate on this ensemble
         (coordinate search, one knob at a time).  Every trial advances the
         members by ``trial_steps`` steps."""
         results = []
-        best = dict(prefetch=prefetch[0], schedule=schedule[0], graph_steps=graph_steps[0])
+        best = dict(prefetch=prefetch[0], schedule=schedule[0], graph_steps=graph_steps[0],
+                    persistent=persistent[0])
         for knob, cands in (("schedule", schedule), ("prefetch", prefetch),
-                            ("graph_steps", graph_steps)):
+                            ("graph_steps", graph_steps), ("persistent", persistent)):
             times = {}
             for v in cands:
                 cfg = dict(best)

@@ -44,15 +44,15 @@ def _lattices(members, storage):
     return lats
 
 
-@pytest.mark.parametrize("graph_steps", [0, 4])
+@pytest.mark.parametrize("graph_steps,persistent", [(0, 0), (4, 0), (0, 1)])
 @pytest.mark.parametrize("storage", ["f32", "f16s"])
-def test_ensemble_equals_members_alone(storage, graph_steps):
+def test_ensemble_equals_members_alone(storage, graph_steps, persistent):
     from paper_2108_08783_gb300 import Ensemble
     members = _members()
     alone = _lattices(members, storage)
     batch = _lattices(members, storage)
     ens = Ensemble(batch)
-    ens.tune(graph_steps=graph_steps, schedule=1, prefetch=64)
+    ens.tune(graph_steps=graph_steps, schedule=1, prefetch=64, persistent=persistent)
     for chunk in (5, 10, 9):  # odd and even counts, graph replays plus direct steps
         ens.step(chunk)
         for lat in alone:
@@ -94,3 +94,30 @@ def test_ensemble_rejects_mixed_members():
     c[0].step(1)
     with pytest.raises(LbmError):
         Ensemble(c)
+
+
+def test_persistent_grid_barrier_times_out_and_the_context_survives():
+    """Fault injection on the host side: the grid barrier is told to wait for
+    one arrival that never comes; every CTA gives up after its bounded spin,
+    lbm_ensemble_sync reports LBM_ETIMEOUT, and the same lattices step on
+    normally afterwards."""
+    from paper_2108_08783_gb300 import Ensemble, LbmError
+    members = _members(n=3)
+    lats = _lattices(members, "f32")
+    ens = Ensemble(lats)
+    ens.tune(persistent=1, barrier_extra=1)
+    ens.step(3)
+    with pytest.raises(LbmError) as e:
+        ens.sync()
+    assert e.value.status == -5  # LBM_ETIMEOUT
+    ens.tune(barrier_extra=0)
+    for lat in lats:
+        lat.init_fields()
+    ens.step(4)
+    ens.sync()
+    alone = _lattices(members, "f32")
+    for a, b in zip(alone, lats):
+        a.step(4)
+        a.sync()
+        np.testing.assert_allclose(b.populations(), a.populations(), rtol=0, atol=ATOL["f32"])
+    ens.close()
