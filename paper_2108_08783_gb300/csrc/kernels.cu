@@ -738,12 +738,15 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
 
 // ------------------------------------------------- persistent ensemble kernel
 // Every CTA stays resident for the whole launch (cooperative launch) and
-// loops over the steps: its warps take chunks of kPersistChunk tiles from a
+// loops over the steps: its warps take chunks of tiles from a
 // per-step device counter - boundary tiles of all members first, then bulk
-// tiles - and the grid meets at a barrier between steps.
+// tiles - and the grid meets at a barrier between steps.  The chunk grows
+// with the work per warp (1 for small ensembles, where a warp's chunk is the
+// critical path of a step; up to 16 for large ones, to keep the counter's
+// atomics few).
 
 constexpr int kPersistWarps = 8;
-constexpr int kPersistChunk = 16;
+constexpr int kPersistChunkMax = 16;
 constexpr long long kBarrierCycles = 1ll << 31;  // ~1 s at the GB300 SM clock
 
 // Grid barrier: bounded spin; false (every thread of the CTA) on timeout.
@@ -795,7 +798,7 @@ __device__ __noinline__ void persist_bulk(const DevLattice& d, const StepParams&
 template <class S>
 __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
     k_ensemble_persistent(const EnsembleLaunch e, const StepParams p, int64_t n_steps,
-                          GridSync* gs, unsigned expected) {
+                          GridSync* gs, unsigned expected, int chunk) {
   using C = typename Codec<S>::C;
   __shared__ __align__(128) int32_t stage[kPersistWarps][18 * kTile];
   __shared__ __align__(16) C gsm[kPersistWarps][kQ * kTile];
@@ -819,11 +822,11 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
       if (lane == 0) {
         t0 = *static_cast<volatile unsigned*>(&gs->abort) ? (unsigned long long)total
                                                           : atomicAdd(&gs->work[slot],
-                                                                      (unsigned long long)kPersistChunk);
+                                                                      (unsigned long long)chunk);
       }
       t0 = __shfl_sync(0xffffffffu, t0, 0);
       if ((int64_t)t0 >= total) break;
-      const int64_t t1 = (int64_t)t0 + kPersistChunk < total ? (int64_t)t0 + kPersistChunk : total;
+      const int64_t t1 = (int64_t)t0 + chunk < total ? (int64_t)t0 + chunk : total;
       for (int64_t t = (int64_t)t0; t < t1; ++t) {
         if (t < e.n_boundary_tiles) {
           const int m = find_member(e.boundary_prefix, e.n_members, t);
@@ -870,7 +873,9 @@ int ensemble_persistent_t(const EnsembleLaunch& e, const StepParams& p, int64_t 
   r = cudaMemsetAsync(gs, 0, sizeof(GridSync), s);
   if (r != cudaSuccess) return (int)r;
   unsigned expected = blocks + (unsigned)(extra > 0 ? extra : 0);
-  void* args[] = {(void*)&e, (void*)&p, (void*)&n_steps, (void*)&gs, (void*)&expected};
+  const int64_t per_warp = (e.n_boundary_tiles + e.n_bulk_tiles) / ((int64_t)blocks * kPersistWarps * 8);
+  int chunk = (int)(per_warp < 1 ? 1 : (per_warp > kPersistChunkMax ? kPersistChunkMax : per_warp));
+  void* args[] = {(void*)&e, (void*)&p, (void*)&n_steps, (void*)&gs, (void*)&expected, (void*)&chunk};
   r = cudaLaunchCooperativeKernel((const void*)k_ensemble_persistent<S>, dim3(blocks),
                                   dim3(kPersistWarps * 32), args, 0, s);
   return (int)r;
