@@ -762,6 +762,7 @@ __device__ bool grid_sync(GridSync* gs, unsigned expected, unsigned& gen, int ne
       atomicAdd(&gs->gen, 1u);
     } else {
       const long long t0 = clock64();
+      unsigned ns = 32;
       while (*static_cast<volatile unsigned*>(&gs->gen) == gen) {
         if (clock64() - t0 > kBarrierCycles) {
           atomicOr(err, kErrTimeout);
@@ -769,7 +770,8 @@ __device__ bool grid_sync(GridSync* gs, unsigned expected, unsigned& gen, int ne
           ok = 0;
           break;
         }
-        __nanosleep(256);
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;  // short sleeps first: most waits are brief
       }
     }
     __threadfence();
