@@ -191,6 +191,33 @@ def cpu_config1_full_run():
     return time.perf_counter() - t0, orc.n
 
 
+def wall_cost(args, geo, params, steps=2000):
+    """ms per step of the elastic wall and of rigid bounce-back on the same
+    workload and storage (the paper finds the elastic step no dearer)."""
+    import torch
+    from paper_2108_08783_gb300 import Lattice
+    out = {}
+    for model in ("elastic", "bounceback"):
+        lat = Lattice(geo.labels, geo.iolets, storage=args.storage, tau=params["tau"])
+        if model == "elastic":
+            lat.set_wall("elastic", rho0=params["rho0"], F=params["F"], kappa=params["kappa"])
+        else:
+            lat.set_wall("bounceback")
+        lat.step(20)
+        lat.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(lat.stream)
+        lat.step(steps)
+        e1.record(lat.stream)
+        e1.synchronize()
+        lat.sync()
+        out[model + "_ms_per_step"] = e0.elapsed_time(e1) / steps
+        lat.close()
+    out["elastic_over_rigid"] = out["elastic_ms_per_step"] / out["bounceback_ms_per_step"]
+    return out
+
+
 def precision_study(args, geo, params, steps, budget=5e-3):
     """MLUPS and error of each storage against the FP64 path on the same workload
     (all from rest, `steps` steps): rel-L2 of the wall shear stress at the wall
@@ -456,6 +483,7 @@ def run_ours(args):
     prec = None
     if rank == 0 and not args.no_precision:
         prec = precision_study(args, geo, params, args.precision_steps)
+    walls = wall_cost(args, geo, params) if rank == 0 and not args.no_precision else None
     # ---------------------------------------------------------------- CPU baseline
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -479,6 +507,7 @@ def run_ours(args):
                        "wall": "elastic GZS", "l2": "populations (%.0f MB) exceed L2; no flush"
                        % (19 * s * n / 1e6), "parallelism": "replicas x%d" % ws},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": prec,
+            "wall_cost": walls,
             "gpu_launches": int(n_bulk_l + n_bnd_l),
             "clocks": clk,
         }
