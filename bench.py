@@ -21,6 +21,8 @@ needed between steps.
              the same step when the recorded kernel source matches;
   cpu_baseline  the FP64 CPU oracle on the same workload, a bounded number of
              steps on all host cores;
+  wall_cost  ms per step with the elastic wall and with rigid bounce-back on the
+             same workload (the paper reports the elastic step no dearer);
   mixed_precision  every storage (FP64/FP32/FP16S/BF16S) run from rest on the
              same workload: MLUPS, and the rel-L2 error of the wall shear
              stress and of u against the FP64 path, with the speed-up over
