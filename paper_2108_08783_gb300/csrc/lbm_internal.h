@@ -15,10 +15,6 @@ namespace lbm {
 
 constexpr int kQ = 19;
 constexpr int kTile = 32;          // sites per tile = one warp
-#ifndef LBM_WARPS_PER_CTA
-#define LBM_WARPS_PER_CTA 4
-#endif
-constexpr int kWarpsPerCta = LBM_WARPS_PER_CTA;  // step kernel: tiles (warps) per CTA
 
 // Flag bits shared by TileDesc::mask and the per-slot masks.  Bits 1..18 mark
 // the non-fluid directions (wall or iolet links).
