@@ -181,8 +181,8 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def cpu_config1_full_run():
-    """Wall seconds of the oracle's full config-1 run (R = 8, L = 64 tube, 2000
+def cpu_short_tube_full_run():
+    """Wall seconds of the oracle's full run of the short tube (R = 8, L = 64, 2000
     steps from rest, all host cores)."""
     from oracle import Oracle
     import lbm_inputs as I
@@ -292,7 +292,7 @@ ENSEMBLE_STEPS = 2000  # timed steps of the ensemble workload (at most)
 
 
 def ensemble_members(seed=0, count=256):
-    """Config-4 family: radius U(6,24), length U(64,512), Eh/r0 log-U(0.05,5),
+    """The 256-tube ensemble family: radius U(6,24), length U(64,512), Eh/r0 log-U(0.05,5),
     inlet period U(1000,5000), tau U(0.55,1.0); F = 0.85, parabolic pulsatile
     inlet of mean 0.01 + 0.005 sin(2 pi n / T).
 
@@ -491,14 +491,14 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         mlups, threads, steps, dt = cpu_oracle(geo, params, seconds=args.cpu_seconds)
         m1, _, steps1, dt1 = cpu_oracle(geo, params, seconds=3.0, max_steps=50, threads=1)
-        c1_s, c1_n = cpu_config1_full_run()
+        c1_s, c1_n = cpu_short_tube_full_run()
         cpu = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                "sample": "%d FP64 oracle steps of the same workload (%.1f s)" % (steps, dt),
                "single_thread_mlups": m1,
                "single_thread_sample": "%d steps (%.1f s)" % (steps1, dt1),
                "cpu_model": cpu_model(),
-               "config1_full_run_s": c1_s,
-               "config1": "R=8 L=64 tube (%d sites), 2000 steps from rest, all cores" % c1_n}
+               "short_tube_full_run_s": c1_s,
+               "short_tube": "R=8 L=64 tube (%d sites), 2000 steps from rest, all cores" % c1_n}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,

@@ -34,7 +34,7 @@ def _declared():
     return sorted(names)
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_calls():
     names = _declared()
     for n in ("lbm_build_lattice", "lbm_set_wall_params", "lbm_step", "lbm_moments"):
         assert n in names

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 TOL = {"f64": 1e-10, "f32": 1e-5}
 
 
-def _config1(length=64, **kw):
+def _short_tube(length=64, **kw):
     # radius 8, length 64, peak inlet 0.05 (mean 0.025), rho_out = 1
     return I.tube(8, length, u_mean=0.025, **kw)
 
@@ -34,7 +34,7 @@ def _compare(lat, orc, tol, what=""):
 # ------------------------------------------------------------------ integer build
 
 @pytest.mark.parametrize("geo", [
-    _config1(), _config1(63), I.duct(5, 7, 33), I.closed_box(9, 11, 13),
+    _short_tube(), _short_tube(63), I.duct(5, 7, 33), I.closed_box(9, 11, 13),
     I.tube(12, 40, u_mean=0.01, u_amp=0.01, period=300.0, profile=1),
 ] + [I.random_labels(s, shape) for s, shape in enumerate(
     [(8, 8, 8), (9, 13, 11), (16, 16, 16), (17, 23, 31), (32, 32, 32), (12, 40, 7)])],
@@ -58,14 +58,14 @@ def test_lattice_build_bit_exact(geo):
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("wall_model", [1, 0])
-def test_config1_1000_steps(storage, wall_model):
-    """Config-1 tube (tau 0.8, peak inlet 0.05, rho_out 1, kappa 12, F 0.85) from rest."""
-    geo = _config1()
+def test_short_tube_1000_steps(storage, wall_model):
+    """R = 8, L = 64 tube (tau 0.8, peak inlet 0.05, rho_out 1, kappa 12, F 0.85) from rest."""
+    geo = _short_tube()
     lat, orc = make_pair(geo, storage, tau=0.8, wall_model=wall_model, F=0.85, kappa=12.0)
     lat.step(1000)
     lat.sync()
     orc.run(1000)
-    _compare(lat, orc, TOL[storage], "config1")
+    _compare(lat, orc, TOL[storage], "short tube")
     if wall_model == 1:
         dEl, Uwl = lat.wall_state()
         dEo, Uwo = orc.wall_state()
@@ -80,7 +80,7 @@ def test_config1_1000_steps(storage, wall_model):
 def test_ragged_tail_random_start_odd_steps(storage):
     """L = 63 (ragged last tile), smooth random initial fields, odd step count,
     per-wall-site F and kappa from a seeded per-voxel field."""
-    geo = _config1(63)
+    geo = _short_tube(63)
     rng = np.random.default_rng(11)
     F_grid = rng.uniform(0.0, 1.0, geo.shape)
     K_grid = rng.uniform(0.0, 40.0, geo.shape)
@@ -140,7 +140,7 @@ def test_zero_and_single_site_lattices():
 # ------------------------------------------------------------------ state API
 
 def test_populations_roundtrip_and_checkpoint_resume():
-    geo = _config1(40)
+    geo = _short_tube(40)
     lat, orc = make_pair(geo, "f32", tau=0.8, wall_model=1, F=0.85, kappa=12.0,
                          fields=I.random_fields(2, geo.shape))
     lat.step(7)  # odd layout
@@ -175,8 +175,8 @@ def test_unstable_run_is_flagged():
 # ------------------------------------------------------------------ full-size sampled parity
 
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f64", 1e-10)])
-def test_config2_full_size_short_run(storage, tol):
-    """Config 2 at full size (R = 40, L = 1024, ~5.1 M sites, tau 0.6, pulsatile
+def test_long_tube_full_size_short_run(storage, tol):
+    """The long tube at full size (R = 40, L = 1024, ~5.1 M sites, tau 0.6, pulsatile
     inlet 0.03 + 0.02 sin(2 pi n / 4000), Eh/r0 = 0.5 -> kappa 60), 20 steps
     from a seeded smooth random state, all sites compared with the oracle."""
     geo = I.tube(40, 1024, u_mean=0.03, u_amp=0.02, period=4000.0)
@@ -184,7 +184,7 @@ def test_config2_full_size_short_run(storage, tol):
                          fields=I.random_fields(7, geo.shape, drho=1e-3, umax=0.03, smooth=1))
     lat.step(20)
     orc.run(20)
-    _compare(lat, orc, tol, "config2")
+    _compare(lat, orc, tol, "long tube")
 
 
 # ------------------------------------------------------------------ reduced precision
@@ -192,11 +192,11 @@ def test_config2_full_size_short_run(storage, tol):
 @pytest.mark.parametrize("storage,bound,wss_bound", [("f32", 1e-5, 2e-5), ("f16s", 2e-3, 5e-3),
                                                      ("bf16s", 6e-2, 6e-2)])
 def test_shifted_storage_error_bounds(storage, bound, wss_bound):
-    """Stated bounds for each storage after 1000 steps on config 1 against the
+    """Stated bounds for each storage after 1000 steps on the short tube against the
     FP64 oracle: rel-L2 of (rho - 1), of u and of the wall shear stress at the
     wall sites.  BF16 keeps 8 significant bits, so its bounds are looser
     (measured 3.2e-2 on rho - 1)."""
-    geo = _config1()
+    geo = _short_tube()
     lat, orc = make_pair(geo, storage, tau=0.8, wall_model=1, F=0.85, kappa=12.0)
     lat.step(1000)
     orc.run(1000)
@@ -215,8 +215,8 @@ def test_shifted_storage_error_bounds(storage, bound, wss_bound):
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-5)])
 def test_wss_matches_oracle(storage, tol):
     """WSS at the wall sites (deviatoric stress of f^neq, tangential traction
-    for the analytic outward normal) after 600 steps of the config-1 tube."""
-    geo = _config1()
+    for the analytic outward normal) after 600 steps of the short tube."""
+    geo = _short_tube()
     lat, orc = make_pair(geo, storage, tau=0.8, wall_model=1, F=0.85, kappa=12.0)
     lat.step(600)
     orc.run(600)

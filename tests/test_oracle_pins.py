@@ -322,8 +322,8 @@ def test_rigid_womersley_tube():
 
 # ----------------------------------------------------------- elastic vs rigid trend
 
-def test_elastic_vs_rigid_trend_config1():
-    """Config-1 tube (R = 8, L = 64, tau = 0.8, peak 0.05, kappa = 12, F = 0.85):
+def test_elastic_vs_rigid_trend_short_tube():
+    """Short tube (R = 8, L = 64, tau = 0.8, peak 0.05, kappa = 12, F = 0.85):
     the elastic wall moves fluid faster next to the wall and needs a smaller
     pressure drop than bounce-back (Sec. 2.4 comparison)."""
     g = I.tube(8, 64, u_mean=0.025)
@@ -377,9 +377,9 @@ def test_sec24_cylinder_numbers():
     h = vals["thickness_over_R"] * vals["radius"]
     k = A.tube_law_coefficient(vals["radius"], vals["young"], h, vals["poisson"])
     assert abs(k - 1.125e-6) < 1e-18
-    # the same coefficient through the stiffness parameter Eh/r0 used by the configs
+    # the same coefficient through the stiffness parameter Eh/r0 used by the workloads
     assert abs(A.kappa_lattice(vals["radius"], vals["young"] * h / vals["radius"]) - k) < 1e-18
-    # config 1: r0 = 8, Eh/r0 = 0.5 (lattice units) -> kappa = 12
+    # the short tube: r0 = 8, Eh/r0 = 0.5 (lattice units) -> kappa = 12
     assert A.kappa_lattice(8.0, 0.5) == 12.0
 
 
