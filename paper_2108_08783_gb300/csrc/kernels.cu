@@ -318,10 +318,20 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
   const C omega = C(omega_t);
   Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
   chk_count(chk, P, P + x, kQ * np, err);
+  // Opposite directions a, b = opp(a) share c_b = -c_a, so their shifted
+  // equilibria split into an even part w (drho + rho (4.5 cu^2 - 1.5 u^2)) and
+  // an odd part 3 w rho cu: g^eq_a = even + odd, g^eq_b = even - odd.
+  const C wd1 = m.drho * C(1.0 / 18.0), wd2 = m.drho * C(1.0 / 36.0);
+  const C wr1 = m.rho * C(1.0 / 18.0), wr2 = m.rho * C(1.0 / 36.0);
+  const C w3r1 = m.rho * C(3.0 / 18.0), w3r2 = m.rho * C(3.0 / 36.0);
   unroll<9>([&](auto Pi) {
     constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
-    const C sa = g[a] + omega * (geq<a, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[a]);
-    const C sb = g[b] + omega * (geq<b, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[b]);
+    const C cu = cdot<a, C>(m.ux, m.uy, m.uz);
+    const C q = C(4.5) * cu * cu - m.usq;
+    const C even = (a <= 6) ? wd1 + wr1 * q : wd2 + wr2 * q;
+    const C odd = ((a <= 6) ? w3r1 : w3r2) * cu;
+    const C sa = g[a] + omega * ((even + odd) - g[a]);
+    const C sb = g[b] + omega * ((even - odd) - g[b]);
     if constexpr (ODD) {
       // The store to (x + c_a, a) hits the address the load of direction
       // opp(a) used; re-reading the offset from shared memory keeps the
