@@ -583,7 +583,10 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
 #define LBM_BULK_MINB 4
 #endif
 constexpr int kBulkWarps = 8;      // k_bulk: tiles (warps) per CTA
-constexpr int kBoundaryWarps = 4;  // k_boundary: tiles (warps) per CTA
+#ifndef LBM_BOUNDARY_WARPS
+#define LBM_BOUNDARY_WARPS 4
+#endif
+constexpr int kBoundaryWarps = LBM_BOUNDARY_WARPS;  // k_boundary: tiles (warps) per CTA
 
 // Bulk tile at launch position k (whole warp); dsc: the warp's 20-word area.
 template <class S, bool ODD>
