@@ -580,9 +580,12 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
 }
 
 #ifndef LBM_BULK_MINB
-#define LBM_BULK_MINB 4
+#define LBM_BULK_MINB 8
 #endif
-constexpr int kBulkWarps = 8;      // k_bulk: tiles (warps) per CTA
+#ifndef LBM_BULK_WARPS
+#define LBM_BULK_WARPS 4
+#endif
+constexpr int kBulkWarps = LBM_BULK_WARPS;  // k_bulk: tiles (warps) per CTA
 #ifndef LBM_BOUNDARY_WARPS
 #define LBM_BOUNDARY_WARPS 4
 #endif
@@ -610,7 +613,7 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
 }
 
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK_MINB)
+__global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 16 / kBulkWarps : LBM_BULK_MINB)
     k_bulk(const DevLattice d, const StepParams p) {
   __shared__ __align__(16) int32_t desc_s[kBulkWarps][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -715,7 +718,7 @@ __device__ __forceinline__ int find_member(const int64_t* prefix, int32_t nm, in
 }
 
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 2 : LBM_BULK_MINB)
+__global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 16 / kBulkWarps : LBM_BULK_MINB)
     k_bulk_ens(const EnsembleLaunch e, const StepParams p) {
   __shared__ __align__(16) int32_t desc_s[kBulkWarps][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
