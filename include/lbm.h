@@ -148,6 +148,15 @@ int lbm_moments(lbm_ctx *ctx, double *rho, double *u, int32_t dst_is_device);
  * is then cleared), LBM_ECUDA on a CUDA error, else LBM_OK. */
 int lbm_sync(lbm_ctx *ctx);
 
+/* lbm_plan_lattice - the host half of lbm_build_lattice alone: the same
+ * validation and compaction on the host, no GPU and no context, returning the
+ * sizes the build would produce in out[8] (host): n_sites, n_wall_sites,
+ * n_wall_links, n_tiles, bulk tiles, coherent boundary tiles, irregular
+ * tiles, sites in bulk tiles (as lbm_info).  Errors as lbm_build_lattice,
+ * message via lbm_last_error(NULL). */
+int lbm_plan_lattice(const uint8_t *labels, int32_t nx, int32_t ny, int32_t nz,
+                     const lbm_iolet *iolets, int32_t n_iolets, double tau, int64_t out[8]);
+
 /* lbm_info - sizes of the context:
  *   out[0] n_sites, [1] n_wall_sites, [2] n_wall_links, [3] n_tiles (32 sites),
  *   [4] bulk tiles, [5] uniform boundary tiles, [6] irregular tiles,

@@ -27,7 +27,7 @@ EXPORTS = (
     "lbm_checkpoint_load", "lbm_wss", "lbm_set_stream", "lbm_last_error", "lbm_status_string",
     "lbm_destroy", "lbm_profile", "lbm_profile_read", "lbm_reduce_noalloc",
     "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_sync", "lbm_ensemble_tune",
-    "lbm_ensemble_last_error", "lbm_ensemble_destroy", "lbm_fmap",
+    "lbm_ensemble_last_error", "lbm_ensemble_destroy", "lbm_fmap", "lbm_plan_lattice",
     # include/lbm_mlp.h
     "lbm_mlp_create", "lbm_mlp_param_count", "lbm_mlp_set_params", "lbm_mlp_get_params",
     "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train_step", "lbm_mlp_sync",
@@ -117,6 +117,7 @@ def lib():
         "lbm_ensemble_last_error": ([P], C.c_char_p),
         "lbm_ensemble_destroy": ([P], None),
         "lbm_fmap": ([P, i64, P, i64, dbl, dbl, P], C.c_int),
+        "lbm_plan_lattice": ([P, i32, i32, i32, P, i32, dbl, P], C.c_int),
         "lbm_mlp_create": ([i32, i32, i32, i32, i64, P, P, C.POINTER(P)], C.c_int),
         "lbm_mlp_param_count": ([P, P], C.c_int),
         "lbm_mlp_set_params": ([P, P, i32], C.c_int),

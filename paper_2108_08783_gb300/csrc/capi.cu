@@ -493,6 +493,34 @@ int lbm_moments(lbm_ctx* c, double* rho, double* u, int32_t dst_is_device) {
   return sync(c, "lbm_moments");
 }
 
+int lbm_plan_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
+                     const lbm_iolet* iolets, int32_t n_iolets, double tau, int64_t out[8]) {
+  g_build_err.clear();
+  if (!out) return LBM_EINVAL;
+  HostLattice L;
+  std::string err;
+  int rc;
+  try {
+    rc = lbm::build_lattice(labels, nx, ny, nz, iolets, n_iolets, tau, L, err);
+  } catch (const std::bad_alloc&) {
+    rc = LBM_ENOMEM;
+    err = "host allocation failed";
+  }
+  if (rc != LBM_OK) {
+    g_build_err = err;
+    return rc;
+  }
+  out[0] = L.n;
+  out[1] = (int64_t)L.wall_sites.size();
+  out[2] = L.n_wall_links;
+  out[3] = L.n_tiles;
+  out[4] = L.n_bulk;
+  out[5] = L.n_uniform;
+  out[6] = L.n_irregular;
+  out[7] = L.bulk_sites;
+  return LBM_OK;
+}
+
 int lbm_info(const lbm_ctx* c, int64_t out[12]) {
   if (!c || !out) return LBM_EINVAL;
   const HostLattice& L = c->L;
