@@ -431,3 +431,35 @@ def test_rigid_wall_shear_exceeds_elastic():
         out[wm] = o.wss(s, I.wall_normals(g, ex["coords"][s]))
     assert out[0].mean() > 2 * out[1].mean()
     assert np.mean(out[0] >= out[1]) > 0.9
+
+
+def test_reduce_flux_balances_and_matches_the_duct_flow_rate():
+    """Steady pressure-driven duct (bounce-back): the oracle's per-iolet flux
+    (sum of rho u . axis over the sites touching the iolet) is the same at
+    inlet and outlet (mass balance) and equals the node sum of rho times the
+    rectangular-duct series velocity on the end planes."""
+    n, tau = 10, 1.0
+    nu = A.viscosity(tau)
+    L = 2 * n
+    G0 = 0.01 * nu / (0.0737 * n * n)
+    d = 1.5 * G0 * L
+    g = I.duct(n, n, L, rho_in=1 + d, rho_out=1 - d)
+    o = Oracle(g.labels, g.iolets, tau=tau, wall_model=0, F=0.0, kappa=0.0)
+    o.run(int(3.0 * n * n / nu))
+    red = o.reduce()
+    q_in, q_out = red[1], red[2]
+    assert q_in > 0 and q_out > 0
+    assert abs(q_in - q_out) < 1e-6 * q_in
+    rho, u = o.moments()
+    c = o.coords()
+    zm = L // 2 + 1
+    plane = lambda z: c[:, 2] == z
+    G = -(rho[plane(zm + 1)].mean() - rho[plane(zm - 1)].mean()) / 2.0 / 3.0
+    m = plane(zm)
+    mu = rho[m].mean() * nu
+    cx = (n + 1) / 2.0
+    ua = duct_velocity(c[m, 0] - cx, c[m, 1] - cx, n / 2.0, n / 2.0, G, mu)
+    q_series = float(np.sum(rho[m] * ua))
+    assert abs(q_in - q_series) < 1e-2 * q_series
+    # the site sum over the mid plane carries the same flux
+    assert abs(float(np.sum(rho[m] * u[m, 2])) - q_in) < 1e-3 * q_in
