@@ -463,3 +463,36 @@ def test_reduce_flux_balances_and_matches_the_duct_flow_rate():
     assert abs(q_in - q_series) < 1e-2 * q_series
     # the site sum over the mid plane carries the same flux
     assert abs(float(np.sum(rho[m] * u[m, 2])) - q_in) < 1e-3 * q_in
+
+
+def _steady_tube(rho_out, u0=0.01, R=6.0, L=24):
+    g = I.tube(R, L, u_mean=u0, rho_out=rho_out)
+    o = Oracle(g.labels, g.iolets, tau=0.8, wall_model=0, F=0.0, kappa=0.0)
+    o.run(2500)
+    rho, u = o.moments()
+    return o, rho, u, o.coords()
+
+
+def test_parabolic_inlet_carries_its_mean_velocity():
+    """A steady parabolic velocity inlet of mean u (R9: 2(1 - r^2/R^2) scaled to
+    unit mean over the disc) delivers a flux of about rho u per inlet-plane
+    node once the tube is steady (the node sum of the profile differs from
+    its disc mean by the discretisation only)."""
+    u0 = 0.01
+    o, rho, u, c = _steady_tube(1.0, u0)
+    first = c[:, 2] == 1
+    per_node = o.reduce()[1] / first.sum()
+    assert abs(per_node / (rho[first].mean() * u0) - 1.0) < 0.02
+
+
+def test_density_outlet_sets_the_pressure_level():
+    """Raising the outlet density by delta raises the density everywhere in a
+    steady, incompressible-regime tube by delta (the flow, set by the inlet,
+    does not change): the outlet fixes the pressure level."""
+    delta = 1e-3
+    _, r0, u0, c = _steady_tube(1.0)
+    _, r1, u1, _ = _steady_tube(1.0 + delta)
+    shift = r1 - r0
+    assert abs(shift.mean() / delta - 1.0) < 0.05
+    assert np.std(shift) < 0.05 * delta
+    assert np.max(np.abs(u1 - u0)) < 1e-3 * np.max(np.abs(u0))
