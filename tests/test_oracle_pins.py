@@ -17,6 +17,10 @@ transposed operand) fails at least one of them:
 * velocity inlet: rigid Womersley flow at alpha = 4 (the M = 1, c -> infinity
   limit of the Sec. 2.2 solution) within 5 %;
 * complex Bessel series against scipy;
+* the tube-law expansion and the wall velocity exported per wall site against
+  the moments the step read (bit for bit for the expansion);
+* the F ratio against the radial mode of the Womersley momentum balance
+  integrated numerically;
 * unit conversions against Table A1 and Sec. 2.4.
 """
 import os
@@ -267,6 +271,53 @@ def test_wall_state_export():
     assert np.all(np.isfinite(Uw))
 
 
+def test_wall_state_is_the_tube_law_of_the_local_pressure():
+    """Sec. 2.4 tube law dE = kappa (p - P0), clamped at 0, with the lattice
+    pressure p - P0 = c_s^2 (rho - rho0) (Eq. Pressure), and Sec. 2.3's
+    U_w = (F + dr - dx)/dr u_f with dr = dx + dE.
+
+    The moments are read from the populations held before the last step
+    (summed here in the oracle's order, so the expansion is compared bit for
+    bit), c_s^2 comes from the velocity set's own second moment, kappa is
+    large enough that dE is O(0.1 - 1) (a dropped or doubled c_s^2 changes
+    it by a factor 3), rho0 sits inside the range of the wall densities so
+    that the clamp acts on some sites and not on others, and F and kappa vary
+    per wall site (a shuffled site index fails)."""
+    c, w, _ = velocity_set()
+    cs2 = float(np.sum(w * c[:, 0].astype(np.float64) ** 2))
+    inv_cs2 = float(round(1.0 / cs2))
+    assert abs(1.0 / cs2 - inv_cs2) < 1e-14 and inv_cs2 == 3.0
+    g = I.tube(6, 24, u_mean=0.02)
+    o = Oracle(g.labels, g.iolets, tau=0.8, wall_model=1)
+    ws = o.export()["wall_sites"]
+    coords = o.coords()
+    rng = np.random.default_rng(4)
+    F = rng.uniform(0.0, 1.0, ws.size)
+    kappa = rng.uniform(30.0, 300.0, ws.size)
+    rho_g, u_g = I.random_fields(3, g.shape, drho=2e-3, umax=0.02)
+    o.init_equilibrium(I.gather(rho_g, coords), I.gather(u_g, coords))
+    o.run(5)
+    f = o.populations()[ws]
+    rho = np.zeros(ws.size)
+    j = np.zeros((ws.size, 3))
+    for i in range(19):  # the oracle's summation order
+        rho = rho + f[:, i]
+        j = j + f[:, i:i + 1] * c[i].astype(np.float64)
+    u = j / rho[:, None]
+    rho0 = float(np.median(rho))
+    o.configure(0.8, 1, rho0, F, kappa)
+    o.run(1)
+    dE, Uw = o.wall_state()
+    want = kappa * np.maximum(0.0, (rho - rho0) / inv_cs2)
+    np.testing.assert_array_equal(dE, want)
+    assert 0.1 < dE.max() < 3.0 and np.count_nonzero(dE == 0.0) > ws.size // 4
+    ratio = (F + dE) / (1.0 + dE)
+    np.testing.assert_allclose(Uw, ratio[:, None] * u, rtol=0, atol=1e-15)
+    # the expansion moves U_w from F u_f (dE = 0) toward u_f
+    big = dE > 0.1
+    assert np.all(np.abs(Uw[big, 2]) > np.abs(F[big] * u[big, 2]) - 1e-18)
+
+
 # ----------------------------------------------------------- Womersley
 
 def test_bessel_series_matches_scipy():
@@ -387,6 +438,42 @@ def test_f_ratio_limits():
     for alpha in (1.0, 3.0, 8.0):
         assert abs(A.f_ratio(alpha, 1e-9, 0.7) - 1.0) < 1e-6  # F -> 1 as dr -> 0
         assert abs(A.f_ratio(alpha, 0.05, 0.0) - 1.0) < 1e-15  # M = 0
+
+
+def _womersley_radial_mode(alpha, xi):
+    """y(xi) / y(1) for the radial part of the oscillating Womersley velocity,
+    integrated numerically from the momentum balance rather than taken from a
+    Bessel function: with time dependence e^(i omega t) (Sec. 2.2), the
+    homogeneous part of rho dw/dt = -dp/dz + mu (w'' + w'/r) is
+    y'' + y'/xi = i alpha^2 y in xi = r/R (alpha^2 = R^2 omega rho / mu),
+    regular at the axis (y(0) = 1, y'(0) = 0)."""
+    from scipy.integrate import solve_ivp
+    a2 = 1j * alpha * alpha
+    x0 = 1e-4  # start off the axis on the regular series y = 1 + a2 x^2/4 + a2^2 x^4/64
+    y0 = np.array([1 + a2 * x0 ** 2 / 4 + a2 ** 2 * x0 ** 4 / 64,
+                   a2 * x0 / 2 + a2 ** 2 * x0 ** 3 / 16], complex)
+    sol = solve_ivp(lambda x, y: [y[1], a2 * y[0] - y[1] / x], (x0, 1.0), y0, method="DOP853",
+                    rtol=1e-12, atol=1e-15, dense_output=True)
+    assert sol.success
+    return sol.sol(xi)[0] / sol.sol(1.0)[0]
+
+
+def test_f_ratio_matches_the_womersley_momentum_balance():
+    """Sec. 2.3's F = w(R) / w(R - dr) with w proportional to 1 - M J0(Lambda r/R)/J0(Lambda),
+    Lambda = i^(3/2) alpha, against the same ratio built from the radial mode
+    integrated from the momentum balance (no Bessel function, no Lambda): a
+    wrong phase of Lambda (i^(1/2) alpha gives the complex conjugate mode), a
+    dropped (1 - dr/R) or a swapped numerator fails."""
+    for alpha in (1.0, 3.0, 8.0):
+        for d in (0.02, 0.1, 0.3):
+            for M in (0.5, 0.9, 1.3 - 0.2j):
+                want = (1.0 - M) / (1.0 - M * _womersley_radial_mode(alpha, 1.0 - d))
+                got = A.f_ratio(alpha, d, M)
+                assert abs(got - want) <= 1e-8 * abs(want), (alpha, d, M, got, want)
+                # the conjugate mode (e^(-i omega t) convention) is distinguishable
+                if M == 0.9 and alpha >= 3.0:
+                    wrong = (1.0 - M) / (1.0 - M * np.conj(_womersley_radial_mode(alpha, 1.0 - d)))
+                    assert abs(got - wrong) > 1e-3 * abs(want)
 
 
 # ----------------------------------------------------------- wall shear stress
