@@ -208,9 +208,11 @@ int lbm_reduce(lbm_ctx *ctx, double *out);
  *   out_is_device  != 0: out is device memory, written asynchronously on the
  *                  context's stream; 0: out is host memory, the call waits.
  * The first call on a device looks up the array's device address (with the
- * context's device current) and caches it; make that first call before any
- * stream capture.  All calls share the array, so calls that overlap on the
- * GPU race; serialise them (one stream, or wait between calls).
+ * context's device current) and caches it for that CUDA context (a device
+ * reset or a new primary context makes the next call look it up again); make
+ * that first call before any stream capture.  All calls share the array, so
+ * calls that overlap on the GPU race; serialise them (one stream, or wait
+ * between calls).
  * Errors: LBM_EINVAL for NULL arguments or more than 255 iolets (beyond the
  * array); LBM_ECUDA. */
 int lbm_reduce_noalloc(lbm_ctx *ctx, double *out, int32_t out_is_device);
@@ -265,7 +267,12 @@ int lbm_wss(lbm_ctx *ctx, const int64_t *sites, const double *normals, int64_t m
  *                        lbm_ensemble_sync report LBM_ETIMEOUT;
  *   LBM_TUNE_BARRIER_EXTRA fault injection for tests: the grid barrier waits for
  *                        this many arrivals that never come (default 0), so a
- *                        persistent step times out instead of completing.
+ *                        persistent step times out instead of completing;
+ *   LBM_TUNE_BULK_SITES  sites per lane of the bulk kernel: 1 (a 32-site tile per
+ *                        warp), or 2 (two tiles per warp, each lane updating two
+ *                        z-adjacent sites with packed loads, stores and FP32
+ *                        pair arithmetic; FP32 and 16-bit storage only, FP64
+ *                        ignores it).
  * Before using a member's own calls (moments, wall state, ...) call
  * lbm_ensemble_sync.  Errors: LBM_EINVAL (bad arguments, mixed storage or
  * steps), LBM_ESTATE (members drifted apart), LBM_ENOMEM, LBM_ECUDA; the
@@ -276,7 +283,8 @@ enum {
   LBM_TUNE_SCHEDULE = 1,
   LBM_TUNE_GRAPH_STEPS = 2,
   LBM_TUNE_PERSISTENT = 3,
-  LBM_TUNE_BARRIER_EXTRA = 4
+  LBM_TUNE_BARRIER_EXTRA = 4,
+  LBM_TUNE_BULK_SITES = 5
 };
 int lbm_ensemble_create(lbm_ctx *const *members, int32_t n, lbm_ensemble **out);
 int lbm_ensemble_step(lbm_ensemble *ens, int64_t n_steps);
@@ -299,6 +307,13 @@ void lbm_ensemble_destroy(lbm_ensemble *ens);
  * arguments out of range.  Runs on the host; no context, no GPU. */
 int lbm_fmap(const double *alpha, int64_t n_alpha, const double *dr_over_R, int64_t n_dr,
              double M_re, double M_im, double *out);
+
+/* lbm_tune - launch knobs of one lattice (no effect on results beyond the
+ * rounding of the collision arithmetic): LBM_TUNE_PREFETCH (L2 prefetch
+ * distance of the bulk kernel, tiles, >= 0) and LBM_TUNE_BULK_SITES (1 or 2
+ * sites per lane of the bulk kernel), as for lbm_ensemble_tune.  Defaults are
+ * chosen per storage at build time.  LBM_EINVAL for another knob or value. */
+int lbm_tune(lbm_ctx *ctx, int32_t knob, int64_t value);
 
 /* lbm_set_stream - run subsequent work on another cudaStream_t. */
 int lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);

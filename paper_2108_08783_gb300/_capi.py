@@ -27,14 +27,14 @@ EXPORTS = (
     "lbm_checkpoint_load", "lbm_wss", "lbm_set_stream", "lbm_last_error", "lbm_status_string",
     "lbm_destroy", "lbm_profile", "lbm_profile_read", "lbm_reduce_noalloc",
     "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_sync", "lbm_ensemble_tune",
-    "lbm_ensemble_last_error", "lbm_ensemble_destroy", "lbm_fmap", "lbm_plan_lattice",
+    "lbm_ensemble_last_error", "lbm_ensemble_destroy", "lbm_fmap", "lbm_plan_lattice", "lbm_tune",
     # include/lbm_mlp.h
     "lbm_mlp_create", "lbm_mlp_param_count", "lbm_mlp_set_params", "lbm_mlp_get_params",
     "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train_step", "lbm_mlp_sync",
     "lbm_mlp_last_error", "lbm_mlp_destroy", "lbm_warm_features", "lbm_warm_start",
 )
 LBM_TUNE_PREFETCH, LBM_TUNE_SCHEDULE, LBM_TUNE_GRAPH_STEPS = 0, 1, 2
-LBM_TUNE_PERSISTENT, LBM_TUNE_BARRIER_EXTRA = 3, 4
+LBM_TUNE_PERSISTENT, LBM_TUNE_BARRIER_EXTRA, LBM_TUNE_BULK_SITES = 3, 4, 5
 
 
 class LbmIolet(C.Structure):
@@ -104,6 +104,7 @@ def lib():
         "lbm_checkpoint_load": ([P, P, C.c_size_t], C.c_int),
         "lbm_wss": ([P, P, P, i64, P], C.c_int),
         "lbm_set_stream": ([P, P], C.c_int),
+        "lbm_tune": ([P, i32, i64], C.c_int),
         "lbm_last_error": ([P], C.c_char_p),
         "lbm_status_string": ([C.c_int], C.c_char_p),
         "lbm_destroy": ([P], None),

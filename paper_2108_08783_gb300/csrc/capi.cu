@@ -21,6 +21,18 @@
 // GB300: FP32 gains from prefetching 4096 tiles ahead; the 16-bit storages are
 // issue-bound and lose more to the prefetch instructions than they gain; FP64
 // is ALU-bound either way.  -DLBM_DEFAULT_PREFETCH=n overrides.
+// Sites per lane of the bulk kernel by storage.  -DLBM_DEFAULT_BULK_SITES=n
+// overrides.
+inline int32_t default_bulk_sites(int storage) {
+#ifdef LBM_DEFAULT_BULK_SITES
+  (void)storage;
+  return LBM_DEFAULT_BULK_SITES;
+#else
+  (void)storage;
+  return 1;
+#endif
+}
+
 inline int64_t default_prefetch(int storage) {
 #ifdef LBM_DEFAULT_PREFETCH
   (void)storage;
@@ -53,6 +65,7 @@ struct lbm_ctx {
   double* red_out = nullptr;
   std::string err;
   int64_t prefetch = 0;  // L2 prefetch distance (tiles), set from the storage at build
+  int32_t bulk_sites = 1;  // sites per lane of the bulk kernel, set from the storage at build
   // optional per-kernel timing (lbm_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;  // 3 per profiled step
@@ -215,6 +228,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   if (!c) return LBM_ENOMEM;
   c->storage = storage;
   c->prefetch = default_prefetch(storage);
+  c->bulk_sites = default_bulk_sites(storage);
   c->tau = tau;
   c->stream = (cudaStream_t)cuda_stream;
   if (alloc) {
@@ -424,6 +438,7 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
   p.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
   p.prefetch = c->prefetch;
   p.step_dev = nullptr;
+  p.bulk_sites = c->bulk_sites;
   for (int64_t s = 0; s < n_steps; ++s) {
     p.step = c->step;
     p.write_state = s == n_steps - 1 ? 1 : 0;
@@ -448,6 +463,22 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
     ++c->step;
   }
   return LBM_OK;
+}
+
+int lbm_tune(lbm_ctx* c, int32_t knob, int64_t value) {
+  if (!c) return LBM_EINVAL;
+  c->err.clear();
+  switch (knob) {
+    case LBM_TUNE_PREFETCH:
+      if (value < 0) return fail(c, LBM_EINVAL, "prefetch distance must be >= 0");
+      c->prefetch = value;
+      return LBM_OK;
+    case LBM_TUNE_BULK_SITES:
+      if (value != 1 && value != 2) return fail(c, LBM_EINVAL, "bulk sites per lane must be 1 or 2");
+      c->bulk_sites = (int32_t)value;
+      return LBM_OK;
+  }
+  return fail(c, LBM_EINVAL, "unknown tuning knob for a lattice");
 }
 
 int lbm_sync(lbm_ctx* c) {
@@ -719,11 +750,46 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocPartials + kNo
 
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+// Cached address per device, valid for the CUDA context it was looked up in:
+// a device reset (or any destruction of the primary context) loads the module
+// again, possibly at another address, and gives the new context a new id.
+struct NoAllocSlot {
+  unsigned long long ctx_id;
+  double* ptr;
+};
+NoAllocSlot g_noalloc_slot[kNoAllocMaxDevices] = {};
+
+// Unique id of the calling thread's current CUDA context (driver entry points
+// resolved through the runtime, so the library does not link libcuda), or 0
+// when it cannot be had - then the address is looked up on every call.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {  // under g_noalloc_mu
+    resolved = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  }
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// once per device and context (with that device current) and cached.
 int noalloc_scratch(lbm_ctx* c, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -731,13 +797,16 @@ int noalloc_scratch(lbm_ctx* c, double** out) {
   if (dev < 0 || dev >= kNoAllocMaxDevices)
     return fail(c, LBM_EINVAL, "lbm_reduce_noalloc: device ordinal beyond 63");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  NoAllocSlot& slot = g_noalloc_slot[dev];
+  if (!slot.ptr || ctx == 0 || slot.ctx_id != ctx) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_reduce_noalloc: cudaGetSymbolAddress");
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
+    slot.ptr = static_cast<double*>(p);
+    slot.ctx_id = ctx;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = slot.ptr;
   return LBM_OK;
 }
 

@@ -351,6 +351,215 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
   });
 }
 
+// --------------------------------------------------- two sites per lane
+// The bulk update of two z-adjacent sites x, x + 1 (x even) by one lane, for
+// the FP32 and 16-bit storages: both sites share the tile's neighbour offsets,
+// so one address serves both; a direction whose offset is even reads (and
+// writes) the two values as one aligned 32-bit (16-bit storage) or 64-bit
+// (FP32) word, an odd offset as two scalars; the collision runs on packed
+// pairs with the two-wide FP32 instructions (add/sub/mul/fma .f32x2), so each
+// floating-point instruction serves both sites.  The arithmetic is that of
+// bulk_update, with the reciprocal of rho from the hardware approximation.
+struct F2 {
+  unsigned long long v;  // low word: site x, high word: site x + 1
+};
+__device__ __forceinline__ F2 mk2(float lo, float hi) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ F2 bc2(float a) { return mk2(a, a); }
+__device__ __forceinline__ void split2(F2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ F2 add2(F2 a, F2 b) {
+  F2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) {
+  F2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+  F2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {  // a b + c
+  F2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ float rcp_approx(float v) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
+// Pair codecs: ld_al / st_al move the aligned word holding sites (x, x + 1);
+// ld_un / st_un move the two elements one by one.  Conversions round as the
+// single-site codecs do (to nearest even).
+template <class S>
+struct Codec2;
+template <>
+struct Codec2<float> {
+  static __device__ __forceinline__ F2 ld_al(const float* p) {
+    F2 r;
+    r.v = *reinterpret_cast<const unsigned long long*>(p);
+    return r;
+  }
+  static __device__ __forceinline__ F2 ld_un(const float* p) { return mk2(p[0], p[1]); }
+  static __device__ __forceinline__ void st_al(float* p, F2 g) {
+    *reinterpret_cast<unsigned long long*>(p) = g.v;
+  }
+  static __device__ __forceinline__ void st_un(float* p, F2 g) {
+    float l, h;
+    split2(g, l, h);
+    p[0] = l;
+    p[1] = h;
+  }
+};
+template <>
+struct Codec2<__half> {
+  static __device__ __forceinline__ F2 ld_al(const __half* p) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(p));
+    return mk2(f.x, f.y);
+  }
+  static __device__ __forceinline__ F2 ld_un(const __half* p) {
+    return mk2(__half2float(p[0]), __half2float(p[1]));
+  }
+  static __device__ __forceinline__ void st_al(__half* p, F2 g) {
+    float l, h;
+    split2(g, l, h);
+    uint32_t w;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(h), "f"(l));
+    *reinterpret_cast<uint32_t*>(p) = w;
+  }
+  static __device__ __forceinline__ void st_un(__half* p, F2 g) {
+    float l, h;
+    split2(g, l, h);
+    p[0] = __float2half_rn(l);
+    p[1] = __float2half_rn(h);
+  }
+};
+template <>
+struct Codec2<__nv_bfloat16> {
+  static __device__ __forceinline__ F2 ld_al(const __nv_bfloat16* p) {
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
+    return mk2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+  }
+  static __device__ __forceinline__ F2 ld_un(const __nv_bfloat16* p) {
+    const uint32_t a = __bfloat16_as_ushort(p[0]), b = __bfloat16_as_ushort(p[1]);
+    return mk2(__uint_as_float(a << 16), __uint_as_float(b << 16));
+  }
+  static __device__ __forceinline__ void st_al(__nv_bfloat16* p, F2 g) {
+    float l, h;
+    split2(g, l, h);
+    uint32_t w;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(h), "f"(l));
+    *reinterpret_cast<uint32_t*>(p) = w;
+  }
+  static __device__ __forceinline__ void st_un(__nv_bfloat16* p, F2 g) {
+    float l, h;
+    split2(g, l, h);
+    p[0] = __float2bfloat16_rn(l);
+    p[1] = __float2bfloat16_rn(h);
+  }
+};
+
+template <class S>
+__device__ __forceinline__ void chk_count2(int* chk, const S* P0, const S* p, int64_t lim,
+                                           int* err) {
+  chk_count(chk, P0, p, lim, err);
+  chk_count(chk, P0, p + 1, lim, err);
+}
+
+// Branch-free update of the sites x, x + 1 (x even) whose 18 links are fluid,
+// both with the neighbour offsets dsc.
+template <class S, bool ODD>
+__device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const int32_t* dsc,
+                                             double omega_t, int* err, int* chk) {
+  using Cd = Codec2<S>;
+  F2 g[kQ];
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int o = dir_opp(j);
+    if constexpr (!ODD || j == 0) {
+      g[j] = Cd::ld_al(P + j * np + x);
+    } else {
+      const int32_t dd = dsc[o - 1];
+      const S* q = P + o * np + x + dd;
+      g[j] = (dd & 1) ? Cd::ld_un(q) : Cd::ld_al(q);
+    }
+  });
+  // Eqs. (Density), (Momentum), grouped as in moments()
+  const F2 a1 = sub2(g[1], g[2]), a3 = sub2(g[3], g[4]), a5 = sub2(g[5], g[6]);
+  const F2 a7 = sub2(g[7], g[8]), a9 = sub2(g[9], g[10]), a11 = sub2(g[11], g[12]);
+  const F2 a13 = sub2(g[13], g[14]), a15 = sub2(g[15], g[16]), a17 = sub2(g[17], g[18]);
+  const F2 drho =
+      add2(add2(add2(add2(g[0], add2(g[1], g[2])), add2(add2(g[3], g[4]), add2(g[5], g[6]))),
+                add2(add2(add2(g[7], g[8]), add2(g[9], g[10])),
+                     add2(add2(g[11], g[12]), add2(g[13], g[14])))),
+           add2(add2(g[15], g[16]), add2(g[17], g[18])));
+  const F2 jx = add2(add2(add2(a1, a7), add2(a9, a11)), a13);
+  const F2 jy = add2(sub2(add2(a3, a7), sub2(a9, a15)), a17);
+  const F2 jz = sub2(sub2(add2(a5, a11), sub2(a13, a15)), a17);
+  const F2 rho = add2(bc2(1.0f), drho);
+  float r0, r1;
+  split2(rho, r0, r1);
+  if (unstable(r0) || unstable(r1)) atomicOr(err, kErrUnstable);
+  const F2 inv = mk2(rcp_approx(r0), rcp_approx(r1));
+  const F2 ux = mul2(jx, inv), uy = mul2(jy, inv), uz = mul2(jz, inv);
+  const F2 usq = mul2(bc2(1.5f), fma2(uz, uz, fma2(uy, uy, mul2(ux, ux))));
+  const F2 omega = bc2(float(omega_t));
+  // rest population: g*_0 = g_0 + omega (w_0 (drho - rho usq) - g_0)
+  const F2 e0 = mul2(bc2(1.0f / 3.0f), sub2(drho, mul2(rho, usq)));
+  Cd::st_al(P + x, fma2(omega, sub2(e0, g[0]), g[0]));
+  chk_count2(chk, P, P + x, kQ * np, err);
+  // opposite pairs (a, b): g^eq = even +- odd (see bulk_update)
+  const F2 wd1 = mul2(drho, bc2(1.0f / 18.0f)), wd2 = mul2(drho, bc2(1.0f / 36.0f));
+  const F2 wr1 = mul2(rho, bc2(1.0f / 18.0f)), wr2 = mul2(rho, bc2(1.0f / 36.0f));
+  const F2 w3r1 = mul2(rho, bc2(3.0f / 18.0f)), w3r2 = mul2(rho, bc2(3.0f / 36.0f));
+  const F2 nusq = sub2(bc2(0.0f), usq);
+  unroll<9>([&](auto Pi) {
+    constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
+    constexpr int pp = (a + 1) / 2;
+    F2 cu;
+    if constexpr (pp == 1) cu = ux;
+    else if constexpr (pp == 2) cu = uy;
+    else if constexpr (pp == 3) cu = uz;
+    else if constexpr (pp == 4) cu = add2(ux, uy);
+    else if constexpr (pp == 5) cu = sub2(ux, uy);
+    else if constexpr (pp == 6) cu = add2(ux, uz);
+    else if constexpr (pp == 7) cu = sub2(ux, uz);
+    else if constexpr (pp == 8) cu = add2(uy, uz);
+    else cu = sub2(uy, uz);
+    const F2 q = fma2(mul2(bc2(4.5f), cu), cu, nusq);
+    const F2 even = (a <= 6) ? fma2(wr1, q, wd1) : fma2(wr2, q, wd2);
+    const F2 odd = mul2((a <= 6) ? w3r1 : w3r2, cu);
+    const F2 sa = fma2(omega, sub2(add2(even, odd), g[a]), g[a]);
+    const F2 sb = fma2(omega, sub2(sub2(even, odd), g[b]), g[b]);
+    if constexpr (ODD) {
+      const int32_t da = lds_volatile(dsc + a - 1), db = lds_volatile(dsc + b - 1);
+      S* pa = P + a * np + x + da;
+      S* pb = P + b * np + x + db;
+      if (da & 1) Cd::st_un(pa, sa);
+      else Cd::st_al(pa, sa);
+      if (db & 1) Cd::st_un(pb, sb);
+      else Cd::st_al(pb, sb);
+      chk_count2(chk, P, pa, kQ * np, err);
+      chk_count2(chk, P, pb, kQ * np, err);
+    } else {
+      Cd::st_al(P + b * np + x, sa);
+      Cd::st_al(P + a * np + x, sb);
+      chk_count2(chk, P, P + b * np + x, kQ * np, err);
+      chk_count2(chk, P, P + a * np + x, kQ * np, err);
+    }
+  });
+}
+
 // Update of a site of a boundary tile.  `code[i]` holds the tile's uniform
 // offsets / non-fluid codes; irregular tiles use the staged per-site table.
 // Pre-collision populations of a boundary site: direction j comes from its own
@@ -612,6 +821,63 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
   bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p.omega, d.err, d.chk);
 }
 
+// Two bulk tiles at launch positions k0, k0 + 1 (whole warp, two sites per
+// lane): lanes 0..15 take tile k0, lanes 16..31 tile k0 + 1 (if any), lane l
+// the sites 2 (l mod 16), 2 (l mod 16) + 1 of its tile; dsc2: the warp's two
+// 20-word descriptor areas.  A site without a partner (the last site of a
+// lattice with an odd site count) takes the single-site update.
+template <class S, bool ODD>
+__device__ __forceinline__ void bulk_tiles2(const DevLattice& d, const StepParams& p, int64_t k0,
+                                            int32_t (*dsc2)[20], int lane) {
+  const bool two = k0 + 1 < d.n_tiles;
+  if (lane < 20) {
+    dsc2[0][lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k0) + lane);
+    if (two) dsc2[1][lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k0 + 1) + lane);
+  }
+  if (p.prefetch > 0 && lane < kQ) {
+    for (int h = 0; h < 2; ++h) {
+      const int64_t kp = k0 + h + p.prefetch;
+      if (kp < d.n_tiles) {
+        const int64_t tp = __ldg(&d.launch[kp].tile);
+        bulk_prefetch_l2(static_cast<const S*>(d.pop) + lane * d.npad + tp * kTile,
+                         kTile * sizeof(S));
+      }
+    }
+  }
+  __syncwarp();
+  const int half = lane >> 4;
+  if (half && !two) return;
+  const int32_t* dsc = dsc2[half];
+  const int64_t x = (int64_t)dsc[19] * kTile + 2 * (lane & 15);
+  if (x >= d.n) return;
+  if constexpr (kChecked && ODD) {
+    bool ok = true;
+    for (int o = 0; o < 18; ++o) ok = chk_site(x + dsc[o], d.n, d.err) && ok;
+    if (x + 1 < d.n)
+      for (int o = 0; o < 18; ++o) ok = chk_site(x + 1 + dsc[o], d.n, d.err) && ok;
+    if (!ok) return;
+  }
+  S* P = static_cast<S*>(d.pop);
+  if (x + 1 < d.n) bulk_update2<S, ODD>(P, d.npad, x, dsc, p.omega, d.err, d.chk);
+  else bulk_update<S, ODD>(P, d.npad, x, dsc, p.omega, d.err, d.chk);
+}
+
+#ifndef LBM_BULK2_MINB
+#define LBM_BULK2_MINB 6
+#endif
+// Bulk tiles, two sites per lane (FP32 and 16-bit storage): warp w of block b
+// takes the bulk tiles at launch positions n_boundary + 2 (b W + w) and the
+// one after it.
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBulkWarps * 32, LBM_BULK2_MINB)
+    k_bulk2(const DevLattice d, const StepParams p) {
+  __shared__ __align__(16) int32_t desc_s[kBulkWarps][2][20];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k0 = d.n_boundary + 2 * ((int64_t)blockIdx.x * kBulkWarps + w);
+  if (k0 >= d.n_tiles) return;  // warp-uniform
+  bulk_tiles2<S, ODD>(d, p, k0, desc_s[w], lane);
+}
+
 template <class S, bool ODD>
 __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 16 / kBulkWarps : LBM_BULK_MINB)
     k_bulk(const DevLattice d, const StepParams p) {
@@ -674,9 +940,15 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
     boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g, d.n, d.err);
   if (stage) {
     const uint32_t ph = bar_phase ? *bar_phase : 0u;
-    if (!mbar_wait_bounded(bar, ph)) {
+    // one decision for the whole warp (lanes could see the limit and the
+    // completion in different polls)
+    if (!__all_sync(0xFFFFFFFFu, mbar_wait_bounded(bar, ph))) {
+      // The copies did not complete: the step's results are invalid from here
+      // on (kErrTimeout), and the caller does no further tile work with this
+      // staging area.  One more bounded wait gives copies still in flight a
+      // chance to land; nothing waits on them after that.
       if (lane == 0) atomicOr(d.err, kErrTimeout);
-      mbar_wait_bounded(bar, ph);  // a second bounded chance for copies still in flight
+      mbar_wait_bounded(bar, ph);
       return false;
     }
     if (bar_phase) *bar_phase = ph ^ 1u;
@@ -835,6 +1107,7 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
     q.write_state = s == n_steps - 1 ? 1 : 0;
     const bool odd = q.step & 1;
     const int slot = (int)(q.step & 1);
+    bool stop = false;  // this warp's staging timed out: no further tile work
     for (;;) {
       unsigned long long t0 = 0;
       if (lane == 0) {
@@ -858,7 +1131,11 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
                                                           &bars[w], gsm[w], lane, &phase)
                               : persist_boundary<S, false>(md.d, pm, k, desc_s[w], stage[w],
                                                            &bars[w], gsm[w], lane, &phase);
-          if (!ok && lane == 0) atomicExch(&gs->abort, 1u);
+          if (!ok) {
+            if (lane == 0) atomicExch(&gs->abort, 1u);
+            stop = true;
+            break;
+          }
         } else {
           const int64_t tb = t - e.n_boundary_tiles;
           const int m = find_member(e.bulk_prefix, e.n_members, tb);
@@ -871,6 +1148,7 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
         }
         __syncwarp();
       }
+      if (stop) break;
     }
     if (!grid_sync(gs, expected, gen, slot ^ 1, err0)) return;
   }
@@ -1152,8 +1430,18 @@ int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void
     else k_boundary<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
   }
   if (nbulk) {
-    if (odd) k_bulk<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
-    else k_bulk<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+    bool pairs = false;
+    if constexpr (sizeof(S) < 8) pairs = p.bulk_sites == 2;
+    if (pairs) {
+      const unsigned nb2 = (unsigned)((nbulk_tiles + 2 * kBulkWarps - 1) / (2 * kBulkWarps));
+      if constexpr (sizeof(S) < 8) {
+        if (odd) k_bulk2<S, true><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
+        else k_bulk2<S, false><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
+      }
+    } else {
+      if (odd) k_bulk<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+      else k_bulk<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
+    }
   }
   if (ev) cudaEventRecord((cudaEvent_t)ev[1], m);
   if (nbnd) {

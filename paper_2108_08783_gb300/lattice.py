@@ -226,6 +226,14 @@ class Lattice:
     def profile(self, enable=True):
         self._check(self._lib.lbm_profile(self.h, 1 if enable else 0))
 
+    def tune(self, prefetch=None, bulk_sites=None):
+        """Launch knobs (``lbm_tune``): L2 prefetch distance of the bulk kernel in
+        tiles, and sites per lane of the bulk kernel (1 or 2)."""
+        if prefetch is not None:
+            self._check(self._lib.lbm_tune(self.h, A.LBM_TUNE_PREFETCH, int(prefetch)))
+        if bulk_sites is not None:
+            self._check(self._lib.lbm_tune(self.h, A.LBM_TUNE_BULK_SITES, int(bulk_sites)))
+
     def profile_read(self):
         """Since profile(True): ((step ms, bulk-kernel ms), (bulk launches, boundary launches))."""
         ms = np.zeros(2)

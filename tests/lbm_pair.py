@@ -22,14 +22,17 @@ def wall_params_from_grid(grid, coords, wall_sites):
 
 
 def make_pair(geo, storage="f64", tau=0.8, wall_model=1, F=0.85, kappa=0.0, rho0=1.0,
-              fields=None, F_grid=None, kappa_grid=None):
+              fields=None, F_grid=None, kappa_grid=None, bulk_sites=None):
     """(Lattice, Oracle) on the same geometry, parameters and initial state.
 
     ``fields`` = (rho_grid, u_grid) per-voxel initial fields or None (rest);
-    ``F_grid`` / ``kappa_grid`` per-voxel wall parameters (else scalars).
+    ``F_grid`` / ``kappa_grid`` per-voxel wall parameters (else scalars);
+    ``bulk_sites`` sites per lane of the bulk kernel (None: the library default).
     """
     from paper_2108_08783_gb300 import Lattice
     lat = Lattice(geo.labels, geo.iolets, storage=storage, tau=tau)
+    if bulk_sites is not None:
+        lat.tune(bulk_sites=bulk_sites)
     orc = Oracle(geo.labels, geo.iolets, tau=tau, wall_model=wall_model, F=F, kappa=kappa,
                  rho0=rho0)
     lex = lat.export()

@@ -12,6 +12,7 @@ import pytest
 
 import lbm_inputs as I
 from lbm_pair import make_pair, rel_l2
+from storage_bounds import BOUND_FACTOR, UNIT_ROUNDOFF, rounding_walk_estimate
 
 pytestmark = pytest.mark.gpu
 
@@ -21,6 +22,19 @@ TOL = {"f64": 1e-10, "f32": 1e-5}
 def _short_tube(length=64, **kw):
     # radius 8, length 64, peak inlet 0.05 (mean 0.025), rho_out = 1
     return I.tube(8, length, u_mean=0.025, **kw)
+
+
+# The R = 8, L = 64 tube has no bulk tile (every 32-site tile of a 64-long
+# z-column touches the inlet or the outlet plane), so the bulk kernel never
+# runs on it.  The 255-long tube of the same radius and flow has 1026 bulk
+# tiles of 1658 (62 % of its 53,040 sites), coherent wall and iolet tiles,
+# irregular tiles where tiles straddle two z-columns, and a ragged last tile.
+BULK_TUBE_LEN = 255
+
+
+def _assert_bulk_path(lat, min_frac=0.5):
+    info = lat.info()
+    assert info[4] > 0 and info[11] >= min_frac * info[0], ("too few bulk tiles", list(info))
 
 
 def _compare(lat, orc, tol, what=""):
@@ -56,16 +70,25 @@ def test_lattice_build_bit_exact(geo):
 
 # ------------------------------------------------------------------ FP64 / FP32 parity
 
+@pytest.mark.parametrize("length,bulk_sites", [(64, 1), (BULK_TUBE_LEN, 1), (BULK_TUBE_LEN, 2)])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("wall_model", [1, 0])
-def test_short_tube_1000_steps(storage, wall_model):
-    """R = 8, L = 64 tube (tau 0.8, peak inlet 0.05, rho_out 1, kappa 12, F 0.85) from rest."""
-    geo = _short_tube()
-    lat, orc = make_pair(geo, storage, tau=0.8, wall_model=wall_model, F=0.85, kappa=12.0)
+def test_short_tube_1000_steps(storage, wall_model, length, bulk_sites):
+    """R = 8 tube (tau 0.8, peak inlet 0.05, rho_out 1, kappa 12, F 0.85) from rest,
+    1000 steps: the 64-long tube of the short-tube workload, and the 255-long one
+    whose bulk tiles run the bulk kernel (one or two sites per lane; FP64 has
+    only the first) at the same tolerance."""
+    if storage == "f64" and bulk_sites == 2:
+        pytest.skip("the two-sites-per-lane bulk kernel serves FP32 and 16-bit storage")
+    geo = _short_tube(length)
+    lat, orc = make_pair(geo, storage, tau=0.8, wall_model=wall_model, F=0.85, kappa=12.0,
+                         bulk_sites=bulk_sites)
+    if length == BULK_TUBE_LEN:
+        _assert_bulk_path(lat)
     lat.step(1000)
     lat.sync()
     orc.run(1000)
-    _compare(lat, orc, TOL[storage], "short tube")
+    _compare(lat, orc, TOL[storage], "tube L=%d" % length)
     if wall_model == 1:
         dEl, Uwl = lat.wall_state()
         dEo, Uwo = orc.wall_state()
@@ -76,17 +99,19 @@ def test_short_tube_1000_steps(storage, wall_model):
     np.testing.assert_allclose(rl, ro, rtol=10 * TOL[storage], atol=1e-9)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_ragged_tail_random_start_odd_steps(storage):
-    """L = 63 (ragged last tile), smooth random initial fields, odd step count,
-    per-wall-site F and kappa from a seeded per-voxel field."""
-    geo = _short_tube(63)
+@pytest.mark.parametrize("storage,length,bulk_sites", [("f64", 63, 1), ("f32", 63, 1),
+                                                       ("f32", BULK_TUBE_LEN, 2)])
+def test_ragged_tail_random_start_odd_steps(storage, length, bulk_sites):
+    """L = 63 (ragged last tile) or 255 (bulk tiles, paired bulk kernel), smooth
+    random initial fields, odd step count, per-wall-site F and kappa from a
+    seeded per-voxel field."""
+    geo = _short_tube(length)
     rng = np.random.default_rng(11)
     F_grid = rng.uniform(0.0, 1.0, geo.shape)
     K_grid = rng.uniform(0.0, 40.0, geo.shape)
     lat, orc = make_pair(geo, storage, tau=0.7, wall_model=1, rho0=0.9995,
                          fields=I.random_fields(5, geo.shape, drho=2e-3, umax=0.03),
-                         F_grid=F_grid, kappa_grid=K_grid)
+                         F_grid=F_grid, kappa_grid=K_grid, bulk_sites=bulk_sites)
     lat.step(333)
     lat.sync()
     orc.run(333)
@@ -174,14 +199,17 @@ def test_unstable_run_is_flagged():
 
 # ------------------------------------------------------------------ full-size sampled parity
 
-@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f64", 1e-10)])
-def test_long_tube_full_size_short_run(storage, tol):
+@pytest.mark.parametrize("storage,tol,bulk_sites", [("f32", 1e-5, 1), ("f32", 1e-5, 2),
+                                                    ("f64", 1e-10, 1)])
+def test_long_tube_full_size_short_run(storage, tol, bulk_sites):
     """The long tube at full size (R = 40, L = 1024, ~5.1 M sites, tau 0.6, pulsatile
     inlet 0.03 + 0.02 sin(2 pi n / 4000), Eh/r0 = 0.5 -> kappa 60), 20 steps
-    from a seeded smooth random state, all sites compared with the oracle."""
+    from a seeded smooth random state, all sites compared with the oracle, in the
+    launch configurations the benchmark times."""
     geo = I.tube(40, 1024, u_mean=0.03, u_amp=0.02, period=4000.0)
     lat, orc = make_pair(geo, storage, tau=0.6, wall_model=1, F=0.85, kappa=60.0,
-                         fields=I.random_fields(7, geo.shape, drho=1e-3, umax=0.03, smooth=1))
+                         fields=I.random_fields(7, geo.shape, drho=1e-3, umax=0.03, smooth=1),
+                         bulk_sites=bulk_sites)
     lat.step(20)
     orc.run(20)
     _compare(lat, orc, tol, "long tube")
@@ -189,25 +217,41 @@ def test_long_tube_full_size_short_run(storage, tol):
 
 # ------------------------------------------------------------------ reduced precision
 
-@pytest.mark.parametrize("storage,bound,wss_bound", [("f32", 1e-5, 2e-5), ("f16s", 2e-3, 5e-3),
-                                                     ("bf16s", 6e-2, 6e-2)])
-def test_shifted_storage_error_bounds(storage, bound, wss_bound):
-    """Stated bounds for each storage after 1000 steps on the short tube against the
-    FP64 oracle: rel-L2 of (rho - 1), of u and of the wall shear stress at the
-    wall sites.  BF16 keeps 8 significant bits, so its bounds are looser
-    (measured 3.2e-2 on rho - 1)."""
-    geo = _short_tube()
-    lat, orc = make_pair(geo, storage, tau=0.8, wall_model=1, F=0.85, kappa=12.0)
+@pytest.mark.parametrize("bulk_sites", [1, 2])
+@pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
+def test_shifted_storage_error_bounds(storage, bulk_sites):
+    """Each storage against the FP64 oracle after 1000 steps from rest on the
+    255-long R = 8 tube (bulk tiles carry 62 % of the sites): rel-L2 of
+    (rho - 1), of u and of the wall shear stress at the wall sites.
+
+    FP32: 1e-5 (2e-5 for the wall shear stress).  FP16S / BF16S: four times
+    the random-walk estimate of per-store rounding (storage_bounds, with the
+    wall shear stress held to the bound of u); measured on GB300 the
+    errors sit between 0.4 and 2.3 estimates, above 1 for bfloat16, whose
+    8-bit significand also loses per-step increments below half an ulp
+    during the start-up transient (errors that are correlated, not a
+    random walk)."""
+    geo = _short_tube(BULK_TUBE_LEN)
+    lat, orc = make_pair(geo, storage, tau=0.8, wall_model=1, F=0.85, kappa=12.0,
+                         bulk_sites=bulk_sites)
+    _assert_bulk_path(lat)
     lat.step(1000)
     orc.run(1000)
+    if storage == "f32":
+        b_rho = b_u = 1e-5
+        b_wss = 2e-5
+    else:
+        e_rho, e_u = rounding_walk_estimate(orc, 1000)
+        b_rho = BOUND_FACTOR * UNIT_ROUNDOFF[storage] * e_rho
+        b_u = b_wss = BOUND_FACTOR * UNIT_ROUNDOFF[storage] * e_u
     rl, ul = lat.moments()
     ro, uo = orc.moments()
-    assert rel_l2(rl - 1, ro - 1) < bound
-    assert rel_l2(ul, uo) < bound
+    er, eu = rel_l2(rl - 1, ro - 1), rel_l2(ul, uo)
     ex = lat.export()
     s = ex["wall_sites"]
     nrm = I.wall_normals(geo, ex["coords"][s])
-    assert rel_l2(lat.wss(s, nrm), orc.wss(s, nrm)) < wss_bound
+    ew = rel_l2(lat.wss(s, nrm), orc.wss(s, nrm))
+    assert er < b_rho and eu < b_u and ew < b_wss, (storage, (er, b_rho), (eu, b_u), (ew, b_wss))
 
 
 # ------------------------------------------------------------------ wall shear stress
