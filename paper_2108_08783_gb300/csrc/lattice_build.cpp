@@ -20,6 +20,8 @@
 #include <complex>
 #include <cstdio>
 #include <limits>
+#include <thread>
+#include <vector>
 
 #include "d3q19.h"
 #include "lbm_internal.h"
@@ -60,6 +62,28 @@ cplx womersley(double alpha, double xi) {
   return (1.0 - j0r / j0L) / (1.0 - 2.0 * j1L / (lam * j0L));
 }
 
+// Host threads of the builder (the machine's, at most 64).
+int host_threads() {
+  const unsigned h = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(h, 64u));
+}
+
+// f(begin, end, thread) over a static split of [0, n) into contiguous ranges,
+// in increasing order of thread index; small ranges run on the caller.
+template <class F>
+void parallel_for(int64_t n, F&& f) {
+  const int64_t grain = 1 << 14;
+  const int nt = (int)std::min<int64_t>(host_threads(), (n + grain - 1) / grain);
+  if (nt <= 1) {
+    if (n > 0) f(int64_t(0), n, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int t = 0; t < nt; ++t) th.emplace_back([&f, n, nt, t] { f(n * t / nt, n * (t + 1) / nt, t); });
+  for (auto& x : th) x.join();
+}
+
 bool finite3(const double* v) {
   return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
 }
@@ -97,148 +121,243 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
       return LBM_EINVAL;
     }
   }
-  const int64_t nvox = (int64_t)nx * ny * nz;
   const int max_label = 1 + n_iolets;
-  std::vector<int32_t> site_of(nvox, -1);
-  int64_t n = 0;
-  for (int64_t v = 0; v < nvox; ++v) {
-    if (labels[v] > max_label) {
-      std::snprintf(msg, sizeof msg, "voxel %lld has label %d > 1 + n_iolets", (long long)v,
-                    (int)labels[v]);
-      err = msg;
-      return LBM_EINVAL;
-    }
-    if (labels[v] == 1) {
-      if (n >= std::numeric_limits<int32_t>::max() - 4 * kTile) {
-        err = "too many fluid sites for 32-bit site ids";
-        return LBM_EINVAL;
-      }
-      site_of[v] = (int32_t)n++;
-    }
-  }
-  L.nx = nx; L.ny = ny; L.nz = nz; L.n = n;
-  L.coords.assign((size_t)3 * n, 0);
-  L.nbr.assign((size_t)18 * n, 0);
-  // ---- links: site id, -1 wall, -2-k iolet k
-  for (int32_t x = 0; x < nx; ++x)
-    for (int32_t y = 0; y < ny; ++y)
+  // ---- fluid runs along z, column by column (column c = x ny + y): the site
+  // of a fluid voxel is found from its column's runs, so no per-voxel index
+  // of the (possibly mostly solid) bounding box is held.
+  const int64_t C = (int64_t)nx * ny;
+  const int nthr = host_threads();
+  std::vector<int32_t> col_n(C), col_runs(C);
+  std::vector<int64_t> bad(nthr, std::numeric_limits<int64_t>::max());
+  parallel_for(C, [&](int64_t c0, int64_t c1, int t) {
+    for (int64_t c = c0; c < c1; ++c) {
+      const uint8_t* lab = labels + c * nz;
+      int32_t cnt = 0, runs = 0;
+      bool in = false;
       for (int32_t z = 0; z < nz; ++z) {
-        const int64_t v = ((int64_t)x * ny + y) * nz + z;
-        const int32_t s = site_of[v];
-        if (s < 0) continue;
-        int32_t* c = &L.coords[(size_t)3 * s];
-        c[0] = x; c[1] = y; c[2] = z;
-        for (int i = 1; i < kQ; ++i) {
-          const int32_t X = x + dir_x(i), Y = y + dir_y(i), Z = z + dir_z(i);
-          int32_t code = -1;
-          if (X >= 0 && Y >= 0 && Z >= 0 && X < nx && Y < ny && Z < nz) {
-            const int64_t w = ((int64_t)X * ny + Y) * nz + Z;
-            const int lab = labels[w];
-            code = lab == 0 ? -1 : lab == 1 ? site_of[w] : -2 - (lab - 2);
-          }
-          L.nbr[(size_t)18 * s + (i - 1)] = code;
-        }
+        const int v = lab[z];
+        if (v > max_label && bad[t] == std::numeric_limits<int64_t>::max()) bad[t] = c * nz + z;
+        const bool f = v == 1;
+        cnt += f;
+        runs += (f && !in);
+        in = f;
       }
-  site_of.clear();
-  site_of.shrink_to_fit();
+      col_n[c] = cnt;
+      col_runs[c] = runs;
+    }
+  });
+  const int64_t first_bad = *std::min_element(bad.begin(), bad.end());
+  if (first_bad != std::numeric_limits<int64_t>::max()) {
+    std::snprintf(msg, sizeof msg, "voxel %lld has label %d > 1 + n_iolets", (long long)first_bad,
+                  (int)labels[first_bad]);
+    err = msg;
+    return LBM_EINVAL;
+  }
+  std::vector<int64_t> col_base(C + 1), run_base(C + 1);
+  col_base[0] = run_base[0] = 0;
+  for (int64_t c = 0; c < C; ++c) {
+    col_base[c + 1] = col_base[c] + col_n[c];
+    run_base[c + 1] = run_base[c] + col_runs[c];
+  }
+  const int64_t n = col_base[C];
+  if (n >= std::numeric_limits<int32_t>::max() - 4 * kTile) {
+    err = "too many fluid sites for 32-bit site ids";
+    return LBM_EINVAL;
+  }
+  col_n.clear();
+  col_n.shrink_to_fit();
+  col_runs.clear();
+  col_runs.shrink_to_fit();
+  struct Run {
+    int32_t z0, z1, base;  // fluid voxels z0 <= z < z1 hold sites base + (z - z0)
+  };
+  std::vector<Run> runs(run_base[C]);
+  L.nx = nx; L.ny = ny; L.nz = nz; L.n = n;
+  L.coords.clear();
+  L.coords.resize((size_t)3 * n);  // every element written below
+  L.nbr.clear();
+  L.nbr.resize((size_t)18 * n);
+  parallel_for(C, [&](int64_t c0, int64_t c1, int) {
+    for (int64_t c = c0; c < c1; ++c) {
+      if (run_base[c + 1] == run_base[c]) continue;
+      const uint8_t* lab = labels + c * nz;
+      const int32_t x = (int32_t)(c / ny), y = (int32_t)(c % ny);
+      int64_t s = col_base[c], r = run_base[c];
+      bool in = false;
+      for (int32_t z = 0; z < nz; ++z) {
+        const bool f = lab[z] == 1;
+        if (f && !in) runs[r] = Run{z, z, (int32_t)s};
+        if (f) {
+          runs[r].z1 = z + 1;
+          int32_t* co = &L.coords[(size_t)3 * s];
+          co[0] = x; co[1] = y; co[2] = z;
+          ++s;
+        } else if (in) {
+          ++r;
+        }
+        in = f;
+      }
+    }
+  });
+  auto site_at = [&](int32_t X, int32_t Y, int32_t Z) -> int32_t {
+    const int64_t c = (int64_t)X * ny + Y;
+    for (int64_t r = run_base[c]; r < run_base[c + 1]; ++r)
+      if (Z >= runs[r].z0 && Z < runs[r].z1) return runs[r].base + (Z - runs[r].z0);
+    return -1;  // not reached for a voxel labelled fluid
+  };
+  // ---- links: site id, -1 wall, -2-k iolet k
+  parallel_for(n, [&](int64_t s0, int64_t s1, int) {
+    for (int64_t s = s0; s < s1; ++s) {
+      const int32_t* co = &L.coords[(size_t)3 * s];
+      for (int i = 1; i < kQ; ++i) {
+        const int32_t X = co[0] + dir_x(i), Y = co[1] + dir_y(i), Z = co[2] + dir_z(i);
+        int32_t code = -1;
+        if (X >= 0 && Y >= 0 && Z >= 0 && X < nx && Y < ny && Z < nz) {
+          const int lab = labels[((int64_t)X * ny + Y) * nz + Z];
+          code = lab == 0 ? -1 : lab == 1 ? site_at(X, Y, Z) : -2 - (lab - 2);
+        }
+        L.nbr[(size_t)18 * s + (i - 1)] = code;
+      }
+    }
+  });
+  runs.clear();
+  runs.shrink_to_fit();
   // ---- per-site summary: link masks, iolet links, the site's iolet id
   std::vector<uint32_t> site_mask(n, 0), site_io(n, 0);
   std::vector<int32_t> site_inlet(n, -1);
+  std::vector<uint8_t> site_walls(n, 0);
+  struct Clash {
+    int64_t s;
+    int a, b;
+  };
+  std::vector<Clash> clash(nthr, Clash{std::numeric_limits<int64_t>::max(), 0, 0});
+  parallel_for(n, [&](int64_t s0, int64_t s1, int t) {
+    for (int64_t s = s0; s < s1; ++s) {
+      uint32_t m = 0, io = 0;
+      int walls = 0, first_io = -1, inlet = -1;
+      const int32_t* nb = &L.nbr[(size_t)18 * s];
+      for (int i = 1; i < kQ; ++i) {
+        const int32_t c = nb[i - 1];
+        if (c >= 0) continue;
+        m |= 1u << i;
+        if (c == -1) {
+          ++walls;
+          m |= kHasWall;
+          continue;
+        }
+        const int k = -2 - c;
+        io |= 1u << i;
+        if (first_io < 0) first_io = k;
+        else if (first_io != k) m |= kMultiIolet;
+        if (iolets[k].kind == LBM_IOLET_VELOCITY) {
+          if (inlet >= 0 && inlet != k && clash[t].s == std::numeric_limits<int64_t>::max())
+            clash[t] = Clash{s, inlet, k};
+          inlet = k;
+          m |= kHasInlet;
+        }
+      }
+      const int id = inlet >= 0 ? inlet : first_io;
+      if (id >= 0) io |= (uint32_t)id << kIoletShift;
+      site_mask[s] = m;
+      site_io[s] = io;
+      site_inlet[s] = inlet;
+      site_walls[s] = (uint8_t)walls;
+    }
+  });
+  const Clash cl = *std::min_element(clash.begin(), clash.end(),
+                                     [](const Clash& a, const Clash& b) { return a.s < b.s; });
+  if (cl.s != std::numeric_limits<int64_t>::max()) {
+    std::snprintf(msg, sizeof msg, "site %lld touches two velocity inlets (%d, %d)",
+                  (long long)cl.s, cl.a, cl.b);
+    err = msg;
+    return LBM_EINVAL;
+  }
   L.wall_sites.clear();
   L.n_wall_links = 0;
   std::vector<std::vector<int64_t>> io_sites(n_iolets);
   for (int64_t s = 0; s < n; ++s) {
-    uint32_t m = 0, io = 0;
-    int walls = 0, first_io = -1;
+    if (site_walls[s]) {
+      L.wall_sites.push_back(s);
+      L.n_wall_links += site_walls[s];
+    }
+    if (!(site_io[s] & kDirBits)) continue;
     const int32_t* nb = &L.nbr[(size_t)18 * s];
     for (int i = 1; i < kQ; ++i) {
       const int32_t c = nb[i - 1];
-      if (c >= 0) continue;
-      m |= 1u << i;
-      if (c == -1) {
-        ++walls;
-        m |= kHasWall;
-        continue;
-      }
+      if (c > -2) continue;
       const int k = -2 - c;
-      io |= 1u << i;
-      if (first_io < 0) first_io = k;
-      else if (first_io != k) m |= kMultiIolet;
       if (io_sites[k].empty() || io_sites[k].back() != s) io_sites[k].push_back(s);
-      if (iolets[k].kind == LBM_IOLET_VELOCITY) {
-        if (site_inlet[s] >= 0 && site_inlet[s] != k) {
-          std::snprintf(msg, sizeof msg, "site %lld touches two velocity inlets (%d, %d)",
-                        (long long)s, site_inlet[s], k);
-          err = msg;
-          return LBM_EINVAL;
-        }
-        site_inlet[s] = k;
-        m |= kHasInlet;
-      }
     }
-    const int id = site_inlet[s] >= 0 ? site_inlet[s] : first_io;
-    if (id >= 0) io |= (uint32_t)id << kIoletShift;
-    site_mask[s] = m;
-    site_io[s] = io;
-    if (walls) L.wall_sites.push_back(s);
-    L.n_wall_links += walls;
   }
+  site_walls.clear();
+  site_walls.shrink_to_fit();
   L.iolet_off.assign(n_iolets + 1, 0);
   L.iolet_sites.clear();
   for (int k = 0; k < n_iolets; ++k) {
     L.iolet_sites.insert(L.iolet_sites.end(), io_sites[k].begin(), io_sites[k].end());
     L.iolet_off[k + 1] = (int64_t)L.iolet_sites.size();
   }
-  // ---- tiles
+  // ---- tiles: classified in parallel, then numbered in order
   const int64_t T = (n + kTile - 1) / kTile;
   L.n_tiles = T;
   L.tiles.assign(T, TileDesc{});
+  std::vector<uint8_t> tile_class(T, 0);  // 0 bulk, 1 coherent boundary, 2 irregular
+  parallel_for(T, [&](int64_t t0, int64_t t1, int) {
+    for (int64_t t = t0; t < t1; ++t) {
+      const int64_t x0 = t * kTile;
+      const int lanes = (int)std::min<int64_t>(kTile, n - x0);
+      TileDesc& d = L.tiles[t];
+      d.slot = -1;
+      uint32_t flags = 0, nonfluid = 0;
+      for (int l = 0; l < lanes; ++l) {
+        flags |= site_mask[x0 + l] & (kHasWall | kHasInlet);
+        nonfluid |= site_mask[x0 + l] & kDirBits;
+      }
+      // coherent: in every direction, the lanes whose link is fluid share one offset
+      bool coherent = true;
+      for (int i = 1; i < kQ && coherent; ++i) {
+        bool have = false;
+        int64_t off = 0;
+        for (int l = 0; l < lanes; ++l) {
+          const int32_t c = L.nbr[(size_t)18 * (x0 + l) + (i - 1)];
+          if (c < 0) continue;
+          const int64_t o = (int64_t)c - (x0 + l);
+          if (!have) {
+            have = true;
+            off = o;
+          } else if (o != off) {
+            coherent = false;
+            break;
+          }
+        }
+        d.code[i - 1] = (int32_t)off;
+      }
+      if (coherent && nonfluid == 0) {
+        tile_class[t] = 0;
+        continue;
+      }
+      if (!coherent) {
+        for (int i = 0; i < 18; ++i) d.code[i] = 0;
+        d.mask = kIrregular;
+        tile_class[t] = 2;
+      } else {
+        d.mask = nonfluid;
+        tile_class[t] = 1;
+      }
+      d.mask |= flags;
+    }
+  });
   L.n_bulk = L.n_uniform = L.n_irregular = L.bulk_sites = 0;
   int64_t nb_tiles = 0;  // boundary tiles so far
   for (int64_t t = 0; t < T; ++t) {
-    const int64_t x0 = t * kTile;
-    const int lanes = (int)std::min<int64_t>(kTile, n - x0);
-    TileDesc& d = L.tiles[t];
-    d.slot = -1;
-    uint32_t flags = 0, nonfluid = 0;
-    for (int l = 0; l < lanes; ++l) {
-      flags |= site_mask[x0 + l] & (kHasWall | kHasInlet);
-      nonfluid |= site_mask[x0 + l] & kDirBits;
-    }
-    // coherent: in every direction, the lanes whose link is fluid share one offset
-    bool coherent = true;
-    for (int i = 1; i < kQ && coherent; ++i) {
-      bool have = false;
-      int64_t off = 0;
-      for (int l = 0; l < lanes; ++l) {
-        const int32_t c = L.nbr[(size_t)18 * (x0 + l) + (i - 1)];
-        if (c < 0) continue;
-        const int64_t o = (int64_t)c - (x0 + l);
-        if (!have) {
-          have = true;
-          off = o;
-        } else if (o != off) {
-          coherent = false;
-          break;
-        }
-      }
-      d.code[i - 1] = (int32_t)off;
-    }
-    if (coherent && nonfluid == 0) {
+    if (tile_class[t] == 0) {
       ++L.n_bulk;
-      L.bulk_sites += lanes;
+      L.bulk_sites += std::min<int64_t>(kTile, n - t * kTile);
       continue;
     }
-    if (!coherent) {
-      for (int i = 0; i < 18; ++i) d.code[i] = 0;
-      d.mask = kIrregular;
-      ++L.n_irregular;
-    } else {
-      d.mask = nonfluid;
-      ++L.n_uniform;
-    }
-    d.mask |= flags;
-    d.slot = (int32_t)(nb_tiles * kTile);
+    if (tile_class[t] == 2) ++L.n_irregular;
+    else ++L.n_uniform;
+    L.tiles[t].slot = (int32_t)(nb_tiles * kTile);
     ++nb_tiles;
   }
   L.launch.clear();
@@ -258,11 +377,18 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   L.n_slots = S;
   L.slot_mask.assign(S, 0);
   L.slot_io.assign(S, 0);
-  L.slot_nbr.assign((size_t)18 * S, 0);
+  L.slot_nbr.clear();
+  L.slot_nbr.resize((size_t)18 * S);  // rows of boundary tiles written below; padding lanes zeroed
+  parallel_for(S / kTile, [&](int64_t b0, int64_t b1, int) {
+    for (int64_t b = b0; b < b1; ++b)
+      for (int i = 0; i < 18; ++i)
+        std::fill_n(&L.slot_nbr[(size_t)i * S + b * kTile], kTile, 0);
+  });
   L.slot_prof.assign((size_t)3 * S, 0.0);
   const double nu = (tau - 0.5) / 3.0;  // Eq. (Viscosity), c_s^2 = 1/3
   std::vector<int64_t> slot_of(n, -1);
-  for (int64_t t = 0; t < T; ++t) {
+  parallel_for(T, [&](int64_t t0, int64_t t1, int) {
+  for (int64_t t = t0; t < t1; ++t) {
     const TileDesc& d = L.tiles[t];
     if (d.slot < 0) continue;
     const int64_t x0 = t * kTile;
@@ -307,8 +433,11 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
       L.slot_prof[(size_t)2 * S + m] = pc;
     }
   }
+  });
   L.wall_slot.resize(L.wall_sites.size());
-  for (size_t w = 0; w < L.wall_sites.size(); ++w) L.wall_slot[w] = slot_of[L.wall_sites[w]];
+  parallel_for((int64_t)L.wall_sites.size(), [&](int64_t w0, int64_t w1, int) {
+    for (int64_t w = w0; w < w1; ++w) L.wall_slot[w] = slot_of[L.wall_sites[w]];
+  });
   return LBM_OK;
 }
 

@@ -5,7 +5,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -73,12 +75,37 @@ struct IoletDev {
 };
 static_assert(sizeof(IoletDev) % 16 == 0, "IoletDev alignment");
 
+// Allocator whose resize() leaves new elements uninitialised, for the large
+// host arrays that the builder's threads write in full (first touch happens
+// in parallel, not in a serial zero fill).
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  using value_type = T;
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using big_vector = std::vector<T, NoInitAlloc<T>>;
+
 // Host-side lattice produced by build_lattice().
 struct HostLattice {
   int32_t nx = 0, ny = 0, nz = 0;
   int64_t n = 0;                  // fluid sites
-  std::vector<int32_t> coords;    // [n][3]
-  std::vector<int32_t> nbr;       // [n][18]
+  big_vector<int32_t> coords;     // [n][3]
+  big_vector<int32_t> nbr;        // [n][18]
   std::vector<int64_t> wall_sites;
   int64_t n_wall_links = 0;
   // tiles (32 sites each, in site order)
@@ -90,7 +117,7 @@ struct HostLattice {
   int64_t n_slots = 0;
   std::vector<uint32_t> slot_mask;   // [n_slots]
   std::vector<uint32_t> slot_io;     // [n_slots] iolet-link word (see kIoletShift)
-  std::vector<int32_t> slot_nbr;     // [18][n_slots] absolute neighbour or non-fluid code
+  big_vector<int32_t> slot_nbr;      // [18][n_slots] absolute neighbour or non-fluid code
   std::vector<double> slot_prof;     // [3][n_slots] inlet shape p0, ps, pc
   std::vector<int64_t> wall_slot;    // [n_wall_sites] slot of each wall site
   // iolet site lists (sites with a link into iolet k), CSR
@@ -136,6 +163,7 @@ struct StepParams {
   int64_t step;      // step index (plus *step_dev when step_dev is set)
   int64_t prefetch;  // L2 prefetch distance in tiles of launch order (0: off)
   const int64_t* step_dev;  // device step counter (captured graphs), or NULL
+  int32_t bulk_sites;       // sites per lane of the bulk kernel: 1, or 2 (FP32 / 16-bit)
 };
 
 // One member of an ensemble: its device view and its wall constants.
