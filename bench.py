@@ -24,9 +24,17 @@ needed between steps.
   wall_cost  ms per step with the elastic wall and with rigid bounce-back on the
              same workload (the paper reports the elastic step no dearer);
   mixed_precision  every storage (FP64/FP32/FP16S/BF16S) run from rest on the
-             same workload: MLUPS, and the rel-L2 error of the wall shear
-             stress and of u against the FP64 path, with the speed-up over
-             FP32 of each storage that meets the WSS error budget.
+             same workload: MLUPS, speed-up over FP32 and the rel-L2 error of
+             the wall shear stress and of u against the FP64 path (which
+             matches the FP64 oracle to 1e-10), a table with no chosen error
+             budget;
+  tree       the seeded depth-6 Murray tree (10.25 M sites, 43 % of its tiles
+             irregular): MLUPS, step roofline fraction and WSS error against
+             the FP64 path for FP32, FP16S and BF16S storage;
+  ensemble   256 seeded elastic tubes (63.5 M sites) batched into one launch
+             per step kernel, autotuned: FP16S and FP32 MLUPS, FP32 stepped
+             one lattice at a time, and the WSS error of every storage
+             against the FP64 path on a 32-member subset.
 
 ``--impl reference`` times the oracle alone (the reference arm of this tier).
 Under torchrun every rank runs its own copy of the workload (independent
@@ -59,11 +67,7 @@ def workload(args):
         params = dict(tau=0.6, F=0.85, kappa=0.75 * 40 / 0.5, rho0=1.0)
         name = "long pulsatile tube R=40 L=1024 (~5.15M sites), tau=0.6, Eh/r0=0.5"
     elif args.config == "tree":
-        geo = I.murray_tree(seed=0, depth=6, root_radius=48.0)
-        geo.iolets[0].u_mean = 0.03
-        geo.iolets[0].u_amp = 0.02
-        geo.iolets[0].period = 4000.0
-        params = dict(tau=0.6, F=0.85, kappa=0.75 * 48.0 / 0.5, rho0=1.0)
+        geo, params = tree_workload()
         name = ("seeded Murray tree depth 6, root R=48, 10%% taper (%d sites), tau=0.6, Eh/r0=0.5"
                 % geo.n_fluid())
     elif args.config == "tube8":
@@ -220,42 +224,82 @@ def wall_cost(args, geo, params, steps=2000):
     return out
 
 
-def precision_study(args, geo, params, steps, budget=5e-3):
-    """MLUPS and error of each storage against the FP64 path on the same workload
-    (all from rest, `steps` steps): rel-L2 of the wall shear stress at the wall
-    sites and of u.  The FP64 path matches the oracle to 1e-10 (tests)."""
+def _timed_run(lat, steps):
+    """Device ms of `steps` steps of one lattice (CUDA events on its stream) and
+    the mean step-event duration (fork to join) from lbm_profile."""
     import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lat.profile(True)
+    torch.cuda.synchronize()
+    e0.record(lat.stream)
+    lat.step(steps)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    (step_ms, _), (n_b, _) = lat.profile_read()
+    lat.profile(False)
+    lat.sync()
+    return e0.elapsed_time(e1), step_ms / max(1, n_b)
+
+
+def storage_table(geo, params, steps, storages=("f64", "f32", "f16s", "bf16s"), tune=None):
+    """Each storage run from rest on the same geometry for `steps` steps: MLUPS,
+    step roofline fraction, and the rel-L2 error of the wall shear stress at the
+    wall sites and of u against the FP64 path (first entry).  No error budget is
+    chosen: the table is read at whatever budget a user has."""
     import lbm_inputs as I
     from paper_2108_08783_gb300 import Lattice
+    peak, _ = measured_peaks()
     res, ref = {}, None
-    for st in ("f64", "f32", "f16s", "bf16s"):
+    for st in storages:
         lat = Lattice(geo.labels, geo.iolets, storage=st, tau=params["tau"])
         lat.set_wall("elastic", rho0=params["rho0"], F=params["F"], kappa=params["kappa"])
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(lat.stream)
-        lat.step(steps)
-        e1.record(lat.stream)
-        torch.cuda.synchronize()
-        lat.sync()
-        ms = e0.elapsed_time(e1)
+        if tune and st != "f64":
+            lat.tune(**tune)
+        ms, step_ms = _timed_run(lat, steps)
         ex = lat.export()
         s = ex["wall_sites"]
         wss = lat.wss(s, I.wall_normals(geo, ex["coords"][s]))
         u = lat.moments()[1]
+        info = lat.info()
+        n = lat.n
         lat.close()
         if ref is None:
             ref = (wss, u)
-        res[st] = {"mlups": lat.n * steps / ms / 1e3,
+        res[st] = {"mlups": n * steps / ms / 1e3,
+                   "roofline_frac": n * 2 * 19 * BYTES[st] / (step_ms * 1e-3) / 1e9 / peak,
                    "wss_rel_l2": float(np.linalg.norm(wss - ref[0]) / np.linalg.norm(ref[0])),
                    "u_rel_l2": float(np.linalg.norm(u - ref[1]) / np.linalg.norm(ref[1]))}
-    f32 = res["f32"]["mlups"]
-    for st in ("f32", "f16s", "bf16s"):
-        res[st]["speedup_vs_f32"] = res[st]["mlups"] / f32
-        res[st]["meets_budget"] = res[st]["wss_rel_l2"] <= budget
-    return {"steps": steps, "reference": "f64 storage (matches the FP64 oracle to 1e-10)",
-            "wss_budget": budget, **res}
+        res["irregular_tile_share"] = float(info[6]) / max(1, int(info[3]))
+        res["sites"] = int(n)
+    if "f32" in res:
+        for st in storages:
+            res[st]["speedup_vs_f32"] = res[st]["mlups"] / res["f32"]["mlups"]
+    return res
+
+
+def precision_study(args, geo, params, steps):
+    """Every storage on the main workload (see storage_table)."""
+    res = storage_table(geo, params, steps)
+    return {"steps": steps, "reference": "f64 storage (matches the FP64 oracle to 1e-10)", **res}
+
+
+def tree_workload():
+    import lbm_inputs as I
+    geo = I.murray_tree(seed=0, depth=6, root_radius=48.0)
+    geo.iolets[0].u_mean = 0.03
+    geo.iolets[0].u_amp = 0.02
+    geo.iolets[0].period = 4000.0
+    params = dict(tau=0.6, F=0.85, kappa=0.75 * 48.0 / 0.5, rho0=1.0)
+    return geo, params
+
+
+def tree_study(args, steps):
+    """The depth-6 tree in FP64 (reference), FP32, FP16S and BF16S storage."""
+    geo, params = tree_workload()
+    res = storage_table(geo, params, steps)
+    return {"workload": "seeded Murray tree depth 6, root R=48, tau=0.6, Eh/r0=0.5", "steps": steps,
+            "reference": "f64 storage", **res}
 
 
 def dist_init():
@@ -309,61 +353,112 @@ def ensemble_members(seed=0, count=256):
     return out
 
 
-def run_ensemble(args):
-    """Batched ensemble (256 uneven tubes): one launch per step kernel for all
-    members, autotuned schedule, FP16S storage; compared with the same tubes
-    in FP32, batched and stepped one lattice at a time."""
+def _ensemble_lattices(members, storage):
+    from paper_2108_08783_gb300 import Lattice
+    lats = []
+    for geo, tau, kappa in members:
+        lat = Lattice(geo.labels, geo.iolets, storage=storage, tau=tau)
+        lat.set_wall("elastic", rho0=1.0, F=0.85, kappa=kappa)
+        lats.append(lat)
+    return lats
+
+
+def _timed(fn, stream):
     import torch
-    from paper_2108_08783_gb300 import Ensemble, Lattice
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def ensemble_error_table(members, steps=1000, every=8):
+    """WSS and u error of each storage against the FP64 path on every `every`-th
+    member of the ensemble, batched, `steps` steps from rest."""
+    import lbm_inputs as I
+    from paper_2108_08783_gb300 import Ensemble
+    sub = members[::every]
+    res, ref = {}, None
+    for st in ("f64", "f32", "f16s", "bf16s"):
+        lats = _ensemble_lattices(sub, st)
+        ens = Ensemble(lats)
+        ens.step(steps)
+        ens.sync()
+        wss, u = [], []
+        for (geo, _, _), lat in zip(sub, lats):
+            ex = lat.export()
+            s = ex["wall_sites"]
+            wss.append(lat.wss(s, I.wall_normals(geo, ex["coords"][s])))
+            u.append(lat.moments()[1].ravel())
+        ens.close()
+        for lat in lats:
+            lat.close()
+        wss, u = np.concatenate(wss), np.concatenate(u)
+        if ref is None:
+            ref = (wss, u)
+        res[st] = {"wss_rel_l2": float(np.linalg.norm(wss - ref[0]) / np.linalg.norm(ref[0])),
+                   "u_rel_l2": float(np.linalg.norm(u - ref[1]) / np.linalg.norm(ref[1]))}
+    return {"members": len(sub), "steps": steps, "reference": "f64 storage", **res}
+
+
+def ensemble_study(args, steps, warmup):
+    """Batched ensemble (256 uneven tubes): one launch per step kernel for all
+    members, autotuned schedule; FP16S and FP32 storage batched, FP32 stepped one
+    lattice at a time, and the storages' errors on a subset."""
+    from paper_2108_08783_gb300 import Ensemble
     members = ensemble_members()
-
-    def build(storage):
-        lats = []
-        for geo, tau, kappa in members:
-            lat = Lattice(geo.labels, geo.iolets, storage=storage, tau=tau)
-            lat.set_wall("elastic", rho0=1.0, F=0.85, kappa=kappa)
-            lats.append(lat)
-        return lats
-
-    def timed(fn, stream):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
-
     out = {}
-    k_steps = min(args.steps, ENSEMBLE_STEPS)
+    peak, _ = measured_peaks()
     for storage in ("f16s", "f32"):
-        lats = build(storage)
+        lats = _ensemble_lattices(members, storage)
         n = sum(l.n for l in lats)
         ens = Ensemble(lats)
         best, trials = ens.autotune(trial_steps=20)
-        ens.step(args.warmup)
-        ms = timed(lambda: ens.step(k_steps), ens.stream)
+        ens.step(warmup)
+        ms = _timed(lambda: ens.step(steps), ens.stream)
         ens.sync()
-        out[storage] = {"batched_mlups": n * k_steps / ms / 1e3, "autotuned": best,
-                        "ms_per_step": ms / k_steps}
+        out[storage] = {"batched_mlups": n * steps / ms / 1e3, "autotuned": best,
+                        "ms_per_step": ms / steps,
+                        "roofline_frac": n * 2 * 19 * BYTES[storage] / (ms / steps * 1e-3) / 1e9
+                        / peak}
         ens.close()
         if storage == "f32":
-            k = max(4, args.steps // 50)
-            ms1 = timed(lambda: [l.step(1) for _ in range(k) for l in lats], lats[0].stream)
+            k = max(4, steps // 50)
+            ms1 = _timed(lambda: [l.step(1) for _ in range(k) for l in lats], lats[0].stream)
             out["f32"]["one_at_a_time_mlups"] = n * k / ms1 / 1e3
         for l in lats:
             l.close()
+    out["sites"] = n
+    out["members"] = len(members)
+    out["steps"] = steps
+    out["errors"] = ensemble_error_table(members)
+    return out
+
+
+def run_ensemble(args):
+    """The ensemble as the main line (FP16S batched)."""
+    k_steps = min(max(args.steps, 1), ENSEMBLE_STEPS)
+    out = ensemble_study(args, k_steps, args.warmup)
     line = {
         "metric": METRIC, "value": out["f16s"]["batched_mlups"], "unit": "MLUPS", "n_gpus": 1,
         "steps": k_steps, "warmup": args.warmup,
         "ms_per_step": out["f16s"]["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "ensemble of 256 seeded elastic tubes (%d sites), FP16S storage"
-                   % n, "sites": n},
+                   % out["sites"], "sites": out["sites"]},
         "ensemble": out,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_config(args, name, n, ws):
+    """The `config` object of both arms (same keys and values for one workload)."""
+    return {"workload": name, "sites": n, "storage": args.storage, "wall": "elastic GZS",
+            "l2": "populations (%.0f MB) exceed L2; no flush" % (19 * BYTES[args.storage] * n / 1e6),
+            "parallelism": "replicas x%d" % ws}
 
 
 def run_reference(args):
@@ -393,7 +488,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / done * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": name, "sites": int(orc.n)},
+        "data": "synthetic", "config": run_config(args, name, int(orc.n), ws),
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                          "sample": "%d of %d full oracle steps of the workload (%.1f s budget)"
                          % (done, args.steps, budget)},
@@ -454,7 +549,11 @@ def run_ours(args):
     traffic = kernel_traffic(args.storage, args.config)
     roof = {"bound": "hbm", "kernel": "step: k_bulk + k_boundary (concurrent)", "achieved": achieved,
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "algorithmic_bytes_per_launch": algo, "launch_ms": step_ms,
+            "traffic": traffic,
+            "traffic_kind": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one step's "
+                             "launches; per-launch counters leave out write-back of lines "
+                             "still dirty in L2 when a launch ends"),
+            "algorithmic_bytes_per_launch": algo, "launch_ms": step_ms,
             "k_bulk_window_ms": bulk_ms_sum / max(1, n_bulk_l), "bulk_sites": bulk_sites,
             "bulk_tiles": int(info[4]), "boundary_tiles": int(info[5] + info[6])}
     # ---------------------------------------------------------------- end to end
@@ -486,6 +585,13 @@ def run_ours(args):
     if rank == 0 and not args.no_precision:
         prec = precision_study(args, geo, params, args.precision_steps)
     walls = wall_cost(args, geo, params) if rank == 0 and not args.no_precision else None
+    tree = None
+    if rank == 0 and not args.no_tree and args.config != "tree":
+        tree = tree_study(args, max(args.steps, args.section_steps))
+    ens = None
+    if rank == 0 and not args.no_ensemble:
+        ens = ensemble_study(args, min(max(args.steps, args.section_steps), ENSEMBLE_STEPS),
+                             args.warmup)
     # ---------------------------------------------------------------- CPU baseline
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -505,11 +611,9 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.storage], "data": "synthetic",
-            "config": {"workload": name, "sites": n, "storage": args.storage,
-                       "wall": "elastic GZS", "l2": "populations (%.0f MB) exceed L2; no flush"
-                       % (19 * s * n / 1e6), "parallelism": "replicas x%d" % ws},
+            "config": run_config(args, name, n, ws),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": prec,
-            "wall_cost": walls,
+            "wall_cost": walls, "tree": tree, "ensemble": ens,
             "gpu_launches": int(n_bulk_l + n_bnd_l),
             "clocks": clk,
         }
@@ -539,6 +643,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--precision-steps", type=int, default=4000)
+    ap.add_argument("--section-steps", type=int, default=400,
+                    help="timed steps (at least) of the tree and ensemble sections")
+    ap.add_argument("--no-tree", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

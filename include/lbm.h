@@ -269,10 +269,16 @@ int lbm_wss(lbm_ctx *ctx, const int64_t *sites, const double *normals, int64_t m
  *                        this many arrivals that never come (default 0), so a
  *                        persistent step times out instead of completing;
  *   LBM_TUNE_BULK_SITES  sites per lane of the bulk kernel: 1 (a 32-site tile per
- *                        warp), or 2 (two tiles per warp, each lane updating two
- *                        z-adjacent sites with packed loads, stores and FP32
- *                        pair arithmetic; FP32 and 16-bit storage only, FP64
- *                        ignores it).
+ *                        warp), or two tiles per warp with two sites per lane and
+ *                        FP32 pair arithmetic (FP32 and 16-bit storage; FP64
+ *                        ignores it), the pairs being either two z-adjacent sites
+ *                        of one tile (one packed load or store per direction
+ *                        where the offset is even) or the same lane of both
+ *                        tiles (scalar, aligned accesses; one address when the
+ *                        second tile follows the first with the same offsets):
+ *                        2 = adjacent sites on even steps, two tiles on odd
+ *                        steps; 3 = adjacent sites on both; 4 = two tiles on
+ *                        both.
  * Before using a member's own calls (moments, wall state, ...) call
  * lbm_ensemble_sync.  Errors: LBM_EINVAL (bad arguments, mixed storage or
  * steps), LBM_ESTATE (members drifted apart), LBM_ENOMEM, LBM_ECUDA; the
@@ -310,8 +316,9 @@ int lbm_fmap(const double *alpha, int64_t n_alpha, const double *dr_over_R, int6
 
 /* lbm_tune - launch knobs of one lattice (no effect on results beyond the
  * rounding of the collision arithmetic): LBM_TUNE_PREFETCH (L2 prefetch
- * distance of the bulk kernel, tiles, >= 0) and LBM_TUNE_BULK_SITES (1 or 2
- * sites per lane of the bulk kernel), as for lbm_ensemble_tune.  Defaults are
+ * distance of the bulk kernel, tiles, >= 0) and LBM_TUNE_BULK_SITES (1 to 4:
+ * one or two sites per lane of the bulk kernel and their pairing), as for
+ * lbm_ensemble_tune.  Defaults are
  * chosen per storage at build time.  LBM_EINVAL for another knob or value. */
 int lbm_tune(lbm_ctx *ctx, int32_t knob, int64_t value);
 

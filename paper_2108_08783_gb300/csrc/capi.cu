@@ -276,8 +276,11 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   c->iolet_sites = dev_alloc<int64_t>(c, L.iolet_sites.size());
   c->partial = dev_alloc<double>(c, lbm::reduce_partials());
   c->red_out = dev_alloc<double>(c, 1 + n_iolets);
+  int32_t* mt = L.multi_tiles.empty() ? nullptr : dev_alloc<int32_t>(c, L.multi_tiles.size());
+  int32_t* stab = L.seg_tab.empty() ? nullptr : dev_alloc<int32_t>(c, L.seg_tab.size());
   if (!d.pop || !td || !to || !sm || !sio || !sn || !sp || !sF || !sK || !sdE || !sUw ||
-      !io || !err || !c->iolet_off || !c->iolet_sites || !c->partial || !c->red_out) {
+      !io || !err || !c->iolet_off || !c->iolet_sites || !c->partial || !c->red_out ||
+      (!L.multi_tiles.empty() && !mt) || (!L.seg_tab.empty() && !stab)) {
     g_build_err = "device allocation failed";
     lbm_destroy(c);
     return LBM_ENOMEM;
@@ -294,6 +297,9 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   d.slot_Uw = sUw;
   d.iolets = io;
   d.err = err;
+  d.multi_tiles = mt;
+  d.seg_tab = stab;
+  d.n_multi = (int64_t)L.multi_tiles.size();
 #ifdef LBM_CHECKED
   // checked builds: per-slot store counts of the current step
   d.chk = dev_alloc<int>(c, (size_t)lbm::kQ * d.npad);
@@ -334,6 +340,8 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   chk(h2d(c, io, hio.data(), hio.size()));
   chk(h2d(c, c->iolet_off, L.iolet_off.data(), L.iolet_off.size()));
   chk(h2d(c, c->iolet_sites, L.iolet_sites.data(), L.iolet_sites.size()));
+  if (mt) chk(h2d(c, mt, L.multi_tiles.data(), L.multi_tiles.size()));
+  if (stab) chk(h2d(c, stab, L.seg_tab.data(), L.seg_tab.size()));
   if (S) {
     chk(cudaMemsetAsync(sF, 0, S * sizeof(double), c->stream));
     chk(cudaMemsetAsync(sK, 0, S * sizeof(double), c->stream));
@@ -474,7 +482,7 @@ int lbm_tune(lbm_ctx* c, int32_t knob, int64_t value) {
       c->prefetch = value;
       return LBM_OK;
     case LBM_TUNE_BULK_SITES:
-      if (value != 1 && value != 2) return fail(c, LBM_EINVAL, "bulk sites per lane must be 1 or 2");
+      if (value < 1 || value > 4) return fail(c, LBM_EINVAL, "bulk sites mode must be 1 to 4");
       c->bulk_sites = (int32_t)value;
       return LBM_OK;
   }
@@ -850,10 +858,12 @@ struct lbm_ensemble {
   std::vector<cudaStream_t> member_streams;  // distinct streams of the members
   std::vector<void*> owned;       // device buffers (member 0's allocator)
   lbm::MemberDev* mem_d = nullptr;
-  int64_t* prefix_d = nullptr;    // bulk prefix [n+1], then boundary prefix [n+1]
+  lbm::TileRef* map_d = nullptr;  // tile maps: bulk tiles, then boundary tiles
+  int64_t n_bulk = 0, n_boundary = 0;  // tiles of all members
   int64_t* step_d = nullptr;      // device step counter of captured graphs
   std::vector<int32_t> order;     // schedule: member order in the launch numbering
   int64_t prefetch = 0;           // set from the storage at creation
+  int32_t bulk_sites = 1;         // sites per lane of the bulk kernel, set from the storage
   int64_t graph_steps = 0;        // 0: direct launches
   int persistent = 0;             // 1: one cooperative launch per lbm_ensemble_step
   int barrier_extra = 0;          // fault injection: arrivals the grid barrier waits for in vain
@@ -862,6 +872,7 @@ struct lbm_ensemble {
   int64_t exec_steps = 0;
   int exec_parity = -1;
   lbm::EnsembleLaunch launch{};
+  std::vector<lbm::MemberDev> multi_host;  // members with multi-iolet tiles (host copies)
   std::string err;
 };
 
@@ -886,10 +897,30 @@ void ens_drop_graph(lbm_ensemble* e) {
 }
 
 // Upload the member table and the prefix tables in schedule order.
+// Tile maps in schedule order: for every global bulk (boundary) tile, its
+// member's position in the member table and its launch position there.
+int ens_maps(lbm_ensemble* e) {
+  const int n = (int)e->members.size();
+  std::vector<lbm::TileRef> map((size_t)(e->n_bulk + e->n_boundary));
+  size_t gb = 0, gd = (size_t)e->n_bulk;
+  for (int q = 0; q < n; ++q) {
+    const lbm_ctx* c = e->members[e->order[q]];
+    for (int64_t k = c->d.n_boundary; k < c->d.n_tiles; ++k) map[gb++] = lbm::TileRef{q, (int32_t)k};
+    for (int64_t k = 0; k < c->d.n_boundary; ++k) map[gd++] = lbm::TileRef{q, (int32_t)k};
+  }
+  cudaError_t r = cudaMemcpyAsync(e->map_d, map.data(), map.size() * sizeof(lbm::TileRef),
+                                  cudaMemcpyHostToDevice, e->stream);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);  // map is a temporary
+  if (r != cudaSuccess) return ens_cuda(e, r, "ensemble tile map upload");
+  e->launch.bulk_map = e->map_d;
+  e->launch.boundary_map = e->map_d + e->n_bulk;
+  ens_drop_graph(e);
+  return LBM_OK;
+}
+
 int ens_upload(lbm_ensemble* e) {
   const int n = (int)e->members.size();
   std::vector<lbm::MemberDev> tab(n);
-  std::vector<int64_t> pre(2 * (n + 1), 0);
   for (int q = 0; q < n; ++q) {
     const lbm_ctx* c = e->members[e->order[q]];
     lbm::MemberDev& md = tab[q];
@@ -899,22 +930,20 @@ int ens_upload(lbm_ensemble* e) {
     md.omega = 1.0 / c->tau;
     md.rho0 = c->rho0;
     md.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
-    pre[q + 1] = pre[q] + (c->d.n_tiles - c->d.n_boundary);
-    pre[n + 1 + q + 1] = pre[n + 1 + q] + c->d.n_boundary;
   }
   cudaError_t r = cudaMemcpyAsync(e->mem_d, tab.data(), n * sizeof(lbm::MemberDev),
                                   cudaMemcpyHostToDevice, e->stream);
-  if (r == cudaSuccess)
-    r = cudaMemcpyAsync(e->prefix_d, pre.data(), pre.size() * sizeof(int64_t),
-                        cudaMemcpyHostToDevice, e->stream);
-  if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);  // tab, pre are temporaries
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);  // tab is a temporary
   if (r != cudaSuccess) return ens_cuda(e, r, "ensemble upload");
+  e->multi_host.clear();
+  for (const lbm::MemberDev& md : tab)
+    if (md.d.n_multi > 0) e->multi_host.push_back(md);
+  e->launch.multi_host = e->multi_host.data();
+  e->launch.n_multi_members = (int32_t)e->multi_host.size();
   e->launch.mem = e->mem_d;
-  e->launch.bulk_prefix = e->prefix_d;
-  e->launch.boundary_prefix = e->prefix_d + (n + 1);
   e->launch.n_members = n;
-  e->launch.n_bulk_tiles = pre[n];
-  e->launch.n_boundary_tiles = pre[2 * n + 1];
+  e->launch.n_bulk_tiles = e->n_bulk;
+  e->launch.n_boundary_tiles = e->n_boundary;
   ens_drop_graph(e);
   return LBM_OK;
 }
@@ -954,6 +983,7 @@ int lbm_ensemble_create(lbm_ctx* const* members, int32_t n, lbm_ensemble** out) 
   e->members.assign(members, members + n);
   e->storage = members[0]->storage;
   e->prefetch = default_prefetch(e->storage);
+  e->bulk_sites = default_bulk_sites(e->storage);
   for (lbm_ctx* c : e->members)
     if (std::find(e->member_streams.begin(), e->member_streams.end(), c->stream) ==
         e->member_streams.end())
@@ -977,15 +1007,20 @@ int lbm_ensemble_create(lbm_ctx* const* members, int32_t n, lbm_ensemble** out) 
     if (p) e->owned.push_back(p);
     return p;
   };
+  for (lbm_ctx* c : e->members) {
+    e->n_bulk += c->d.n_tiles - c->d.n_boundary;
+    e->n_boundary += c->d.n_boundary;
+  }
   e->mem_d = static_cast<lbm::MemberDev*>(alloc(n * sizeof(lbm::MemberDev)));
-  e->prefix_d = static_cast<int64_t*>(alloc(2 * (n + 1) * sizeof(int64_t)));
+  e->map_d = static_cast<lbm::TileRef*>(
+      alloc(std::max<int64_t>(1, e->n_bulk + e->n_boundary) * sizeof(lbm::TileRef)));
   e->step_d = static_cast<int64_t*>(alloc(sizeof(int64_t)));
   e->sync_d = static_cast<lbm::GridSync*>(alloc(sizeof(lbm::GridSync)));
-  if (!e->mem_d || !e->prefix_d || !e->step_d || !e->sync_d) {
+  if (!e->mem_d || !e->map_d || !e->step_d || !e->sync_d) {
     lbm_ensemble_destroy(e);
     return LBM_ENOMEM;
   }
-  if (ens_upload(e) != LBM_OK) {
+  if (ens_maps(e) != LBM_OK || ens_upload(e) != LBM_OK) {
     lbm_ensemble_destroy(e);
     return LBM_ECUDA;
   }
@@ -1012,6 +1047,7 @@ int lbm_ensemble_tune(lbm_ensemble* e, int32_t knob, int64_t value) {
       } else if (value != 0) {
         return ens_fail(e, LBM_EINVAL, "schedule must be 0 (given order) or 1 (largest first)");
       }
+      if (ens_maps(e) != LBM_OK) return LBM_ECUDA;
       return ens_upload(e);
     }
     case LBM_TUNE_GRAPH_STEPS:
@@ -1026,6 +1062,11 @@ int lbm_ensemble_tune(lbm_ensemble* e, int32_t knob, int64_t value) {
     case LBM_TUNE_BARRIER_EXTRA:
       if (value < 0 || value > 1024) return ens_fail(e, LBM_EINVAL, "barrier extra out of range");
       e->barrier_extra = (int)value;
+      return LBM_OK;
+    case LBM_TUNE_BULK_SITES:
+      if (value < 1 || value > 4) return ens_fail(e, LBM_EINVAL, "bulk sites mode must be 1 to 4");
+      e->bulk_sites = (int32_t)value;
+      ens_drop_graph(e);
       return LBM_OK;
   }
   return ens_fail(e, LBM_EINVAL, "unknown tuning knob");
@@ -1048,6 +1089,7 @@ int lbm_ensemble_step(lbm_ensemble* e, int64_t n_steps) {
   const lbm::StepStreams ss{e->stream, e->side, e->fork, e->join};
   lbm::StepParams p{};
   p.prefetch = e->prefetch;
+  p.bulk_sites = e->bulk_sites;
   int64_t done = 0;
   if (e->persistent && n_steps > 0) {
     p.step = step0;

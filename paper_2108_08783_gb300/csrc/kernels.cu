@@ -162,6 +162,19 @@ struct Mom {
   C drho, rho, ux, uy, uz, usq;
 };
 
+// 1 / (1 + drho) to about one rounding of the exact value, from r = 1 + drho
+// (rounded) and a reciprocal estimate y of r: the rounding error of r,
+// d = drho - (r - 1), is exact (r - 1 is exact for r in [1/2, 2]), and one
+// Newton step on the residual 1 - y (r + d) removes both d and the error of y.
+// Without it the rounding of r (2^-24 relative in FP32) enters every velocity
+// u = j / rho once per step.
+template <class C>
+__device__ __forceinline__ C inv_one_plus(C drho, C r, C y) {
+  const C d = drho - (r - C(1));
+  const C e = fma_pin(-y, d, fma_pin(-y, r, C(1)));
+  return fma_pin(y, e, y);
+}
+
 // Eqs. (Density), (Momentum) on shifted populations (sum w_i c_i = 0).
 template <class C>
 __device__ __forceinline__ Mom<C> moments(const C (&g)[kQ]) {
@@ -176,7 +189,7 @@ __device__ __forceinline__ Mom<C> moments(const C (&g)[kQ]) {
   const C jy = (a3 + a7) - (a9 - a15) + a17;
   const C jz = (a5 + a11) - (a13 - a15) - a17;
   m.rho = C(1) + m.drho;
-  const C inv = recip(m.rho);
+  const C inv = inv_one_plus(m.drho, m.rho, recip(m.rho));
   m.ux = jx * inv;
   m.uy = jy * inv;
   m.uz = jz * inv;
@@ -229,6 +242,20 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(src)),
                "r"(bytes)
                : "memory");
+}
+// Asynchronous 8-byte global -> shared copy: no register holds the value while
+// it is in flight; the copying thread waits for its own copies with
+// cp_async_wait_all before reading them.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)),
+               "l"(__cvta_generic_to_global(gmem))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
@@ -476,8 +503,67 @@ __device__ __forceinline__ void chk_count2(int* chk, const S* P0, const S* p, in
   chk_count(chk, P0, p + 1, lim, err);
 }
 
+// The collision of bulk_update for two sites at once, on packed pairs: g
+// holds the pre-collision values; store0(g*_0) receives the rest population
+// and store<a, b>(g*_a, g*_b) those of each opposite pair (a odd, b = a + 1).
+template <class St0, class St>
+__device__ __forceinline__ void collide2(const F2 (&g)[kQ], F2 omega, int* err_lo, int* err_hi,
+                                         St0&& store0, St&& store) {
+  // Eqs. (Density), (Momentum), grouped as in moments()
+  const F2 a1 = sub2(g[1], g[2]), a3 = sub2(g[3], g[4]), a5 = sub2(g[5], g[6]);
+  const F2 a7 = sub2(g[7], g[8]), a9 = sub2(g[9], g[10]), a11 = sub2(g[11], g[12]);
+  const F2 a13 = sub2(g[13], g[14]), a15 = sub2(g[15], g[16]), a17 = sub2(g[17], g[18]);
+  const F2 drho =
+      add2(add2(add2(add2(g[0], add2(g[1], g[2])), add2(add2(g[3], g[4]), add2(g[5], g[6]))),
+                add2(add2(add2(g[7], g[8]), add2(g[9], g[10])),
+                     add2(add2(g[11], g[12]), add2(g[13], g[14])))),
+           add2(add2(g[15], g[16]), add2(g[17], g[18])));
+  const F2 jx = add2(add2(add2(a1, a7), add2(a9, a11)), a13);
+  const F2 jy = add2(sub2(add2(a3, a7), sub2(a9, a15)), a17);
+  const F2 jz = sub2(sub2(add2(a5, a11), sub2(a13, a15)), a17);
+  const F2 rho = add2(bc2(1.0f), drho);
+  float r0, r1;
+  split2(rho, r0, r1);
+  if (unstable(r0)) atomicOr(err_lo, kErrUnstable);
+  if (unstable(r1)) atomicOr(err_hi, kErrUnstable);
+  float d0, d1;
+  split2(drho, d0, d1);
+  const F2 inv = mk2(inv_one_plus(d0, r0, rcp_approx(r0)), inv_one_plus(d1, r1, rcp_approx(r1)));
+  const F2 ux = mul2(jx, inv), uy = mul2(jy, inv), uz = mul2(jz, inv);
+  const F2 usq = mul2(bc2(1.5f), fma2(uz, uz, fma2(uy, uy, mul2(ux, ux))));
+  // rest population: g*_0 = g_0 + omega (w_0 (drho - rho usq) - g_0)
+  const F2 e0 = mul2(bc2(1.0f / 3.0f), sub2(drho, mul2(rho, usq)));
+  store0(fma2(omega, sub2(e0, g[0]), g[0]));
+  // opposite pairs (a, b): g^eq = even +- odd (see bulk_update)
+  const F2 wd1 = mul2(drho, bc2(1.0f / 18.0f)), wd2 = mul2(drho, bc2(1.0f / 36.0f));
+  const F2 wr1 = mul2(rho, bc2(1.0f / 18.0f)), wr2 = mul2(rho, bc2(1.0f / 36.0f));
+  const F2 w3r1 = mul2(rho, bc2(3.0f / 18.0f)), w3r2 = mul2(rho, bc2(3.0f / 36.0f));
+  const F2 nusq = sub2(bc2(0.0f), usq);
+  unroll<9>([&](auto Pi) {
+    constexpr int a = 2 * decltype(Pi)::value + 1;
+    constexpr int pp = (a + 1) / 2;
+    F2 cu;
+    if constexpr (pp == 1) cu = ux;
+    else if constexpr (pp == 2) cu = uy;
+    else if constexpr (pp == 3) cu = uz;
+    else if constexpr (pp == 4) cu = add2(ux, uy);
+    else if constexpr (pp == 5) cu = sub2(ux, uy);
+    else if constexpr (pp == 6) cu = add2(ux, uz);
+    else if constexpr (pp == 7) cu = sub2(ux, uz);
+    else if constexpr (pp == 8) cu = add2(uy, uz);
+    else cu = sub2(uy, uz);
+    const F2 q = fma2(mul2(bc2(4.5f), cu), cu, nusq);
+    const F2 even = (a <= 6) ? fma2(wr1, q, wd1) : fma2(wr2, q, wd2);
+    const F2 odd = mul2((a <= 6) ? w3r1 : w3r2, cu);
+    const F2 sa = fma2(omega, sub2(add2(even, odd), g[a]), g[a]);
+    const F2 sb = fma2(omega, sub2(sub2(even, odd), g[a + 1]), g[a + 1]);
+    store(std::integral_constant<int, a>{}, sa, sb);
+  });
+}
+
 // Branch-free update of the sites x, x + 1 (x even) whose 18 links are fluid,
-// both with the neighbour offsets dsc.
+// both with the neighbour offsets dsc: one address per direction for both
+// sites, packed loads and stores where the offset is even.
 template <class S, bool ODD>
 __device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const int32_t* dsc,
                                              double omega_t, int* err, int* chk) {
@@ -494,70 +580,84 @@ __device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const 
       g[j] = (dd & 1) ? Cd::ld_un(q) : Cd::ld_al(q);
     }
   });
-  // Eqs. (Density), (Momentum), grouped as in moments()
-  const F2 a1 = sub2(g[1], g[2]), a3 = sub2(g[3], g[4]), a5 = sub2(g[5], g[6]);
-  const F2 a7 = sub2(g[7], g[8]), a9 = sub2(g[9], g[10]), a11 = sub2(g[11], g[12]);
-  const F2 a13 = sub2(g[13], g[14]), a15 = sub2(g[15], g[16]), a17 = sub2(g[17], g[18]);
-  const F2 drho =
-      add2(add2(add2(add2(g[0], add2(g[1], g[2])), add2(add2(g[3], g[4]), add2(g[5], g[6]))),
-                add2(add2(add2(g[7], g[8]), add2(g[9], g[10])),
-                     add2(add2(g[11], g[12]), add2(g[13], g[14])))),
-           add2(add2(g[15], g[16]), add2(g[17], g[18])));
-  const F2 jx = add2(add2(add2(a1, a7), add2(a9, a11)), a13);
-  const F2 jy = add2(sub2(add2(a3, a7), sub2(a9, a15)), a17);
-  const F2 jz = sub2(sub2(add2(a5, a11), sub2(a13, a15)), a17);
-  const F2 rho = add2(bc2(1.0f), drho);
-  float r0, r1;
-  split2(rho, r0, r1);
-  if (unstable(r0) || unstable(r1)) atomicOr(err, kErrUnstable);
-  const F2 inv = mk2(rcp_approx(r0), rcp_approx(r1));
-  const F2 ux = mul2(jx, inv), uy = mul2(jy, inv), uz = mul2(jz, inv);
-  const F2 usq = mul2(bc2(1.5f), fma2(uz, uz, fma2(uy, uy, mul2(ux, ux))));
-  const F2 omega = bc2(float(omega_t));
-  // rest population: g*_0 = g_0 + omega (w_0 (drho - rho usq) - g_0)
-  const F2 e0 = mul2(bc2(1.0f / 3.0f), sub2(drho, mul2(rho, usq)));
-  Cd::st_al(P + x, fma2(omega, sub2(e0, g[0]), g[0]));
-  chk_count2(chk, P, P + x, kQ * np, err);
-  // opposite pairs (a, b): g^eq = even +- odd (see bulk_update)
-  const F2 wd1 = mul2(drho, bc2(1.0f / 18.0f)), wd2 = mul2(drho, bc2(1.0f / 36.0f));
-  const F2 wr1 = mul2(rho, bc2(1.0f / 18.0f)), wr2 = mul2(rho, bc2(1.0f / 36.0f));
-  const F2 w3r1 = mul2(rho, bc2(3.0f / 18.0f)), w3r2 = mul2(rho, bc2(3.0f / 36.0f));
-  const F2 nusq = sub2(bc2(0.0f), usq);
-  unroll<9>([&](auto Pi) {
-    constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
-    constexpr int pp = (a + 1) / 2;
-    F2 cu;
-    if constexpr (pp == 1) cu = ux;
-    else if constexpr (pp == 2) cu = uy;
-    else if constexpr (pp == 3) cu = uz;
-    else if constexpr (pp == 4) cu = add2(ux, uy);
-    else if constexpr (pp == 5) cu = sub2(ux, uy);
-    else if constexpr (pp == 6) cu = add2(ux, uz);
-    else if constexpr (pp == 7) cu = sub2(ux, uz);
-    else if constexpr (pp == 8) cu = add2(uy, uz);
-    else cu = sub2(uy, uz);
-    const F2 q = fma2(mul2(bc2(4.5f), cu), cu, nusq);
-    const F2 even = (a <= 6) ? fma2(wr1, q, wd1) : fma2(wr2, q, wd2);
-    const F2 odd = mul2((a <= 6) ? w3r1 : w3r2, cu);
-    const F2 sa = fma2(omega, sub2(add2(even, odd), g[a]), g[a]);
-    const F2 sb = fma2(omega, sub2(sub2(even, odd), g[b]), g[b]);
-    if constexpr (ODD) {
-      const int32_t da = lds_volatile(dsc + a - 1), db = lds_volatile(dsc + b - 1);
-      S* pa = P + a * np + x + da;
-      S* pb = P + b * np + x + db;
-      if (da & 1) Cd::st_un(pa, sa);
-      else Cd::st_al(pa, sa);
-      if (db & 1) Cd::st_un(pb, sb);
-      else Cd::st_al(pb, sb);
-      chk_count2(chk, P, pa, kQ * np, err);
-      chk_count2(chk, P, pb, kQ * np, err);
+  collide2(
+      g, bc2(float(omega_t)), err, err,
+      [&](F2 s0) {
+        Cd::st_al(P + x, s0);
+        chk_count2(chk, P, P + x, kQ * np, err);
+      },
+      [&](auto A, F2 sa, F2 sb) {
+        constexpr int a = decltype(A)::value, b = a + 1;
+        if constexpr (ODD) {
+          const int32_t da = lds_volatile(dsc + a - 1), db = lds_volatile(dsc + b - 1);
+          S* pa = P + a * np + x + da;
+          S* pb = P + b * np + x + db;
+          if (da & 1) Cd::st_un(pa, sa);
+          else Cd::st_al(pa, sa);
+          if (db & 1) Cd::st_un(pb, sb);
+          else Cd::st_al(pb, sb);
+          chk_count2(chk, P, pa, kQ * np, err);
+          chk_count2(chk, P, pb, kQ * np, err);
+        } else {
+          Cd::st_al(P + b * np + x, sa);
+          Cd::st_al(P + a * np + x, sb);
+          chk_count2(chk, P, P + b * np + x, kQ * np, err);
+          chk_count2(chk, P, P + a * np + x, kQ * np, err);
+        }
+      });
+}
+
+// Branch-free update of site xa of one bulk tile and site xb of another tile of
+// the same lattice (the same lane of both), with their offsets da and db.
+// SAME: the second tile directly follows the first with the same offsets, so
+// each of its addresses is the first tile's plus one tile (an immediate
+// offset, no second address).
+template <class S, bool ODD, bool SAME>
+__device__ __forceinline__ void bulk_update2v(S* P, int64_t np, int64_t xa, int64_t xb,
+                                              const int32_t* da, const int32_t* db, double omega_t,
+                                              int* err, int* chk) {
+  using Cd = Codec<S>;
+  F2 g[kQ];
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int o = dir_opp(j);
+    const S *qa, *qb;
+    if constexpr (!ODD || j == 0) {
+      qa = P + j * np + xa;
+      qb = SAME ? qa + kTile : P + j * np + xb;
     } else {
-      Cd::st_al(P + b * np + x, sa);
-      Cd::st_al(P + a * np + x, sb);
-      chk_count2(chk, P, P + b * np + x, kQ * np, err);
-      chk_count2(chk, P, P + a * np + x, kQ * np, err);
+      qa = P + o * np + xa + da[o - 1];
+      qb = SAME ? qa + kTile : P + o * np + xb + db[o - 1];
     }
+    g[j] = mk2(Cd::ld(qa, j), Cd::ld(qb, j));
   });
+  auto put = [&](S* pa, S* pb, F2 v, int i) {
+    float lo, hi;
+    split2(v, lo, hi);
+    Cd::st(pa, i, lo);
+    Cd::st(pb, i, hi);
+    chk_count(chk, P, pa, kQ * np, err);
+    chk_count(chk, P, pb, kQ * np, err);
+  };
+  collide2(
+      g, bc2(float(omega_t)), err, err,
+      [&](F2 s0) { put(P + xa, SAME ? P + xa + kTile : P + xb, s0, 0); },
+      [&](auto A, F2 sa, F2 sb) {
+        constexpr int i = decltype(A)::value, k = i + 1;  // the pair (i, k = opp i)
+        if constexpr (ODD) {
+          S* pi = P + i * np + xa + lds_volatile(da + i - 1);
+          S* pk = P + k * np + xa + lds_volatile(da + k - 1);
+          S* qi = SAME ? pi + kTile : P + i * np + xb + lds_volatile(db + i - 1);
+          S* qk = SAME ? pk + kTile : P + k * np + xb + lds_volatile(db + k - 1);
+          put(pi, qi, sa, i);
+          put(pk, qk, sb, k);
+        } else {
+          S* pk = P + k * np + xa;
+          S* pi = P + i * np + xa;
+          put(pk, SAME ? pk + kTile : P + k * np + xb, sa, i);
+          put(pi, SAME ? pi + kTile : P + i * np + xb, sb, k);
+        }
+      });
 }
 
 // Update of a site of a boundary tile.  `code[i]` holds the tile's uniform
@@ -588,27 +688,249 @@ __device__ __forceinline__ void boundary_load(const S* P, int64_t np, int64_t x,
   });
 }
 
-// D3Q19 vectors and weights for directions known only at run time (the
-// boundary rule loops over the links that leave the fluid).
-__constant__ float c_dir_f[4][kQ] = {
-    {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0},
-    {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1},
-    {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1},
-    {1.f / 3, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 36, 1.f / 36,
-     1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36,
-     1.f / 36}};
-__constant__ double c_dir_d[4][kQ] = {
-    {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0},
-    {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1},
-    {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1},
-    {1.0 / 3, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 36, 1.0 / 36,
-     1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36,
-     1.0 / 36}};
-
+// Per-warp shared-memory area of the boundary kernels, in compute-type units:
+// rows 0..18 the parked populations g, rows 19..24 the lanes' iolet states,
+// then [5][32] doubles of per-site data (F, kappa/3, inlet profile p0, ps, pc).
 template <class C>
-__device__ __forceinline__ C dir_tab(int row, int i) {
-  if constexpr (std::is_same<C, double>::value) return c_dir_d[row][i];
-  else return c_dir_f[row][i];
+struct BoundaryArea {
+  static constexpr int size = 25 * kTile + 5 * kTile * (int)(sizeof(double) / sizeof(C));
+};
+constexpr int kAreaIolet = 19;  // first row of the iolet states
+constexpr int kAreaSite = 25;   // first row (compute-type units) of the per-site doubles
+
+// Update of a boundary site whose iolet links (if any) all lead to one iolet,
+// without branches that differ between lanes: every direction does one load
+// and one store, and each store's value and address are selected.
+//   Loads: direction j from the site's own slot when the link opp(j) leaves
+//     the fluid, else (odd steps) from the neighbour along opp(j).
+//   Collision in the pair form of bulk_update: for each opposite pair (a, b)
+//     the even and odd parts of the equilibrium give g^eq_a, g^eq_b and the
+//     post-collision g*_a, g*_b.
+//   Link i of the pair leaving the fluid (j = opp i, the other direction of the
+//     same pair): half-way bounce-back stores g*_i into (x, j); the GZS form
+//     stores f^eq_j(rho_b, u_b) + (1 - 1/tau) (g_j - g^eq_j) into (x, j), with
+//     (rho_b, u_b) = (rho, U_w) at a wall link - whose equilibrium parts are
+//     those of (rho, u) with c.u scaled by U_w/u_f = sw - and the site's iolet
+//     state at an iolet link: (rho, u_in) at a velocity inlet, (rho_out, u) at a
+//     density outlet.  A fluid link i streams g*_i: into (x, j) on even steps,
+//     into (x + c_i, i) on odd steps.
+// warp_io / warp_wall (warp-uniform): some lane of the tile has iolet links /
+// elastic wall links, so their equilibria are computed at all; warp_nf: the
+// union of the tile's non-fluid directions (pairs no lane needs skip the
+// boundary values); site: the
+// warp's [5][32] per-site F, kappa/3, p0, ps, pc (copies in flight until
+// cp_async_wait_all); area: the warp's shared-memory area (BoundaryArea).
+template <class S, bool ODD>
+__device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepParams& p,
+                                              double omega_t, S* P, int64_t x,
+                                              const int32_t* offp, int ostride, uint32_t smask,
+                                              uint32_t iom, const double* site,
+                                              const int32_t* nbr_s, int lane, int64_t slot,
+                                              bool warp_io, bool warp_wall, uint32_t warp_nf,
+                                              typename Codec<S>::C* area) {
+  using Cd = Codec<S>;
+  using C = typename Cd::C;
+  const int64_t np = d.npad;
+  const uint32_t nf = smask & kDirBits;
+  // Odd steps: the offset nbr(x, i) - x of a fluid link i is offp[(i - 1)
+  // ostride] (the tile's or the lane's segment's offsets with stride 1, or the
+  // lane's column of the staged per-site rows with stride 32), read the same
+  // way in every case, and the choice between the site's own slot and the
+  // neighbour's is a select, not a branch.
+  auto off = [&](int i) -> int32_t { return offp[(i - 1) * ostride]; };
+  // the same offset re-read at store time (volatile: not held in registers
+  // from the loads to the stores)
+  auto off_again = [&](int i) -> int32_t { return lds_volatile(offp + (i - 1) * ostride); };
+  C g[kQ];
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int o = dir_opp(j);
+    if constexpr (!ODD || j == 0) {
+      g[j] = Cd::ld(P + j * np + x, j);
+    } else {
+      const bool own = (nf >> o) & 1u;
+      int64_t y = own ? x : x + off(o);
+      if (!chk_site(y, d.n, d.err)) y = x;  // checked builds: flagged, read a safe slot
+      // one index from one base (row selected as an integer), so that no
+      // per-direction row pointer is kept live across the update
+      g[j] = Cd::ld(P + ((int64_t)(own ? j : o) * np + y), j);
+    }
+  });
+  const Mom<C> m = moments(g);
+  // Park g in the warp's area; the pairs below read it back (volatile, so the
+  // 19 values are not held in registers through the boundary rule).
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    area[j * kTile + lane] = g[j];
+  });
+  auto gv = [&](int j) -> C { return static_cast<const volatile C*>(area)[j * kTile + lane]; };
+  if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
+  const C omega = C(omega_t);
+  const C keep = C(1) - omega;  // (1 - 1/tau)
+  // Elastic wall (Sec. 2.3-2.4): dE in FP64, the ratio sw = U_w/u_f =
+  // (F + dr - dx)/dr with dr = dx + dE in the compute type.
+  C sw = C(0);
+  if ((smask & kHasWall) && p.elastic) {
+    cp_async_wait_all();
+    const double Fw = site[lane], Kw = site[kTile + lane];  // F, kappa c_s^2
+    const double dp = (double)m.rho - p.rho0;
+    const double dE = Kw * (dp > 0.0 ? dp : 0.0);
+    if constexpr (std::is_same<C, double>::value) {
+      const double dr = 1.0 + dE;
+      sw = (Fw + dr - 1.0) / dr;
+    } else {
+      const float e = (float)dE;
+      sw = (float(Fw) + e) * recip(1.0f + e);
+    }
+    if (p.write_state) {
+      const int64_t ss = d.slot_stride;
+      d.slot_dE[slot] = dE;
+      d.slot_Uw[slot] = (double)(sw * m.ux);
+      d.slot_Uw[ss + slot] = (double)(sw * m.uy);
+      d.slot_Uw[2 * ss + slot] = (double)(sw * m.uz);
+    }
+  }
+  const C sw2 = sw * sw;
+  // The site's iolet state (rho_b, u_b): velocity inlet (Sec. 3) u_in =
+  // a (u_mean p0 + u_amp (ps sin th + pc cos th)) with rho_b = rho; density
+  // outlet rho_b = rho_out with u_b = u.  Parked in the warp's shared-memory
+  // area (read back only by tiles with iolet links), not held in registers.
+  if (warp_io) {
+  C rb = m.rho, drb = m.drho, ubx = m.ux, uby = m.uy, ubz = m.uz, usqb = m.usq;
+  if (iom & kDirBits) {
+    const int k = (int)((iom & kIoletIdBits) >> kIoletShift);
+    const IoletDev& io = d.iolets[k];
+    if (io.kind == LBM_IOLET_VELOCITY) {
+      cp_async_wait_all();
+      const double pr0 = site[2 * kTile + lane], pr1 = site[3 * kTile + lane];
+      const double pr2 = site[4 * kTile + lane];
+      double gval = io.u_mean * pr0;
+      if (!io.steady) {
+        double sn, cs;
+        const int64_t step = p.step + (p.step_dev ? *p.step_dev : 0);
+        if constexpr (std::is_same<C, double>::value) {
+          sincos(2.0 * M_PI * (double)step / io.period + io.phase, &sn, &cs);
+        } else {
+          double t = (double)step / io.period + io.phase * (0.5 / M_PI);
+          t -= floor(t);
+          float sf, cf;
+          sincospif(2.0f * (float)t, &sf, &cf);
+          sn = sf;
+          cs = cf;
+        }
+        gval = fma(io.u_amp, fma(pr1, sn, pr2 * cs), gval);
+      }
+      ubx = C(gval * io.axis[0]);
+      uby = C(gval * io.axis[1]);
+      ubz = C(gval * io.axis[2]);
+      usqb = C(1.5) * (ubx * ubx + uby * uby + ubz * ubz);
+    } else {
+      rb = C(io.rho);
+      drb = C(io.rho - 1.0);
+    }
+  }
+  C* iost = area + kAreaIolet * kTile;
+  iost[0 * kTile + lane] = rb;
+  iost[1 * kTile + lane] = drb;
+  iost[2 * kTile + lane] = ubx;
+  iost[3 * kTile + lane] = uby;
+  iost[4 * kTile + lane] = ubz;
+  iost[5 * kTile + lane] = usqb;
+  }
+  // rest population: stays at x
+  {
+    const C g0 = gv(0);
+    Cd::st(P + x, 0, g0 + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g0));
+  }
+  chk_count(d.chk, P, P + x, kQ * np, d.err);
+  const bool bounce = !p.elastic;
+  // Store addresses from a base the compiler cannot identify with the load
+  // addresses (an opaque copy): otherwise it keeps the 19 load addresses live
+  // until the stores that reuse them.
+  S* Pst;
+  asm volatile("mov.b64 %0, %1;" : "=l"(Pst) : "l"(P));
+  unroll<9>([&](auto Pi) {
+    constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
+    constexpr C w = a <= 6 ? C(1.0 / 18.0) : C(1.0 / 36.0);
+    const C cu = cdot<a, C>(m.ux, m.uy, m.uz);
+    const C wr = m.rho * w;
+    const C wrq = wr * (C(4.5) * cu * cu - m.usq);
+    const C wd = m.drho * w;
+    const C even = wd + wrq;
+    const C odd = C(3) * wr * cu;
+    const C eqa = even + odd, eqb = even - odd;
+    const C ga = gv(a), gb = gv(b);
+    const C sa = ga + omega * (eqa - ga);
+    const C sb = gb + omega * (eqb - gb);
+    // the pair's links leave the fluid at some lane of the tile (warp-uniform)
+    const bool pair_nf = (warp_nf >> a) & 3u;
+    // GZS values of the pair's two directions at a wall: f^eq(rho, sw u) parts
+    C wa = C(0), wb = C(0);
+    if (warp_wall && pair_nf) {
+      const C evw = wd + sw2 * wrq, odw = sw * odd;
+      wa = evw + odw + keep * (ga - eqa);
+      wb = evw - odw + keep * (gb - eqb);
+    }
+    // ... and at the site's iolet
+    C ia = C(0), ib = C(0);
+    if (warp_io && pair_nf) {
+      const C* iost = area + kAreaIolet * kTile;
+      const C rb = iost[0 * kTile + lane], drb = iost[1 * kTile + lane];
+      const C cub = cdot<a, C>(iost[2 * kTile + lane], iost[3 * kTile + lane],
+                               iost[4 * kTile + lane]);
+      const C evb = w * (drb + rb * (C(4.5) * cub * cub - iost[5 * kTile + lane]));
+      const C odb = w * C(3) * rb * cub;
+      ia = evb + odb + keep * (ga - eqa);
+      ib = evb - odb + keep * (gb - eqb);
+    }
+    // link a (store into direction b's slot when it leaves the fluid) and link b
+    const bool nfa = (nf >> a) & 1u, nfb = (nf >> b) & 1u;
+    const bool ioa = (iom >> a) & 1u, iob = (iom >> b) & 1u;
+    const C va = nfa ? (ioa ? ib : (bounce ? sa : wb)) : sa;
+    const C vb = nfb ? (iob ? ia : (bounce ? sb : wa)) : sb;
+    S* pa;
+    S* pb;
+    if constexpr (ODD) {
+      int64_t ya = nfa ? x : x + off_again(a), yb = nfb ? x : x + off_again(b);
+      if (!chk_site(ya, d.n, d.err)) ya = x;
+      if (!chk_site(yb, d.n, d.err)) yb = x;
+      pa = Pst + ((int64_t)(nfa ? b : a) * np + ya);
+      pb = Pst + ((int64_t)(nfb ? a : b) * np + yb);
+    } else {
+      pa = Pst + b * np + x;
+      pb = Pst + a * np + x;
+    }
+    Cd::st(pa, nfa ? b : a, va);
+    Cd::st(pb, nfb ? a : b, vb);
+    chk_count(d.chk, P, pa, kQ * np, d.err);
+    chk_count(d.chk, P, pb, kQ * np, d.err);
+  });
+}
+
+// D3Q19 vectors and weights for directions known only at run time (the
+// boundary rule loops over the links that leave the fluid), computed from bit
+// masks of the directions with c = +1 and c = -1 in each axis: no table, so
+// lanes asking for different directions do not serialise on a memory port.
+template <int (*F)(int)>
+__host__ __device__ constexpr uint32_t dir_mask(int v) {
+  uint32_t m = 0;
+  for (int i = 0; i < kQ; ++i)
+    if (F(i) == v) m |= 1u << i;
+  return m;
+}
+template <class C>
+__device__ __forceinline__ C dir_component(uint32_t plus, uint32_t minus, int i) {
+  return C((int)((plus >> i) & 1u) - (int)((minus >> i) & 1u));
+}
+template <class C>
+__device__ __forceinline__ void dir_vec(int i, C& cx, C& cy, C& cz) {
+  cx = dir_component<C>(dir_mask<dir_x>(1), dir_mask<dir_x>(-1), i);
+  cy = dir_component<C>(dir_mask<dir_y>(1), dir_mask<dir_y>(-1), i);
+  cz = dir_component<C>(dir_mask<dir_z>(1), dir_mask<dir_z>(-1), i);
+}
+template <class C>
+__device__ __forceinline__ C dir_weight(int i) {
+  return i == 0 ? C(1.0 / 3.0) : (i <= 6 ? C(1.0 / 18.0) : C(1.0 / 36.0));
 }
 
 // Collision, boundary rule and stores of a boundary site with pre-collision
@@ -777,15 +1099,31 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
       const int i = __ffs(nf) - 1;
       nf &= nf - 1;
       const int j = dir_opp(i);
-      const C cx = dir_tab<C>(0, j), cy = dir_tab<C>(1, j), cz = dir_tab<C>(2, j);
+      C cx, cy, cz;
+      dir_vec<C>(j, cx, cy, cz);
       const C cu = fma_pin(cz, m.uz, fma_pin(cy, m.uy, mul_pin(cx, m.ux)));
       const C ci = fma_pin(cz, uiz, fma_pin(cy, uiy, mul_pin(cx, uix)));
-      const C val = link_value(link_code(i), cu, ci, dir_tab<C>(3, j), gsm[i * kTile + lane],
+      const C val = link_value(link_code(i), cu, ci, dir_weight<C>(j), gsm[i * kTile + lane],
                                gsm[j * kTile + lane]);
       Cd::st(P + j * np + x, j, val);
       chk_count(d.chk, P, P + j * np + x, kQ * np, d.err);
     }
   }
+}
+
+// Sites linked to two or more iolets (each non-fluid link takes its own code
+// from the neighbour table): loads and the per-link boundary rule, out of line
+// so that its registers do not weigh on the common path.
+template <class S, bool ODD>
+__device__ __noinline__ void boundary_slow(const DevLattice& d, const StepParams& p, S* P,
+                                           int64_t x, const int32_t* dsc, bool irr, uint32_t smask,
+                                           uint32_t iom, double Fw, double Kw, double pr0,
+                                           double pr1, double pr2, const int32_t* nbr_s, int lane,
+                                           int64_t slot, typename Codec<S>::C* gsm) {
+  typename Codec<S>::C g[kQ];
+  boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g, d.n, d.err);
+  boundary_update<S, ODD>(d, p, p.omega, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s,
+                          lane, slot, g, gsm);
 }
 
 #ifndef LBM_BULK_MINB
@@ -821,61 +1159,122 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
   bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p.omega, d.err, d.chk);
 }
 
-// Two bulk tiles at launch positions k0, k0 + 1 (whole warp, two sites per
-// lane): lanes 0..15 take tile k0, lanes 16..31 tile k0 + 1 (if any), lane l
-// the sites 2 (l mod 16), 2 (l mod 16) + 1 of its tile; dsc2: the warp's two
-// 20-word descriptor areas.  A site without a partner (the last site of a
-// lattice with an odd site count) takes the single-site update.
-template <class S, bool ODD>
-__device__ __forceinline__ void bulk_tiles2(const DevLattice& d, const StepParams& p, int64_t k0,
-                                            int32_t (*dsc2)[20], int lane) {
-  const bool two = k0 + 1 < d.n_tiles;
-  if (lane < 20) {
-    dsc2[0][lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k0) + lane);
-    if (two) dsc2[1][lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k0 + 1) + lane);
-  }
-  if (p.prefetch > 0 && lane < kQ) {
-    for (int h = 0; h < 2; ++h) {
-      const int64_t kp = k0 + h + p.prefetch;
-      if (kp < d.n_tiles) {
-        const int64_t tp = __ldg(&d.launch[kp].tile);
-        bulk_prefetch_l2(static_cast<const S*>(d.pop) + lane * d.npad + tp * kTile,
-                         kTile * sizeof(S));
-      }
-    }
-  }
-  __syncwarp();
-  const int half = lane >> 4;
-  if (half && !two) return;
-  const int32_t* dsc = dsc2[half];
-  const int64_t x = (int64_t)dsc[19] * kTile + 2 * (lane & 15);
-  if (x >= d.n) return;
-  if constexpr (kChecked && ODD) {
-    bool ok = true;
-    for (int o = 0; o < 18; ++o) ok = chk_site(x + dsc[o], d.n, d.err) && ok;
-    if (x + 1 < d.n)
-      for (int o = 0; o < 18; ++o) ok = chk_site(x + 1 + dsc[o], d.n, d.err) && ok;
-    if (!ok) return;
-  }
-  S* P = static_cast<S*>(d.pop);
-  if (x + 1 < d.n) bulk_update2<S, ODD>(P, d.npad, x, dsc, p.omega, d.err, d.chk);
-  else bulk_update<S, ODD>(P, d.npad, x, dsc, p.omega, d.err, d.chk);
-}
-
 #ifndef LBM_BULK2_MINB
 #define LBM_BULK2_MINB 6
 #endif
-// Bulk tiles, two sites per lane (FP32 and 16-bit storage): warp w of block b
-// takes the bulk tiles at launch positions n_boundary + 2 (b W + w) and the
-// one after it.
-template <class S, bool ODD>
+
+// The fields of a lattice the bulk kernels read (a member of an ensemble is
+// read field by field from its device table, not copied whole).
+struct BulkView {
+  void* pop;
+  const LaunchDesc* launch;
+  int* err;
+  int* chk;
+  int64_t npad, n, n_tiles;
+};
+__device__ __forceinline__ BulkView bulk_view(const DevLattice& d) {
+  return BulkView{d.pop, d.launch, d.err, d.chk, d.npad, d.n, d.n_tiles};
+}
+
+// Two bulk tiles per warp, two sites per lane (FP32 and 16-bit storage): tile
+// A at launch position kA of lattice dA and, when `two`, tile B at launch
+// position kB of lattice dB (the same lattice, or another member of an
+// ensemble); omA, omB their relaxation rates; dsc2: the warp's two 20-word
+// descriptor areas.
+//   VERT = false: lanes 0..15 take tile A, lanes 16..31 tile B, lane l the
+//     z-adjacent sites 2 (l mod 16), 2 (l mod 16) + 1 of its tile (packed words);
+//   VERT = true: lane l takes site l of both tiles (scalar accesses; one
+//     address for both when B directly follows A in the same lattice with the
+//     same offsets).
+// A site without a partner takes the single-site update.
+template <class S, bool ODD, bool VERT>
+__device__ __forceinline__ void bulk_pair_warp(const BulkView& dA, int64_t kA, double omA,
+                                               const BulkView& dB, int64_t kB, double omB,
+                                               bool two, bool one_lattice, int64_t prefetch,
+                                               int32_t (*dsc2)[20], int lane) {
+  if (lane < 20) {
+    dsc2[0][lane] = __ldg(reinterpret_cast<const int32_t*>(dA.launch + kA) + lane);
+    if (two) dsc2[1][lane] = __ldg(reinterpret_cast<const int32_t*>(dB.launch + kB) + lane);
+  }
+  if (prefetch > 0 && lane < kQ) {
+    if (kA + prefetch < dA.n_tiles) {
+      const int64_t tp = __ldg(&dA.launch[kA + prefetch].tile);
+      bulk_prefetch_l2(static_cast<const S*>(dA.pop) + lane * dA.npad + tp * kTile,
+                       kTile * sizeof(S));
+    }
+    if (two && kB + prefetch < dB.n_tiles) {
+      const int64_t tp = __ldg(&dB.launch[kB + prefetch].tile);
+      bulk_prefetch_l2(static_cast<const S*>(dB.pop) + lane * dB.npad + tp * kTile,
+                       kTile * sizeof(S));
+    }
+  }
+  __syncwarp();
+  if constexpr (!VERT) {
+    const int half = lane >> 4;
+    if (half && !two) return;
+    // this half's lattice, field by field (no reference chosen at run time)
+    S* P = static_cast<S*>(half ? dB.pop : dA.pop);
+    const int64_t np = half ? dB.npad : dA.npad, n = half ? dB.n : dA.n;
+    int* err = half ? dB.err : dA.err;
+    int* chk = half ? dB.chk : dA.chk;
+    const int32_t* dsc = dsc2[half];
+    const int64_t x = (int64_t)dsc[19] * kTile + 2 * (lane & 15);
+    if (x >= n) return;
+    if constexpr (kChecked && ODD) {
+      bool ok = true;
+      for (int o = 0; o < 18; ++o) ok = chk_site(x + dsc[o], n, err) && ok;
+      if (x + 1 < n)
+        for (int o = 0; o < 18; ++o) ok = chk_site(x + 1 + dsc[o], n, err) && ok;
+      if (!ok) return;
+    }
+    // a bulk tile is never the ragged last tile (its last site has a +x link
+    // out of the fluid), so x + 1 < n; the guard keeps the update in bounds
+    if (x + 1 < n) bulk_update2<S, ODD>(P, np, x, dsc, half ? omB : omA, err, chk);
+    else bulk_update<S, ODD>(P, np, x, dsc, half ? omB : omA, err, chk);
+  } else {
+    const int32_t* da = dsc2[0];
+    const int64_t xa = (int64_t)da[19] * kTile + lane;
+    S* PA = static_cast<S*>(dA.pop);
+    if (!two) {
+      if (xa < dA.n) bulk_update<S, ODD>(PA, dA.npad, xa, da, omA, dA.err, dA.chk);
+      return;
+    }
+    const int32_t* db = dsc2[1];
+    const int64_t xb = (int64_t)db[19] * kTile + lane;
+    if (!one_lattice || xa >= dA.n || xb >= dA.n) {
+      // the two tiles belong to different members of an ensemble (or a site
+      // has no partner, not reached for bulk tiles): one site at a time
+      S* PB = static_cast<S*>(dB.pop);
+      if (xa < dA.n) bulk_update<S, ODD>(PA, dA.npad, xa, da, omA, dA.err, dA.chk);
+      if (xb < dB.n) bulk_update<S, ODD>(PB, dB.npad, xb, db, omB, dB.err, dB.chk);
+      return;
+    }
+    // B directly follows A with the same offsets (warp-uniform)
+    const bool same = __all_sync(
+        0xFFFFFFFFu, lane < 18 ? da[lane] == db[lane] : (lane == 18 ? db[19] == da[19] + 1 : true));
+    if constexpr (kChecked && ODD) {
+      bool ok = true;
+      for (int o = 0; o < 18; ++o)
+        ok = chk_site(xa + da[o], dA.n, dA.err) && chk_site(xb + db[o], dA.n, dA.err) && ok;
+      if (!ok) return;
+    }
+    if (same) bulk_update2v<S, ODD, true>(PA, dA.npad, xa, xb, da, db, omA, dA.err, dA.chk);
+    else bulk_update2v<S, ODD, false>(PA, dA.npad, xa, xb, da, db, omA, dA.err, dA.chk);
+  }
+}
+
+// Bulk tiles of one lattice, two per warp (warp w of block b: the bulk tiles
+// at launch positions n_boundary + 2 (b W + w) and the one after it).
+template <class S, bool ODD, bool VERT>
 __global__ void __launch_bounds__(kBulkWarps * 32, LBM_BULK2_MINB)
     k_bulk2(const DevLattice d, const StepParams p) {
   __shared__ __align__(16) int32_t desc_s[kBulkWarps][2][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k0 = d.n_boundary + 2 * ((int64_t)blockIdx.x * kBulkWarps + w);
   if (k0 >= d.n_tiles) return;  // warp-uniform
-  bulk_tiles2<S, ODD>(d, p, k0, desc_s[w], lane);
+  const BulkView v = bulk_view(d);
+  bulk_pair_warp<S, ODD, VERT>(v, k0, p.omega, v, k0 + 1, p.omega, k0 + 1 < d.n_tiles, true,
+                               p.prefetch, desc_s[w], lane);
 }
 
 template <class S, bool ODD>
@@ -894,7 +1293,11 @@ __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 16 / kBulkWa
 // Boundary tile at launch position k (whole warp); nbr_s, bar: the warp's
 // staging area (18 rows of per-site neighbours) and mbarrier; dsc: its
 // 20-word descriptor area.
-template <class S, bool ODD>
+// PART selects the sites updated: 0 those whose iolet links (if any) all lead
+// to one iolet (boundary_fast), 1 the sites linked to two or more iolets (the
+// per-link form, run by k_boundary_multi over the tiles that have such sites),
+// 2 both (the persistent kernel).
+template <class S, bool ODD, int PART = 0>
 __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepParams& p, int64_t k,
                                               int32_t* dsc, int32_t* nbr_s, uint64_t* bar,
                                               typename Codec<S>::C* gsm, int lane,
@@ -909,9 +1312,17 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
   const uint32_t tmask = (uint32_t)dsc[18];
   const bool irr = tmask & kIrregular;
   const int64_t x = (int64_t)dsc[19] * kTile + lane;
-  // odd steps of an irregular tile: stage the per-site neighbour rows
-  // (cp.async.bulk into shared memory, completing on the warp's mbarrier)
-  const bool stage = ODD && irr;
+  // odd steps of an irregular tile: its segment table (80 words, coalesced
+  // loads into the staging area) when its lanes form at most kMaxSegments
+  // runs of shared offsets, else its per-site neighbour rows (cp.async.bulk
+  // into shared memory, completing on the warp's mbarrier); the per-link form
+  // of multi-iolet sites (PART 1, 2) always reads the per-site rows
+  const bool seg = ODD && irr && (tmask & kSegmented) && PART == 0;
+  const bool stage = ODD && irr && !seg;
+  if (seg) {
+    const int32_t* src = d.seg_tab + k * kSegWords;
+    for (int q = lane; q < kSegWords; q += kTile) nbr_s[q] = __ldg(src + q);
+  }
   // bar_phase: a warp that stages repeatedly (persistent kernel) keeps one
   // initialised mbarrier and tracks its phase; otherwise it is set up here.
   if (stage) {
@@ -924,20 +1335,27 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
     }
   }
   const bool valid = smask & kValid;
-  double Fw = 0.0, Kw = 0.0, pr0 = 0.0, pr1 = 0.0, pr2 = 0.0;
+  // per-site wall and inlet data (F, kappa/3, inlet profile p0, ps, pc) into
+  // the warp's area (from row kAreaSite), copied asynchronously so that no register
+  // holds them while the populations load
+  double* site = reinterpret_cast<double*>(gsm + kAreaSite * kTile);  // [5][32]
   if (valid && (smask & kHasWall)) {
-    Fw = __ldg(d.slot_F + slot);
-    Kw = __ldg(d.slot_kappa + slot);  // kappa / 3
+    cp_async8(site + lane, d.slot_F + slot);
+    cp_async8(site + kTile + lane, d.slot_kappa + slot);
   }
   if (valid && (smask & kHasInlet)) {
-    pr0 = __ldg(d.slot_prof + slot);
-    pr1 = __ldg(d.slot_prof + d.slot_stride + slot);
-    pr2 = __ldg(d.slot_prof + 2 * d.slot_stride + slot);
+    cp_async8(site + 2 * kTile + lane, d.slot_prof + slot);
+    cp_async8(site + 3 * kTile + lane, d.slot_prof + d.slot_stride + slot);
+    cp_async8(site + 4 * kTile + lane, d.slot_prof + 2 * d.slot_stride + slot);
   }
-  C g[kQ];
+  cp_async_commit();
+  // warp-uniform: which boundary states the tile needs at all
+  const bool warp_io = __any_sync(0xFFFFFFFFu, valid && (iom & kDirBits));
+  const bool warp_wall = p.elastic && __any_sync(0xFFFFFFFFu, valid && (smask & kHasWall));
+  const uint32_t warp_nf = __reduce_or_sync(0xFFFFFFFFu, valid ? (smask & kDirBits) : 0u);
+  // sites linked to two or more iolets take the per-link form
+  const bool multi = smask & kMultiIolet;
   S* P = static_cast<S*>(d.pop);
-  if (!stage && valid)
-    boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g, d.n, d.err);
   if (stage) {
     const uint32_t ph = bar_phase ? *bar_phase : 0u;
     // one decision for the whole warp (lanes could see the limit and the
@@ -952,12 +1370,46 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
       return false;
     }
     if (bar_phase) *bar_phase = ph ^ 1u;
-    if (valid)
-      boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, true, nbr_s, lane, g, d.n, d.err);
   }
+  if (seg) __syncwarp();  // the segment table is in shared memory
   if (!valid) return true;
-  boundary_update<S, ODD>(d, p, p.omega, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s,
-                          lane, slot, g, gsm);
+  if (!multi) {
+    if constexpr (PART != 1) {
+      // this lane's offsets: the tile's (coherent tiles), its segment's, or
+      // its column of the staged per-site rows turned into offsets (the rows
+      // of links leaving the fluid are left as they are and never used)
+      const int32_t* offp = dsc;
+      int ostride = 1;
+      if (seg) {
+        const int q = (lane >= nbr_s[1]) + (lane >= nbr_s[2]) + (lane >= nbr_s[3]);
+        offp = nbr_s + kMaxSegments + 18 * q;
+      } else if (stage) {
+        const uint32_t nfl = smask & kDirBits;
+        for (int i = 1; i < kQ; ++i)
+          if (!((nfl >> i) & 1u)) nbr_s[(i - 1) * kTile + lane] -= (int32_t)x;
+        offp = nbr_s + lane;
+        ostride = kTile;
+      }
+      boundary_fast<S, ODD>(d, p, p.omega, P, x, offp, ostride, smask, iom, site, nbr_s, lane,
+                            slot, warp_io, warp_wall, warp_nf, gsm);
+    }
+    return true;
+  }
+  if constexpr (PART == 0) return true;
+  cp_async_wait_all();
+  const double Fw = site[lane], Kw = site[kTile + lane];
+  const double pr0 = site[2 * kTile + lane], pr1 = site[3 * kTile + lane];
+  const double pr2 = site[4 * kTile + lane];
+  if constexpr (PART == 1) {
+    using C = typename Codec<S>::C;
+    C g[kQ];
+    boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g, d.n, d.err);
+    boundary_update<S, ODD>(d, p, p.omega, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2,
+                            nbr_s, lane, slot, g, gsm);
+  } else {
+    boundary_slow<S, ODD>(d, p, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s, lane,
+                          slot, gsm);
+  }
   return true;
 }
 
@@ -966,7 +1418,7 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
     k_boundary(const DevLattice d, const StepParams p) {
   using C = typename Codec<S>::C;
   __shared__ __align__(128) int32_t stage[kBoundaryWarps][18 * kTile];
-  __shared__ __align__(16) C gs[kBoundaryWarps][kQ * kTile];
+  __shared__ __align__(16) C gs[kBoundaryWarps][BoundaryArea<C>::size];
   __shared__ __align__(16) int32_t desc_s[kBoundaryWarps][20];
   __shared__ uint64_t bars[kBoundaryWarps];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -975,18 +1427,32 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
   boundary_tile<S, ODD>(d, p, k, desc_s[w], stage[w], &bars[w], gs[w], lane);
 }
 
-// -------------------------------------------------------------- ensembles
-// One launch of each step kernel covers every member of an ensemble: global
-// tile g belongs to the member m with prefix[m] <= g < prefix[m + 1].
+// The sites linked to two or more iolets, over the boundary tiles that have
+// such sites (d.multi_tiles); every other site of those tiles is left to
+// k_boundary.
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBoundaryWarps * 32)
+    k_boundary_multi(const DevLattice d, const StepParams p) {
+  using C = typename Codec<S>::C;
+  __shared__ __align__(128) int32_t stage[kBoundaryWarps][18 * kTile];
+  __shared__ __align__(16) C gs[kBoundaryWarps][BoundaryArea<C>::size];
+  __shared__ __align__(16) int32_t desc_s[kBoundaryWarps][20];
+  __shared__ uint64_t bars[kBoundaryWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * kBoundaryWarps + w;
+  if (q >= d.n_multi) return;  // warp-uniform
+  boundary_tile<S, ODD, 1>(d, p, __ldg(d.multi_tiles + q), desc_s[w], stage[w], &bars[w], gs[w],
+                           lane);
+}
 
-__device__ __forceinline__ int find_member(const int64_t* prefix, int32_t nm, int64_t g) {
-  int lo = 0, hi = nm;  // prefix[lo] <= g < prefix[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(prefix + mid) <= g) lo = mid;
-    else hi = mid;
-  }
-  return lo;
+// -------------------------------------------------------------- ensembles
+// One launch of each step kernel covers every member of an ensemble: the
+// tile map names the member and launch position of each global tile (one
+// 8-byte load, no search).
+
+__device__ __forceinline__ TileRef tile_ref(const TileRef* map, int64_t g) {
+  const long long v = __ldg(reinterpret_cast<const long long*>(map + g));
+  return TileRef{(int32_t)(v & 0xFFFFFFFFll), (int32_t)(v >> 32)};
 }
 
 template <class S, bool ODD>
@@ -996,11 +1462,41 @@ __global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 16 / kBulkWa
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t g = (int64_t)blockIdx.x * kBulkWarps + w;
   if (g >= e.n_bulk_tiles) return;  // warp-uniform
-  const int m = find_member(e.bulk_prefix, e.n_members, g);
-  const MemberDev& md = e.mem[m];
+  const TileRef t = tile_ref(e.bulk_map, g);
+  const MemberDev& md = e.mem[t.member];
   StepParams pm = p;
   pm.omega = md.omega;
-  bulk_tile<S, ODD>(md.d, pm, md.d.n_boundary + (g - __ldg(e.bulk_prefix + m)), desc_s[w], lane);
+  bulk_tile<S, ODD>(md.d, pm, t.k, desc_s[w], lane);
+}
+
+__device__ __forceinline__ BulkView member_view(const MemberDev* m) {
+  const DevLattice* d = &m->d;
+  BulkView v;
+  v.pop = (void*)__ldg(reinterpret_cast<const unsigned long long*>(&d->pop));
+  v.launch = reinterpret_cast<const LaunchDesc*>(
+      __ldg(reinterpret_cast<const unsigned long long*>(&d->launch)));
+  v.err = (int*)__ldg(reinterpret_cast<const unsigned long long*>(&d->err));
+  v.chk = (int*)__ldg(reinterpret_cast<const unsigned long long*>(&d->chk));
+  v.npad = __ldg(&d->npad);
+  v.n = __ldg(&d->n);
+  v.n_tiles = __ldg(&d->n_tiles);
+  return v;
+}
+
+// Bulk tiles of all members, two per warp (the pair may span two members).
+template <class S, bool ODD, bool VERT>
+__global__ void __launch_bounds__(kBulkWarps * 32, LBM_BULK2_MINB)
+    k_bulk2_ens(const EnsembleLaunch e, const StepParams p) {
+  __shared__ __align__(16) int32_t desc_s[kBulkWarps][2][20];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g0 = 2 * ((int64_t)blockIdx.x * kBulkWarps + w);
+  if (g0 >= e.n_bulk_tiles) return;  // warp-uniform
+  const bool two = g0 + 1 < e.n_bulk_tiles;
+  const TileRef ta = tile_ref(e.bulk_map, g0), tb = two ? tile_ref(e.bulk_map, g0 + 1) : ta;
+  const BulkView A = member_view(e.mem + ta.member), B = member_view(e.mem + tb.member);
+  bulk_pair_warp<S, ODD, VERT>(A, ta.k, __ldg(&e.mem[ta.member].omega), B, tb.k,
+                               __ldg(&e.mem[tb.member].omega), two, ta.member == tb.member,
+                               p.prefetch, desc_s[w], lane);
 }
 
 template <class S, bool ODD>
@@ -1008,20 +1504,19 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
     k_boundary_ens(const EnsembleLaunch e, const StepParams p) {
   using C = typename Codec<S>::C;
   __shared__ __align__(128) int32_t stage[kBoundaryWarps][18 * kTile];
-  __shared__ __align__(16) C gs[kBoundaryWarps][kQ * kTile];
+  __shared__ __align__(16) C gs[kBoundaryWarps][BoundaryArea<C>::size];
   __shared__ __align__(16) int32_t desc_s[kBoundaryWarps][20];
   __shared__ uint64_t bars[kBoundaryWarps];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t g = (int64_t)blockIdx.x * kBoundaryWarps + w;
   if (g >= e.n_boundary_tiles) return;  // warp-uniform
-  const int m = find_member(e.boundary_prefix, e.n_members, g);
-  const MemberDev& md = e.mem[m];
+  const TileRef t = tile_ref(e.boundary_map, g);
+  const MemberDev& md = e.mem[t.member];
   StepParams pm = p;
   pm.omega = md.omega;
   pm.rho0 = md.rho0;
   pm.elastic = md.elastic;
-  boundary_tile<S, ODD>(md.d, pm, g - __ldg(e.boundary_prefix + m), desc_s[w], stage[w], &bars[w],
-                        gs[w], lane);
+  boundary_tile<S, ODD>(md.d, pm, t.k, desc_s[w], stage[w], &bars[w], gs[w], lane);
 }
 
 // ------------------------------------------------- persistent ensemble kernel
@@ -1077,7 +1572,7 @@ __device__ __noinline__ bool persist_boundary(const DevLattice& d, const StepPar
                                               int32_t* dsc, int32_t* nbr_s, uint64_t* bar,
                                               typename Codec<S>::C* gsm, int lane,
                                               uint32_t* phase) {
-  return boundary_tile<S, ODD>(d, p, k, dsc, nbr_s, bar, gsm, lane, phase);
+  return boundary_tile<S, ODD, 2>(d, p, k, dsc, nbr_s, bar, gsm, lane, phase);
 }
 template <class S, bool ODD>
 __device__ __noinline__ void persist_bulk(const DevLattice& d, const StepParams& p, int64_t k,
@@ -1091,7 +1586,7 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
                           GridSync* gs, unsigned expected, int chunk) {
   using C = typename Codec<S>::C;
   __shared__ __align__(128) int32_t stage[kPersistWarps][18 * kTile];
-  __shared__ __align__(16) C gsm[kPersistWarps][kQ * kTile];
+  __shared__ __align__(16) C gsm[kPersistWarps][BoundaryArea<C>::size];
   __shared__ __align__(16) int32_t desc_s[kPersistWarps][20];
   __shared__ uint64_t bars[kPersistWarps];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1120,13 +1615,13 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
       const int64_t t1 = (int64_t)t0 + chunk < total ? (int64_t)t0 + chunk : total;
       for (int64_t t = (int64_t)t0; t < t1; ++t) {
         if (t < e.n_boundary_tiles) {
-          const int m = find_member(e.boundary_prefix, e.n_members, t);
-          const MemberDev& md = e.mem[m];
+          const TileRef tr = tile_ref(e.boundary_map, t);
+          const MemberDev& md = e.mem[tr.member];
           StepParams pm = q;
           pm.omega = md.omega;
           pm.rho0 = md.rho0;
           pm.elastic = md.elastic;
-          const int64_t k = t - __ldg(e.boundary_prefix + m);
+          const int64_t k = tr.k;
           const bool ok = odd ? persist_boundary<S, true>(md.d, pm, k, desc_s[w], stage[w],
                                                           &bars[w], gsm[w], lane, &phase)
                               : persist_boundary<S, false>(md.d, pm, k, desc_s[w], stage[w],
@@ -1137,12 +1632,11 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
             break;
           }
         } else {
-          const int64_t tb = t - e.n_boundary_tiles;
-          const int m = find_member(e.bulk_prefix, e.n_members, tb);
-          const MemberDev& md = e.mem[m];
+          const TileRef tr = tile_ref(e.bulk_map, t - e.n_boundary_tiles);
+          const MemberDev& md = e.mem[tr.member];
           StepParams pm = q;
           pm.omega = md.omega;
-          const int64_t k = md.d.n_boundary + (tb - __ldg(e.bulk_prefix + m));
+          const int64_t k = tr.k;
           if (odd) persist_bulk<S, true>(md.d, pm, k, desc_s[w], lane);
           else persist_bulk<S, false>(md.d, pm, k, desc_s[w], lane);
         }
@@ -1411,6 +1905,27 @@ __global__ void k_wss(const DevLattice d, int odd, double tau, const int64_t* si
 
 // ------------------------------------------------------------- dispatch
 
+// The multi-iolet sites of one lattice (nothing when it has none).
+template <class S>
+void launch_multi(const DevLattice& d, const StepParams& p, bool odd, cudaStream_t s) {
+  if (d.n_multi <= 0) return;
+  const unsigned nb = (unsigned)((d.n_multi + kBoundaryWarps - 1) / kBoundaryWarps);
+  if (odd) k_boundary_multi<S, true><<<nb, kBoundaryWarps * 32, 0, s>>>(d, p);
+  else k_boundary_multi<S, false><<<nb, kBoundaryWarps * 32, 0, s>>>(d, p);
+}
+
+// Pairing of the bulk kernel's two sites per lane for this step's parity
+// (LBM_TUNE_BULK_SITES): 0 one site per lane, 1 z-adjacent sites of one tile
+// (packed words), 2 the same lane of two tiles (scalar, aligned).
+inline int bulk_pairing(int32_t bulk_sites, bool odd) {
+  switch (bulk_sites) {
+    case 2: return odd ? 2 : 1;
+    case 3: return 1;
+    case 4: return 2;
+  }
+  return 0;
+}
+
 // One step: k_boundary on the side stream, k_bulk on the main stream, joined
 // on the main stream.  ev (profiling): before the fork, after k_bulk, after
 // the join, all on the main stream.
@@ -1428,15 +1943,20 @@ int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void
     cudaStreamWaitEvent(side, (cudaEvent_t)ss.fork, 0);
     if (odd) k_boundary<S, true><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
     else k_boundary<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
+    launch_multi<S>(d, p, odd, side);
   }
   if (nbulk) {
-    bool pairs = false;
-    if constexpr (sizeof(S) < 8) pairs = p.bulk_sites == 2;
-    if (pairs) {
+    const int pairing = sizeof(S) < 8 ? bulk_pairing(p.bulk_sites, odd) : 0;
+    if (pairing) {
       const unsigned nb2 = (unsigned)((nbulk_tiles + 2 * kBulkWarps - 1) / (2 * kBulkWarps));
       if constexpr (sizeof(S) < 8) {
-        if (odd) k_bulk2<S, true><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
-        else k_bulk2<S, false><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
+        if (pairing == 1) {
+          if (odd) k_bulk2<S, true, false><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
+          else k_bulk2<S, false, false><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
+        } else {
+          if (odd) k_bulk2<S, true, true><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
+          else k_bulk2<S, false, true><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
+        }
       }
     } else {
       if (odd) k_bulk<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
@@ -1496,8 +2016,28 @@ int ensemble_step_t(const EnsembleLaunch& e, const StepParams& p, const StepStre
     cudaStreamWaitEvent(side, (cudaEvent_t)ss.fork, 0);
     if (odd) k_boundary_ens<S, true><<<nbnd, kBoundaryWarps * 32, 0, side>>>(e, p);
     else k_boundary_ens<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(e, p);
+    for (int32_t q = 0; q < e.n_multi_members; ++q) {
+      const MemberDev& md = e.multi_host[q];
+      StepParams pm = p;
+      pm.omega = md.omega;
+      pm.rho0 = md.rho0;
+      pm.elastic = md.elastic;
+      launch_multi<S>(md.d, pm, odd, side);
+    }
   }
-  if (nbulk) {
+  const int pairing = sizeof(S) < 8 ? bulk_pairing(p.bulk_sites, odd) : 0;
+  if (nbulk && pairing) {
+    const unsigned nb2 = (unsigned)((e.n_bulk_tiles + 2 * kBulkWarps - 1) / (2 * kBulkWarps));
+    if constexpr (sizeof(S) < 8) {
+      if (pairing == 1) {
+        if (odd) k_bulk2_ens<S, true, false><<<nb2, kBulkWarps * 32, 0, m>>>(e, p);
+        else k_bulk2_ens<S, false, false><<<nb2, kBulkWarps * 32, 0, m>>>(e, p);
+      } else {
+        if (odd) k_bulk2_ens<S, true, true><<<nb2, kBulkWarps * 32, 0, m>>>(e, p);
+        else k_bulk2_ens<S, false, true><<<nb2, kBulkWarps * 32, 0, m>>>(e, p);
+      }
+    }
+  } else if (nbulk) {
     if (odd) k_bulk_ens<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(e, p);
     else k_bulk_ens<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(e, p);
   }

@@ -434,6 +434,58 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     }
   }
   });
+  // segment tables of irregular tiles: split the lanes greedily into runs
+  // that share one offset per direction (links leaving the fluid constrain
+  // nothing); tiles that need at most kMaxSegments runs are marked kSegmented
+  L.seg_tab.assign((size_t)nb_tiles * kSegWords, 0);
+  parallel_for(T, [&](int64_t t0, int64_t t1, int) {
+    for (int64_t t = t0; t < t1; ++t) {
+      TileDesc& td = L.tiles[t];
+      if (td.slot < 0 || !(td.mask & kIrregular)) continue;
+      const int64_t x0 = t * kTile;
+      const int lanes = (int)std::min<int64_t>(kTile, n - x0);
+      int32_t* st = &L.seg_tab[(size_t)(td.slot / kTile) * kSegWords];
+      int32_t off[18];
+      bool have[18];
+      int nseg = 0;
+      bool ok = true;
+      for (int l = 0; l < lanes && ok; ++l) {
+        const int32_t* nb = &L.nbr[(size_t)18 * (x0 + l)];
+        bool fits = nseg > 0;
+        for (int i = 0; i < 18 && fits; ++i)
+          if (nb[i] >= 0 && have[i] && nb[i] - (int32_t)(x0 + l) != off[i]) fits = false;
+        if (!fits) {  // start a segment at lane l
+          if (nseg == kMaxSegments) {
+            ok = false;
+            break;
+          }
+          st[nseg++] = l;
+          for (int i = 0; i < 18; ++i) have[i] = false;
+        }
+        for (int i = 0; i < 18; ++i)
+          if (nb[i] >= 0 && !have[i]) {
+            have[i] = true;
+            off[i] = nb[i] - (int32_t)(x0 + l);
+          }
+        for (int i = 0; i < 18; ++i) st[4 + 18 * (nseg - 1) + i] = have[i] ? off[i] : 0;
+      }
+      if (!ok) {
+        std::fill(st, st + kSegWords, 0);
+        continue;
+      }
+      for (int q = nseg; q < kMaxSegments; ++q) st[q] = kTile;
+      td.mask |= kSegmented;
+    }
+  });
+  for (LaunchDesc& e : L.launch)
+    if (e.mask & kIrregular) e.mask = L.tiles[e.tile].mask;
+  L.multi_tiles.clear();
+  for (int64_t b = 0; b < nb_tiles; ++b)
+    for (int l = 0; l < kTile; ++l)
+      if (L.slot_mask[b * kTile + l] & kMultiIolet) {
+        L.multi_tiles.push_back((int32_t)b);  // boundary tiles lead the launch order
+        break;
+      }
   L.wall_slot.resize(L.wall_sites.size());
   parallel_for((int64_t)L.wall_sites.size(), [&](int64_t w0, int64_t w1, int) {
     for (int64_t w = w0; w < w1; ++w) L.wall_slot[w] = slot_of[L.wall_sites[w]];

@@ -32,6 +32,15 @@ constexpr int kMaxIolets = 4095;
 constexpr uint32_t kHasInlet = 1u << 29;   // a velocity-inlet link is present
 constexpr uint32_t kHasWall = 1u << 30;    // a wall link is present
 constexpr uint32_t kIrregular = 1u << 31;  // tile: fluid-link offsets differ between lanes
+// Irregular tile whose lanes fall into at most kMaxSegments runs of consecutive
+// lanes that each share one offset per direction (tile masks only); its
+// segment table replaces the per-site neighbour rows on odd steps.
+constexpr uint32_t kSegmented = 1u << 20;
+constexpr int kMaxSegments = 4;
+// Segment table of a boundary tile, in 32-bit words: [0..3] first lane of
+// each segment (32 for an unused one), then [4 + 18 q + (i - 1)] the offset
+// nbr(x, i) - x of segment q's fluid links in direction i; padded to 80.
+constexpr int kSegWords = 80;
 
 // Sticky device error bits (ctx->err).
 constexpr int kErrUnstable = 1;
@@ -120,6 +129,9 @@ struct HostLattice {
   big_vector<int32_t> slot_nbr;      // [18][n_slots] absolute neighbour or non-fluid code
   std::vector<double> slot_prof;     // [3][n_slots] inlet shape p0, ps, pc
   std::vector<int64_t> wall_slot;    // [n_wall_sites] slot of each wall site
+  std::vector<int32_t> seg_tab;      // [n_boundary tiles][kSegWords] segment tables
+  std::vector<int32_t> multi_tiles;  // launch positions of boundary tiles with a site
+                                     // linked to two or more iolets
   // iolet site lists (sites with a link into iolet k), CSR
   std::vector<int64_t> iolet_off;    // [n_iolets + 1]
   std::vector<int64_t> iolet_sites;
@@ -153,6 +165,9 @@ struct DevLattice {
   int* err = nullptr;
   int64_t n_boundary = 0;  // boundary tiles = leading entries of the launch order
   int* chk = nullptr;      // checked builds: stores per population slot this step, [19][npad]
+  const int32_t* seg_tab = nullptr;      // [n_boundary][kSegWords] (segmented irregular tiles)
+  const int32_t* multi_tiles = nullptr;  // boundary tiles with multi-iolet sites
+  int64_t n_multi = 0;
 };
 
 struct StepParams {
@@ -192,14 +207,23 @@ struct StepStreams {
 int launch_step(int storage, const DevLattice& d, const StepParams& p, const StepStreams& ss,
                 void* const* events);
 
+// A tile of an ensemble: its member and its launch position in that member.
+struct TileRef {
+  int32_t member;
+  int32_t k;
+};
+
 // Ensemble launch: the members' bulk (boundary) tiles are numbered in
-// schedule order; prefix[m] is the number of tiles of members before m.
+// schedule order; bulk_map[g] (boundary_map[g]) names the member and launch
+// position of global bulk (boundary) tile g.
 struct EnsembleLaunch {
   const MemberDev* mem;
-  const int64_t* bulk_prefix;      // [n_members + 1]
-  const int64_t* boundary_prefix;  // [n_members + 1]
+  const TileRef* bulk_map;      // [n_bulk_tiles]
+  const TileRef* boundary_map;  // [n_boundary_tiles]
   int32_t n_members;
   int64_t n_bulk_tiles, n_boundary_tiles;
+  const MemberDev* multi_host;  // host copies of the members with multi-iolet tiles
+  int32_t n_multi_members;
 };
 int launch_ensemble_step(int storage, const EnsembleLaunch& e, const StepParams& p,
                          const StepStreams& ss);

@@ -228,11 +228,46 @@ class Lattice:
 
     def tune(self, prefetch=None, bulk_sites=None):
         """Launch knobs (``lbm_tune``): L2 prefetch distance of the bulk kernel in
-        tiles, and sites per lane of the bulk kernel (1 or 2)."""
+        tiles, and the bulk kernel's sites per lane and their pairing (1 to 4)."""
         if prefetch is not None:
             self._check(self._lib.lbm_tune(self.h, A.LBM_TUNE_PREFETCH, int(prefetch)))
         if bulk_sites is not None:
             self._check(self._lib.lbm_tune(self.h, A.LBM_TUNE_BULK_SITES, int(bulk_sites)))
+
+    def time_steps(self, n):
+        """Device ms of n steps (CUDA events on the lattice's stream)."""
+        import torch
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        self.sync()
+        e0.record(self.stream)
+        self.step(n)
+        e1.record(self.stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def autotune(self, bulk_sites=(1, 2, 3, 4), prefetch=(0, 2048, 4096), trial_steps=40):
+        """Choose the bulk kernel's site tile (one site per lane, a 32-site tile per
+        warp; or two per lane, 64 sites per warp, paired as adjacent sites or as
+        two tiles) and its L2 prefetch distance by timing each candidate on this
+        lattice (coordinate search).  Every trial advances the lattice by
+        ``trial_steps`` steps (an even number keeps both parities equal)."""
+        if self.storage == "f64":
+            bulk_sites = (1,)
+        best = dict(bulk_sites=bulk_sites[0], prefetch=prefetch[0])
+        results = []
+        for knob, cands in (("bulk_sites", bulk_sites), ("prefetch", prefetch)):
+            times = {}
+            for v in cands:
+                cfg = dict(best)
+                cfg[knob] = v
+                self.tune(**cfg)
+                self.time_steps(trial_steps)
+                times[v] = self.time_steps(trial_steps)
+                results.append((dict(cfg), times[v]))
+            best[knob] = min(times, key=times.get)
+        self.tune(**best)
+        return best, results
 
     def profile_read(self):
         """Since profile(True): ((step ms, bulk-kernel ms), (bulk launches, boundary launches))."""
@@ -266,7 +301,8 @@ class Ensemble:
         self.h = h
         self.stream = self.members[0].stream  # the ensemble's work is ordered with it
         self.n = sum(m.n for m in self.members)
-        self.settings = {"prefetch": None, "schedule": 0, "graph_steps": 0, "persistent": 0}
+        self.settings = {"prefetch": None, "schedule": 0, "graph_steps": 0, "persistent": 0,
+                         "bulk_sites": None}
 
     def _check(self, rc):
         if rc != A.LBM_OK:
@@ -279,7 +315,7 @@ class Ensemble:
         self._check(self._lib.lbm_ensemble_sync(self.h))
 
     def tune(self, prefetch=None, schedule=None, graph_steps=None, persistent=None,
-             barrier_extra=None):
+             barrier_extra=None, bulk_sites=None):
         if prefetch is not None:
             self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_PREFETCH, int(prefetch)))
             self.settings["prefetch"] = int(prefetch)
@@ -297,6 +333,10 @@ class Ensemble:
         if barrier_extra is not None:
             self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_BARRIER_EXTRA,
                                                     int(barrier_extra)))
+        if bulk_sites is not None:
+            self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_BULK_SITES,
+                                                    int(bulk_sites)))
+            self.settings["bulk_sites"] = int(bulk_sites)
 
     def time_steps(self, n):
         """Device ms of n steps (CUDA events on the ensemble's stream)."""
@@ -311,15 +351,22 @@ class Ensemble:
         return e0.elapsed_time(e1)
 
     def autotune(self, prefetch=(0, 1024, 2048, 4096, 8192), schedule=(0, 1),
-                 graph_steps=(0, 20), persistent=(0, 1), trial_steps=40):
+                 graph_steps=(0, 20), persistent=(0, 1), bulk_sites=(1, 2, 3, 4),
+                 trial_steps=40):
         """Choose the schedule knobs by timing each candidate on this ensemble
-        (coordinate search, one knob at a time).  Every trial advances the
-        members by ``trial_steps`` steps."""
+        (coordinate search, one knob at a time): member order, the bulk kernel's
+        site tile (one site per lane, 32 sites per warp; or two per lane, 64 per
+        warp, paired as adjacent sites or as two tiles), its L2 prefetch distance,
+        graph replay and the persistent kernel.  Every trial advances the members
+        by ``trial_steps`` steps."""
         results = []
+        if self.members[0].storage == "f64":
+            bulk_sites = (1,)
         best = dict(prefetch=prefetch[0], schedule=schedule[0], graph_steps=graph_steps[0],
-                    persistent=persistent[0])
-        for knob, cands in (("schedule", schedule), ("prefetch", prefetch),
-                            ("graph_steps", graph_steps), ("persistent", persistent)):
+                    persistent=persistent[0], bulk_sites=bulk_sites[0])
+        for knob, cands in (("schedule", schedule), ("bulk_sites", bulk_sites),
+                            ("prefetch", prefetch), ("graph_steps", graph_steps),
+                            ("persistent", persistent)):
             times = {}
             for v in cands:
                 cfg = dict(best)

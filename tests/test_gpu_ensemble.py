@@ -65,6 +65,33 @@ def test_ensemble_equals_members_alone(storage, graph_steps, persistent):
     ens.close()
 
 
+@pytest.mark.parametrize("bulk_sites", [2, 3, 4])
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_ensemble_bulk_pairing_equals_members_alone(storage, bulk_sites):
+    """The two-sites-per-lane bulk kernels in an ensemble (a warp's two tiles may
+    belong to two members) against the same members stepped alone with the same
+    kernels, on tubes large enough to have bulk tiles."""
+    from paper_2108_08783_gb300 import Ensemble
+    members = _members(n=6, seed=3, scale=0.5)
+    alone = _lattices(members, storage)
+    batch = _lattices(members, storage)
+    assert sum(int(l.info()[4]) for l in batch) > 50  # bulk tiles
+    for lat in alone:
+        lat.tune(bulk_sites=bulk_sites)
+    ens = Ensemble(batch)
+    ens.tune(bulk_sites=bulk_sites, schedule=1)
+    for chunk in (5, 10, 9):
+        ens.step(chunk)
+        for lat in alone:
+            lat.step(chunk)
+        ens.sync()
+        for a, b in zip(alone, batch):
+            a.sync()
+            np.testing.assert_allclose(b.populations(), a.populations(), rtol=0,
+                                       atol=ATOL[storage])
+    ens.close()
+
+
 def test_ensemble_members_match_oracle():
     from oracle import Oracle
     from paper_2108_08783_gb300 import Ensemble
