@@ -278,7 +278,10 @@ int lbm_wss(lbm_ctx *ctx, const int64_t *sites, const double *normals, int64_t m
  *                        second tile follows the first with the same offsets):
  *                        2 = adjacent sites on even steps, two tiles on odd
  *                        steps; 3 = adjacent sites on both; 4 = two tiles on
- *                        both.
+ *                        both.  Default: 2 (lattices) and 3 (ensembles) for
+ *                        16-bit storage, 1 otherwise;
+ *   LBM_TUNE_BULK_WARPS  warps (tiles, or tile pairs) per CTA of the bulk
+ *                        kernel: 4 (default) or 8, the same warps per SM.
  * Before using a member's own calls (moments, wall state, ...) call
  * lbm_ensemble_sync.  Errors: LBM_EINVAL (bad arguments, mixed storage or
  * steps), LBM_ESTATE (members drifted apart), LBM_ENOMEM, LBM_ECUDA; the
@@ -290,7 +293,8 @@ enum {
   LBM_TUNE_GRAPH_STEPS = 2,
   LBM_TUNE_PERSISTENT = 3,
   LBM_TUNE_BARRIER_EXTRA = 4,
-  LBM_TUNE_BULK_SITES = 5
+  LBM_TUNE_BULK_SITES = 5,
+  LBM_TUNE_BULK_WARPS = 6
 };
 int lbm_ensemble_create(lbm_ctx *const *members, int32_t n, lbm_ensemble **out);
 int lbm_ensemble_step(lbm_ensemble *ens, int64_t n_steps);
@@ -316,8 +320,9 @@ int lbm_fmap(const double *alpha, int64_t n_alpha, const double *dr_over_R, int6
 
 /* lbm_tune - launch knobs of one lattice (no effect on results beyond the
  * rounding of the collision arithmetic): LBM_TUNE_PREFETCH (L2 prefetch
- * distance of the bulk kernel, tiles, >= 0) and LBM_TUNE_BULK_SITES (1 to 4:
- * one or two sites per lane of the bulk kernel and their pairing), as for
+ * distance of the bulk kernel, tiles, >= 0), LBM_TUNE_BULK_SITES (1 to 4:
+ * one or two sites per lane of the bulk kernel and their pairing) and
+ * LBM_TUNE_BULK_WARPS (4 or 8 warps per CTA of the bulk kernel), as for
  * lbm_ensemble_tune.  Defaults are
  * chosen per storage at build time.  LBM_EINVAL for another knob or value. */
 int lbm_tune(lbm_ctx *ctx, int32_t knob, int64_t value);

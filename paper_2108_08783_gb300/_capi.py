@@ -34,7 +34,7 @@ EXPORTS = (
     "lbm_mlp_last_error", "lbm_mlp_destroy", "lbm_warm_features", "lbm_warm_start",
 )
 LBM_TUNE_PREFETCH, LBM_TUNE_SCHEDULE, LBM_TUNE_GRAPH_STEPS = 0, 1, 2
-LBM_TUNE_PERSISTENT, LBM_TUNE_BARRIER_EXTRA, LBM_TUNE_BULK_SITES = 3, 4, 5
+LBM_TUNE_PERSISTENT, LBM_TUNE_BARRIER_EXTRA, LBM_TUNE_BULK_SITES, LBM_TUNE_BULK_WARPS = 3, 4, 5, 6
 
 
 class LbmIolet(C.Structure):

@@ -21,14 +21,19 @@
 // GB300: FP32 gains from prefetching 4096 tiles ahead; the 16-bit storages are
 // issue-bound and lose more to the prefetch instructions than they gain; FP64
 // is ALU-bound either way.  -DLBM_DEFAULT_PREFETCH=n overrides.
-// Sites per lane of the bulk kernel by storage.  -DLBM_DEFAULT_BULK_SITES=n
-// overrides.
-inline int32_t default_bulk_sites(int storage) {
+// Bulk kernel mode (LBM_TUNE_BULK_SITES) by storage, measured on GB300: the
+// 16-bit storages gain from two sites per lane (single lattices: adjacent
+// sites on even steps, two tiles on odd steps, +11-15 % on the long tube and
+// +4 % on the tree; ensembles: adjacent sites on both, +6 %); FP32 is
+// DRAM-bound with one site per lane and loses 3-6 % with two; FP64 has one
+// form only.  -DLBM_DEFAULT_BULK_SITES=n overrides.
+inline int32_t default_bulk_sites(int storage, bool ensemble = false) {
 #ifdef LBM_DEFAULT_BULK_SITES
   (void)storage;
+  (void)ensemble;
   return LBM_DEFAULT_BULK_SITES;
 #else
-  (void)storage;
+  if (storage == LBM_F16S || storage == LBM_BF16S) return ensemble ? 3 : 2;
   return 1;
 #endif
 }
@@ -65,7 +70,8 @@ struct lbm_ctx {
   double* red_out = nullptr;
   std::string err;
   int64_t prefetch = 0;  // L2 prefetch distance (tiles), set from the storage at build
-  int32_t bulk_sites = 1;  // sites per lane of the bulk kernel, set from the storage at build
+  int32_t bulk_sites = 1;  // bulk kernel mode, set from the storage at build
+  int32_t bulk_warps = 4;  // warps per CTA of the bulk kernel
   // optional per-kernel timing (lbm_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;  // 3 per profiled step
@@ -447,6 +453,7 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
   p.prefetch = c->prefetch;
   p.step_dev = nullptr;
   p.bulk_sites = c->bulk_sites;
+  p.bulk_warps = c->bulk_warps;
   for (int64_t s = 0; s < n_steps; ++s) {
     p.step = c->step;
     p.write_state = s == n_steps - 1 ? 1 : 0;
@@ -484,6 +491,10 @@ int lbm_tune(lbm_ctx* c, int32_t knob, int64_t value) {
     case LBM_TUNE_BULK_SITES:
       if (value < 1 || value > 4) return fail(c, LBM_EINVAL, "bulk sites mode must be 1 to 4");
       c->bulk_sites = (int32_t)value;
+      return LBM_OK;
+    case LBM_TUNE_BULK_WARPS:
+      if (value != 4 && value != 8) return fail(c, LBM_EINVAL, "bulk warps per CTA must be 4 or 8");
+      c->bulk_warps = (int32_t)value;
       return LBM_OK;
   }
   return fail(c, LBM_EINVAL, "unknown tuning knob for a lattice");
@@ -863,7 +874,8 @@ struct lbm_ensemble {
   int64_t* step_d = nullptr;      // device step counter of captured graphs
   std::vector<int32_t> order;     // schedule: member order in the launch numbering
   int64_t prefetch = 0;           // set from the storage at creation
-  int32_t bulk_sites = 1;         // sites per lane of the bulk kernel, set from the storage
+  int32_t bulk_sites = 1;         // bulk kernel mode, set from the storage
+  int32_t bulk_warps = 4;         // warps per CTA of the bulk kernel
   int64_t graph_steps = 0;        // 0: direct launches
   int persistent = 0;             // 1: one cooperative launch per lbm_ensemble_step
   int barrier_extra = 0;          // fault injection: arrivals the grid barrier waits for in vain
@@ -983,7 +995,7 @@ int lbm_ensemble_create(lbm_ctx* const* members, int32_t n, lbm_ensemble** out) 
   e->members.assign(members, members + n);
   e->storage = members[0]->storage;
   e->prefetch = default_prefetch(e->storage);
-  e->bulk_sites = default_bulk_sites(e->storage);
+  e->bulk_sites = default_bulk_sites(e->storage, true);
   for (lbm_ctx* c : e->members)
     if (std::find(e->member_streams.begin(), e->member_streams.end(), c->stream) ==
         e->member_streams.end())
@@ -1068,6 +1080,11 @@ int lbm_ensemble_tune(lbm_ensemble* e, int32_t knob, int64_t value) {
       e->bulk_sites = (int32_t)value;
       ens_drop_graph(e);
       return LBM_OK;
+    case LBM_TUNE_BULK_WARPS:
+      if (value != 4 && value != 8) return ens_fail(e, LBM_EINVAL, "bulk warps must be 4 or 8");
+      e->bulk_warps = (int32_t)value;
+      ens_drop_graph(e);
+      return LBM_OK;
   }
   return ens_fail(e, LBM_EINVAL, "unknown tuning knob");
 }
@@ -1090,6 +1107,7 @@ int lbm_ensemble_step(lbm_ensemble* e, int64_t n_steps) {
   lbm::StepParams p{};
   p.prefetch = e->prefetch;
   p.bulk_sites = e->bulk_sites;
+  p.bulk_warps = e->bulk_warps;
   int64_t done = 0;
   if (e->persistent && n_steps > 0) {
     p.step = step0;

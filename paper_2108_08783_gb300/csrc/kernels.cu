@@ -751,9 +751,9 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
       const bool own = (nf >> o) & 1u;
       int64_t y = own ? x : x + off(o);
       if (!chk_site(y, d.n, d.err)) y = x;  // checked builds: flagged, read a safe slot
-      // one index from one base (row selected as an integer), so that no
-      // per-direction row pointer is kept live across the update
-      g[j] = Cd::ld(P + ((int64_t)(own ? j : o) * np + y), j);
+      // one index from one base: the row offset is chosen between two
+      // products by compile-time rows, not multiplied at run time
+      g[j] = Cd::ld(P + ((own ? (int64_t)j * np : (int64_t)o * np) + y), j);
     }
   });
   const Mom<C> m = moments(g);
@@ -844,11 +844,13 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
   }
   chk_count(d.chk, P, P + x, kQ * np, d.err);
   const bool bounce = !p.elastic;
-  // Store addresses from a base the compiler cannot identify with the load
-  // addresses (an opaque copy): otherwise it keeps the 19 load addresses live
-  // until the stores that reuse them.
+  // Store addresses from a base and a stride the compiler cannot identify
+  // with those of the loads (opaque copies): otherwise it keeps the 19 load
+  // addresses, or the rows' offsets, live until the stores that reuse them.
   S* Pst;
   asm volatile("mov.b64 %0, %1;" : "=l"(Pst) : "l"(P));
+  int64_t npst;
+  asm volatile("mov.b64 %0, %1;" : "=l"(npst) : "l"(np));
   unroll<9>([&](auto Pi) {
     constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
     constexpr C w = a <= 6 ? C(1.0 / 18.0) : C(1.0 / 36.0);
@@ -894,8 +896,8 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
       int64_t ya = nfa ? x : x + off_again(a), yb = nfb ? x : x + off_again(b);
       if (!chk_site(ya, d.n, d.err)) ya = x;
       if (!chk_site(yb, d.n, d.err)) yb = x;
-      pa = Pst + ((int64_t)(nfa ? b : a) * np + ya);
-      pb = Pst + ((int64_t)(nfb ? a : b) * np + yb);
+      pa = Pst + ((nfa ? (int64_t)b * npst : (int64_t)a * npst) + ya);
+      pb = Pst + ((nfb ? (int64_t)a * npst : (int64_t)b * npst) + yb);
     } else {
       pa = Pst + b * np + x;
       pb = Pst + a * np + x;
@@ -1129,10 +1131,17 @@ __device__ __noinline__ void boundary_slow(const DevLattice& d, const StepParams
 #ifndef LBM_BULK_MINB
 #define LBM_BULK_MINB 8
 #endif
-#ifndef LBM_BULK_WARPS
-#define LBM_BULK_WARPS 4
+#ifndef LBM_BULK2_MINB
+#define LBM_BULK2_MINB 6
 #endif
-constexpr int kBulkWarps = LBM_BULK_WARPS;  // k_bulk: tiles (warps) per CTA
+// Resident CTAs per SM requested of the bulk kernels with W warps per CTA: the
+// same warps per SM whatever W (FP64: 16 warps; else LBM_BULK_MINB (one site
+// per lane) or LBM_BULK2_MINB (two sites per lane) CTAs of 4 warps).
+template <class S, int W>
+struct BulkMinBlocks {
+  static constexpr int one = sizeof(S) == 8 ? 16 / W : LBM_BULK_MINB * 4 / W;
+  static constexpr int two = LBM_BULK2_MINB * 4 / W < 1 ? 1 : LBM_BULK2_MINB * 4 / W;
+};
 #ifndef LBM_BOUNDARY_WARPS
 #define LBM_BOUNDARY_WARPS 4
 #endif
@@ -1159,9 +1168,6 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
   bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p.omega, d.err, d.chk);
 }
 
-#ifndef LBM_BULK2_MINB
-#define LBM_BULK2_MINB 6
-#endif
 
 // The fields of a lattice the bulk kernels read (a member of an ensemble is
 // read field by field from its device table, not copied whole).
@@ -1265,24 +1271,24 @@ __device__ __forceinline__ void bulk_pair_warp(const BulkView& dA, int64_t kA, d
 
 // Bulk tiles of one lattice, two per warp (warp w of block b: the bulk tiles
 // at launch positions n_boundary + 2 (b W + w) and the one after it).
-template <class S, bool ODD, bool VERT>
-__global__ void __launch_bounds__(kBulkWarps * 32, LBM_BULK2_MINB)
+template <class S, bool ODD, bool VERT, int W>
+__global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::two)
     k_bulk2(const DevLattice d, const StepParams p) {
-  __shared__ __align__(16) int32_t desc_s[kBulkWarps][2][20];
+  __shared__ __align__(16) int32_t desc_s[W][2][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t k0 = d.n_boundary + 2 * ((int64_t)blockIdx.x * kBulkWarps + w);
+  const int64_t k0 = d.n_boundary + 2 * ((int64_t)blockIdx.x * W + w);
   if (k0 >= d.n_tiles) return;  // warp-uniform
   const BulkView v = bulk_view(d);
   bulk_pair_warp<S, ODD, VERT>(v, k0, p.omega, v, k0 + 1, p.omega, k0 + 1 < d.n_tiles, true,
                                p.prefetch, desc_s[w], lane);
 }
 
-template <class S, bool ODD>
-__global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 16 / kBulkWarps : LBM_BULK_MINB)
+template <class S, bool ODD, int W>
+__global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::one)
     k_bulk(const DevLattice d, const StepParams p) {
-  __shared__ __align__(16) int32_t desc_s[kBulkWarps][20];
+  __shared__ __align__(16) int32_t desc_s[W][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t k = d.n_boundary + (int64_t)blockIdx.x * kBulkWarps + w;
+  const int64_t k = d.n_boundary + (int64_t)blockIdx.x * W + w;
   if (k >= d.n_tiles) return;  // warp-uniform
   bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
 }
@@ -1329,6 +1335,10 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
     if (lane == 0 && !bar_phase) mbar_init(bar, 1);
     __syncwarp();
     if (lane == 0) {
+      // the lanes' earlier ordinary writes to the staging area (a previous
+      // tile's rows turned into offsets, or its segment table) are ordered
+      // before the asynchronous copies that overwrite it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(bar, 18u * kTile * 4u);
       for (int i = 0; i < 18; ++i)
         bulk_g2s(nbr_s + i * kTile, d.slot_nbr + i * d.slot_stride + k * kTile, kTile * 4, bar);
@@ -1455,12 +1465,12 @@ __device__ __forceinline__ TileRef tile_ref(const TileRef* map, int64_t g) {
   return TileRef{(int32_t)(v & 0xFFFFFFFFll), (int32_t)(v >> 32)};
 }
 
-template <class S, bool ODD>
-__global__ void __launch_bounds__(kBulkWarps * 32, sizeof(S) == 8 ? 16 / kBulkWarps : LBM_BULK_MINB)
+template <class S, bool ODD, int W>
+__global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::one)
     k_bulk_ens(const EnsembleLaunch e, const StepParams p) {
-  __shared__ __align__(16) int32_t desc_s[kBulkWarps][20];
+  __shared__ __align__(16) int32_t desc_s[W][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t g = (int64_t)blockIdx.x * kBulkWarps + w;
+  const int64_t g = (int64_t)blockIdx.x * W + w;
   if (g >= e.n_bulk_tiles) return;  // warp-uniform
   const TileRef t = tile_ref(e.bulk_map, g);
   const MemberDev& md = e.mem[t.member];
@@ -1484,12 +1494,12 @@ __device__ __forceinline__ BulkView member_view(const MemberDev* m) {
 }
 
 // Bulk tiles of all members, two per warp (the pair may span two members).
-template <class S, bool ODD, bool VERT>
-__global__ void __launch_bounds__(kBulkWarps * 32, LBM_BULK2_MINB)
+template <class S, bool ODD, bool VERT, int W>
+__global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::two)
     k_bulk2_ens(const EnsembleLaunch e, const StepParams p) {
-  __shared__ __align__(16) int32_t desc_s[kBulkWarps][2][20];
+  __shared__ __align__(16) int32_t desc_s[W][2][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t g0 = 2 * ((int64_t)blockIdx.x * kBulkWarps + w);
+  const int64_t g0 = 2 * ((int64_t)blockIdx.x * W + w);
   if (g0 >= e.n_bulk_tiles) return;  // warp-uniform
   const bool two = g0 + 1 < e.n_bulk_tiles;
   const TileRef ta = tile_ref(e.bulk_map, g0), tb = two ? tile_ref(e.bulk_map, g0 + 1) : ta;
@@ -1926,6 +1936,48 @@ inline int bulk_pairing(int32_t bulk_sites, bool odd) {
   return 0;
 }
 
+// The bulk kernel of one step with W warps per CTA (pairing: bulk_pairing).
+template <class S, int W>
+void launch_bulk(const DevLattice& d, const StepParams& p, bool odd, int pairing, int64_t tiles,
+                 cudaStream_t m) {
+  if (pairing) {
+    const unsigned nb = (unsigned)((tiles + 2 * W - 1) / (2 * W));
+    if constexpr (sizeof(S) < 8) {
+      if (pairing == 1) {
+        if (odd) k_bulk2<S, true, false, W><<<nb, W * 32, 0, m>>>(d, p);
+        else k_bulk2<S, false, false, W><<<nb, W * 32, 0, m>>>(d, p);
+      } else {
+        if (odd) k_bulk2<S, true, true, W><<<nb, W * 32, 0, m>>>(d, p);
+        else k_bulk2<S, false, true, W><<<nb, W * 32, 0, m>>>(d, p);
+      }
+    }
+  } else {
+    const unsigned nb = (unsigned)((tiles + W - 1) / W);
+    if (odd) k_bulk<S, true, W><<<nb, W * 32, 0, m>>>(d, p);
+    else k_bulk<S, false, W><<<nb, W * 32, 0, m>>>(d, p);
+  }
+}
+template <class S, int W>
+void launch_bulk_ens(const EnsembleLaunch& e, const StepParams& p, bool odd, int pairing,
+                     cudaStream_t m) {
+  if (pairing) {
+    const unsigned nb = (unsigned)((e.n_bulk_tiles + 2 * W - 1) / (2 * W));
+    if constexpr (sizeof(S) < 8) {
+      if (pairing == 1) {
+        if (odd) k_bulk2_ens<S, true, false, W><<<nb, W * 32, 0, m>>>(e, p);
+        else k_bulk2_ens<S, false, false, W><<<nb, W * 32, 0, m>>>(e, p);
+      } else {
+        if (odd) k_bulk2_ens<S, true, true, W><<<nb, W * 32, 0, m>>>(e, p);
+        else k_bulk2_ens<S, false, true, W><<<nb, W * 32, 0, m>>>(e, p);
+      }
+    }
+  } else {
+    const unsigned nb = (unsigned)((e.n_bulk_tiles + W - 1) / W);
+    if (odd) k_bulk_ens<S, true, W><<<nb, W * 32, 0, m>>>(e, p);
+    else k_bulk_ens<S, false, W><<<nb, W * 32, 0, m>>>(e, p);
+  }
+}
+
 // One step: k_boundary on the side stream, k_bulk on the main stream, joined
 // on the main stream.  ev (profiling): before the fork, after k_bulk, after
 // the join, all on the main stream.
@@ -1935,7 +1987,6 @@ int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void
 
   const unsigned nbnd = (unsigned)((d.n_boundary + kBoundaryWarps - 1) / kBoundaryWarps);
   const int64_t nbulk_tiles = d.n_tiles - d.n_boundary;
-  const unsigned nbulk = (unsigned)((nbulk_tiles + kBulkWarps - 1) / kBulkWarps);
   const bool odd = p.step & 1;
   if (ev) cudaEventRecord((cudaEvent_t)ev[0], m);
   if (nbnd) {
@@ -1945,23 +1996,10 @@ int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void
     else k_boundary<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
     launch_multi<S>(d, p, odd, side);
   }
-  if (nbulk) {
+  if (nbulk_tiles > 0) {
     const int pairing = sizeof(S) < 8 ? bulk_pairing(p.bulk_sites, odd) : 0;
-    if (pairing) {
-      const unsigned nb2 = (unsigned)((nbulk_tiles + 2 * kBulkWarps - 1) / (2 * kBulkWarps));
-      if constexpr (sizeof(S) < 8) {
-        if (pairing == 1) {
-          if (odd) k_bulk2<S, true, false><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
-          else k_bulk2<S, false, false><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
-        } else {
-          if (odd) k_bulk2<S, true, true><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
-          else k_bulk2<S, false, true><<<nb2, kBulkWarps * 32, 0, m>>>(d, p);
-        }
-      }
-    } else {
-      if (odd) k_bulk<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
-      else k_bulk<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(d, p);
-    }
+    if (p.bulk_warps == 8) launch_bulk<S, 8>(d, p, odd, pairing, nbulk_tiles, m);
+    else launch_bulk<S, 4>(d, p, odd, pairing, nbulk_tiles, m);
   }
   if (ev) cudaEventRecord((cudaEvent_t)ev[1], m);
   if (nbnd) {
@@ -2009,7 +2047,6 @@ template <class S>
 int ensemble_step_t(const EnsembleLaunch& e, const StepParams& p, const StepStreams& ss) {
   cudaStream_t m = (cudaStream_t)ss.main, side = (cudaStream_t)ss.side;
   const unsigned nbnd = (unsigned)((e.n_boundary_tiles + kBoundaryWarps - 1) / kBoundaryWarps);
-  const unsigned nbulk = (unsigned)((e.n_bulk_tiles + kBulkWarps - 1) / kBulkWarps);
   const bool odd = p.step & 1;  // every member is at the same step; graphs keep the parity
   if (nbnd) {
     cudaEventRecord((cudaEvent_t)ss.fork, m);
@@ -2025,21 +2062,10 @@ int ensemble_step_t(const EnsembleLaunch& e, const StepParams& p, const StepStre
       launch_multi<S>(md.d, pm, odd, side);
     }
   }
-  const int pairing = sizeof(S) < 8 ? bulk_pairing(p.bulk_sites, odd) : 0;
-  if (nbulk && pairing) {
-    const unsigned nb2 = (unsigned)((e.n_bulk_tiles + 2 * kBulkWarps - 1) / (2 * kBulkWarps));
-    if constexpr (sizeof(S) < 8) {
-      if (pairing == 1) {
-        if (odd) k_bulk2_ens<S, true, false><<<nb2, kBulkWarps * 32, 0, m>>>(e, p);
-        else k_bulk2_ens<S, false, false><<<nb2, kBulkWarps * 32, 0, m>>>(e, p);
-      } else {
-        if (odd) k_bulk2_ens<S, true, true><<<nb2, kBulkWarps * 32, 0, m>>>(e, p);
-        else k_bulk2_ens<S, false, true><<<nb2, kBulkWarps * 32, 0, m>>>(e, p);
-      }
-    }
-  } else if (nbulk) {
-    if (odd) k_bulk_ens<S, true><<<nbulk, kBulkWarps * 32, 0, m>>>(e, p);
-    else k_bulk_ens<S, false><<<nbulk, kBulkWarps * 32, 0, m>>>(e, p);
+  if (e.n_bulk_tiles > 0) {
+    const int pairing = sizeof(S) < 8 ? bulk_pairing(p.bulk_sites, odd) : 0;
+    if (p.bulk_warps == 8) launch_bulk_ens<S, 8>(e, p, odd, pairing, m);
+    else launch_bulk_ens<S, 4>(e, p, odd, pairing, m);
   }
   if (nbnd) {
     cudaEventRecord((cudaEvent_t)ss.join, side);

@@ -178,7 +178,8 @@ struct StepParams {
   int64_t step;      // step index (plus *step_dev when step_dev is set)
   int64_t prefetch;  // L2 prefetch distance in tiles of launch order (0: off)
   const int64_t* step_dev;  // device step counter (captured graphs), or NULL
-  int32_t bulk_sites;       // sites per lane of the bulk kernel: 1, or 2 (FP32 / 16-bit)
+  int32_t bulk_sites;       // bulk kernel mode (LBM_TUNE_BULK_SITES)
+  int32_t bulk_warps;       // warps per CTA of the bulk kernel: 4 or 8
 };
 
 // One member of an ensemble: its device view and its wall constants.

@@ -226,13 +226,16 @@ class Lattice:
     def profile(self, enable=True):
         self._check(self._lib.lbm_profile(self.h, 1 if enable else 0))
 
-    def tune(self, prefetch=None, bulk_sites=None):
+    def tune(self, prefetch=None, bulk_sites=None, bulk_warps=None):
         """Launch knobs (``lbm_tune``): L2 prefetch distance of the bulk kernel in
-        tiles, and the bulk kernel's sites per lane and their pairing (1 to 4)."""
+        tiles, the bulk kernel's sites per lane and their pairing (1 to 4), and
+        its warps per CTA (4 or 8)."""
         if prefetch is not None:
             self._check(self._lib.lbm_tune(self.h, A.LBM_TUNE_PREFETCH, int(prefetch)))
         if bulk_sites is not None:
             self._check(self._lib.lbm_tune(self.h, A.LBM_TUNE_BULK_SITES, int(bulk_sites)))
+        if bulk_warps is not None:
+            self._check(self._lib.lbm_tune(self.h, A.LBM_TUNE_BULK_WARPS, int(bulk_warps)))
 
     def time_steps(self, n):
         """Device ms of n steps (CUDA events on the lattice's stream)."""
@@ -246,17 +249,20 @@ class Lattice:
         e1.synchronize()
         return e0.elapsed_time(e1)
 
-    def autotune(self, bulk_sites=(1, 2, 3, 4), prefetch=(0, 2048, 4096), trial_steps=40):
+    def autotune(self, bulk_sites=(1, 2, 3, 4), bulk_warps=(4, 8), prefetch=(0, 2048, 4096),
+                 trial_steps=40):
         """Choose the bulk kernel's site tile (one site per lane, a 32-site tile per
         warp; or two per lane, 64 sites per warp, paired as adjacent sites or as
-        two tiles) and its L2 prefetch distance by timing each candidate on this
-        lattice (coordinate search).  Every trial advances the lattice by
-        ``trial_steps`` steps (an even number keeps both parities equal)."""
+        two tiles), its CTA size and its L2 prefetch distance by timing each
+        candidate on this lattice (coordinate search).  Every trial advances the
+        lattice by ``trial_steps`` steps (an even number keeps both parities
+        equal)."""
         if self.storage == "f64":
             bulk_sites = (1,)
-        best = dict(bulk_sites=bulk_sites[0], prefetch=prefetch[0])
+        best = dict(bulk_sites=bulk_sites[0], bulk_warps=bulk_warps[0], prefetch=prefetch[0])
         results = []
-        for knob, cands in (("bulk_sites", bulk_sites), ("prefetch", prefetch)):
+        for knob, cands in (("bulk_sites", bulk_sites), ("bulk_warps", bulk_warps),
+                            ("prefetch", prefetch)):
             times = {}
             for v in cands:
                 cfg = dict(best)
@@ -302,7 +308,7 @@ class Ensemble:
         self.stream = self.members[0].stream  # the ensemble's work is ordered with it
         self.n = sum(m.n for m in self.members)
         self.settings = {"prefetch": None, "schedule": 0, "graph_steps": 0, "persistent": 0,
-                         "bulk_sites": None}
+                         "bulk_sites": None, "bulk_warps": 4}
 
     def _check(self, rc):
         if rc != A.LBM_OK:
@@ -315,7 +321,7 @@ class Ensemble:
         self._check(self._lib.lbm_ensemble_sync(self.h))
 
     def tune(self, prefetch=None, schedule=None, graph_steps=None, persistent=None,
-             barrier_extra=None, bulk_sites=None):
+             barrier_extra=None, bulk_sites=None, bulk_warps=None):
         if prefetch is not None:
             self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_PREFETCH, int(prefetch)))
             self.settings["prefetch"] = int(prefetch)
@@ -337,6 +343,10 @@ class Ensemble:
             self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_BULK_SITES,
                                                     int(bulk_sites)))
             self.settings["bulk_sites"] = int(bulk_sites)
+        if bulk_warps is not None:
+            self._check(self._lib.lbm_ensemble_tune(self.h, A.LBM_TUNE_BULK_WARPS,
+                                                    int(bulk_warps)))
+            self.settings["bulk_warps"] = int(bulk_warps)
 
     def time_steps(self, n):
         """Device ms of n steps (CUDA events on the ensemble's stream)."""
@@ -352,7 +362,7 @@ class Ensemble:
 
     def autotune(self, prefetch=(0, 1024, 2048, 4096, 8192), schedule=(0, 1),
                  graph_steps=(0, 20), persistent=(0, 1), bulk_sites=(1, 2, 3, 4),
-                 trial_steps=40):
+                 bulk_warps=(4, 8), trial_steps=40):
         """Choose the schedule knobs by timing each candidate on this ensemble
         (coordinate search, one knob at a time): member order, the bulk kernel's
         site tile (one site per lane, 32 sites per warp; or two per lane, 64 per
@@ -363,10 +373,10 @@ class Ensemble:
         if self.members[0].storage == "f64":
             bulk_sites = (1,)
         best = dict(prefetch=prefetch[0], schedule=schedule[0], graph_steps=graph_steps[0],
-                    persistent=persistent[0], bulk_sites=bulk_sites[0])
+                    persistent=persistent[0], bulk_sites=bulk_sites[0], bulk_warps=bulk_warps[0])
         for knob, cands in (("schedule", schedule), ("bulk_sites", bulk_sites),
-                            ("prefetch", prefetch), ("graph_steps", graph_steps),
-                            ("persistent", persistent)):
+                            ("bulk_warps", bulk_warps), ("prefetch", prefetch),
+                            ("graph_steps", graph_steps), ("persistent", persistent)):
             times = {}
             for v in cands:
                 cfg = dict(best)

@@ -245,6 +245,46 @@ def test_long_tube_full_size_short_run(storage, tol, bulk_sites):
     _compare(lat, orc, tol, "long tube")
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_every_bulk_kernel_variant_against_the_oracle(storage):
+    """The bulk kernel in each launch configuration the autotuner chooses from
+    (one or two sites per lane with either pairing, 4 or 8 warps per CTA) on the
+    R = 12, L = 159 tube, 301 steps from a smooth random state: FP32 within the
+    1e-5 tolerance; FP16S within its storage bound at that step count; and for
+    FP32 the variants agree with one another to 1e-6."""
+    geo = _bulk_tube()
+    fields = I.random_fields(13, geo.shape, drho=1e-3, umax=0.02)
+    orc = None
+    res = {}
+    for bulk_sites in (1, 2, 3, 4):
+        for warps in (4, 8):
+            lat, o = make_pair(geo, storage, tau=0.8, wall_model=1, F=0.85, kappa=BULK_KAPPA,
+                               fields=fields, bulk_sites=bulk_sites)
+            lat.tune(bulk_warps=warps)
+            _assert_bulk_path(lat)
+            lat.step(301)
+            lat.sync()
+            if orc is None:
+                o.run(301)
+                orc = o
+            rl, ul = lat.moments()
+            res[(bulk_sites, warps)] = (rl, ul)
+            lat.close()
+    ro, uo = orc.moments()
+    if storage == "f32":
+        bound_r = bound_u = 1e-5
+    else:
+        e_rho, e_u = rounding_walk_estimate(orc, 301)
+        bound_r = BOUND_FACTOR * UNIT_ROUNDOFF[storage] * e_rho
+        bound_u = BOUND_FACTOR * UNIT_ROUNDOFF[storage] * e_u
+    r0, u0 = res[(1, 4)]
+    for key, (rl, ul) in res.items():
+        er = rel_l2(rl, ro) if storage == "f32" else rel_l2(rl - 1, ro - 1)
+        assert er < bound_r and rel_l2(ul, uo) < bound_u, (key, er, rel_l2(ul, uo))
+        if storage == "f32":
+            assert rel_l2(ul, u0) < 1e-6, key
+
+
 # ------------------------------------------------------------------ reduced precision
 
 @pytest.mark.parametrize("bulk_sites", [1, 2])

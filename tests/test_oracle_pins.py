@@ -583,3 +583,32 @@ def test_density_outlet_sets_the_pressure_level():
     assert abs(shift.mean() / delta - 1.0) < 0.05
     assert np.std(shift) < 0.05 * delta
     assert np.max(np.abs(u1 - u0)) < 1e-3 * np.max(np.abs(u0))
+
+
+# ----------------------------------------------------------- wall times (Sec. 2.4)
+
+def _walltimes():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "walltimes.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        r, el, ri, sites, cores = line.split()
+        rows.append((int(r), float(el), float(ri), int(sites), int(cores)))
+    return rows
+
+
+def test_walltime_table_is_consistent_with_table_a1_and_the_papers_claim():
+    """Table WallTimes (Sec. 2.4, wall time of 1000 iterations, elastic wall vs
+    rigid bounce-back on the same domain and cores) against Table A1's sites and
+    cores for the three cylinders, the paper's statement that the elastic wall
+    is no slower than the rigid one, and the site-update rates the two tables
+    imply (sites x 1000 / wall time): 5,318 / 13,168 / 31,235 MLUPS elastic,
+    1.73 / 2.19 / 2.60 MLUPS per core."""
+    a1 = {name: (sites, cores) for name, _, _, _, _, sites, cores in _table_a1()}
+    want = {50: (5318, 1.73), 100: (13168, 2.19), 200: (31235, 2.60)}
+    for r, elastic, rigid, sites, cores in _walltimes():
+        assert a1["cylinder_R%d" % r] == (sites, cores)
+        assert elastic <= rigid
+        mlups = sites * 1000 / elastic / 1e6
+        assert abs(mlups - want[r][0]) < 1.0
+        assert abs(mlups / cores - want[r][1]) < 0.005
