@@ -278,8 +278,7 @@ int lbm_wss(lbm_ctx *ctx, const int64_t *sites, const double *normals, int64_t m
  *                        second tile follows the first with the same offsets):
  *                        2 = adjacent sites on even steps, two tiles on odd
  *                        steps; 3 = adjacent sites on both; 4 = two tiles on
- *                        both.  Default: 2 (lattices) and 3 (ensembles) for
- *                        16-bit storage, 1 otherwise;
+ *                        both.  Default: 2 for 16-bit storage, 1 otherwise;
  *   LBM_TUNE_BULK_WARPS  warps (tiles, or tile pairs) per CTA of the bulk
  *                        kernel: 4 (default) or 8, the same warps per SM.
  * Before using a member's own calls (moments, wall state, ...) call

@@ -22,19 +22,17 @@
 // issue-bound and lose more to the prefetch instructions than they gain; FP64
 // is ALU-bound either way.  -DLBM_DEFAULT_PREFETCH=n overrides.
 // Bulk kernel mode (LBM_TUNE_BULK_SITES) by storage, measured on GB300: the
-// 16-bit storages gain from two sites per lane (single lattices: adjacent
-// sites on even steps, two tiles on odd steps, +11-15 % on the long tube and
-// +4 % on the tree; ensembles: adjacent sites on both, +6 %); FP32 is
-// DRAM-bound with one site per lane and loses 3-6 % with two; FP64 has one
-// form only.  -DLBM_DEFAULT_BULK_SITES=n overrides.
-inline int32_t default_bulk_sites(int storage, bool ensemble = false) {
+// 16-bit storages gain from two sites per lane, adjacent sites on even steps
+// and two tiles on odd steps (+11-15 % on the long tube, +4 % on the tree,
+// +9 % on the 256-tube ensemble); FP32 is DRAM-bound with one site per lane
+// and loses 0-6 % with two; FP64 has one form only.
+// -DLBM_DEFAULT_BULK_SITES=n overrides.
+inline int32_t default_bulk_sites(int storage) {
 #ifdef LBM_DEFAULT_BULK_SITES
   (void)storage;
-  (void)ensemble;
   return LBM_DEFAULT_BULK_SITES;
 #else
-  if (storage == LBM_F16S || storage == LBM_BF16S) return ensemble ? 3 : 2;
-  return 1;
+  return (storage == LBM_F16S || storage == LBM_BF16S) ? 2 : 1;
 #endif
 }
 
@@ -995,7 +993,7 @@ int lbm_ensemble_create(lbm_ctx* const* members, int32_t n, lbm_ensemble** out) 
   e->members.assign(members, members + n);
   e->storage = members[0]->storage;
   e->prefetch = default_prefetch(e->storage);
-  e->bulk_sites = default_bulk_sites(e->storage, true);
+  e->bulk_sites = default_bulk_sites(e->storage);
   for (lbm_ctx* c : e->members)
     if (std::find(e->member_streams.begin(), e->member_streams.end(), c->stream) ==
         e->member_streams.end())

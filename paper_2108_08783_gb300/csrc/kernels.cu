@@ -1142,6 +1142,25 @@ struct BulkMinBlocks {
   static constexpr int one = sizeof(S) == 8 ? 16 / W : LBM_BULK_MINB * 4 / W;
   static constexpr int two = LBM_BULK2_MINB * 4 / W < 1 ? 1 : LBM_BULK2_MINB * 4 / W;
 };
+// The ensemble kernels hold each member's pointers and strides in registers
+// (a single lattice reads them from the kernel parameters), so they get their
+// own register budgets, measured on the 256-tube ensemble: 80 registers for the
+// one-site bulk kernel and the boundary kernel (FP32 +14 % over 64, which
+// spill), 128 for the two-site bulk kernel (FP16S +11 % over 80).
+#ifndef LBM_ENS_BULK_MINB
+#define LBM_ENS_BULK_MINB 6
+#endif
+#ifndef LBM_ENS_BULK2_MINB
+#define LBM_ENS_BULK2_MINB 4
+#endif
+#ifndef LBM_ENS_BOUNDARY_MINB
+#define LBM_ENS_BOUNDARY_MINB 6
+#endif
+template <class S, int W>
+struct EnsBulkMinBlocks {
+  static constexpr int one = sizeof(S) == 8 ? 16 / W : LBM_ENS_BULK_MINB * 4 / W;
+  static constexpr int two = LBM_ENS_BULK2_MINB * 4 / W < 1 ? 1 : LBM_ENS_BULK2_MINB * 4 / W;
+};
 #ifndef LBM_BOUNDARY_WARPS
 #define LBM_BOUNDARY_WARPS 4
 #endif
@@ -1466,7 +1485,7 @@ __device__ __forceinline__ TileRef tile_ref(const TileRef* map, int64_t g) {
 }
 
 template <class S, bool ODD, int W>
-__global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::one)
+__global__ void __launch_bounds__(W * 32, EnsBulkMinBlocks<S, W>::one)
     k_bulk_ens(const EnsembleLaunch e, const StepParams p) {
   __shared__ __align__(16) int32_t desc_s[W][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1495,7 +1514,7 @@ __device__ __forceinline__ BulkView member_view(const MemberDev* m) {
 
 // Bulk tiles of all members, two per warp (the pair may span two members).
 template <class S, bool ODD, bool VERT, int W>
-__global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::two)
+__global__ void __launch_bounds__(W * 32, EnsBulkMinBlocks<S, W>::two)
     k_bulk2_ens(const EnsembleLaunch e, const StepParams p) {
   __shared__ __align__(16) int32_t desc_s[W][2][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1510,7 +1529,7 @@ __global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::two)
 }
 
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_BOUNDARY_MINB)
+__global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_ENS_BOUNDARY_MINB)
     k_boundary_ens(const EnsembleLaunch e, const StepParams p) {
   using C = typename Codec<S>::C;
   __shared__ __align__(128) int32_t stage[kBoundaryWarps][18 * kTile];
