@@ -269,8 +269,11 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   uint32_t* sm = dev_alloc<uint32_t>(c, S);
   uint32_t* sio = dev_alloc<uint32_t>(c, S);
   int32_t* sn = dev_alloc<int32_t>(c, 18 * S);
-  double* sp = dev_alloc<double>(c, 3 * S);
-  double* sF = dev_alloc<double>(c, S);
+  // inlet profile and wall F in the compute type (FP64 storage: double; the
+  // FP32-compute storages: float, so the step kernels convert nothing)
+  const size_t cb = storage == LBM_F64 ? sizeof(double) : sizeof(float);
+  unsigned char* sp = dev_alloc<unsigned char>(c, 3 * S * cb);
+  unsigned char* sF = dev_alloc<unsigned char>(c, S * cb);
   double* sK = dev_alloc<double>(c, S);
   double* sdE = dev_alloc<double>(c, S);
   double* sUw = dev_alloc<double>(c, 3 * S);
@@ -332,6 +335,16 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     t.phase = s.phase;
     const double an = std::sqrt(s.axis[0] * s.axis[0] + s.axis[1] * s.axis[1] + s.axis[2] * s.axis[2]);
     for (int a = 0; a < 3; ++a) t.axis[a] = s.axis[a] / an;
+    // fixed-point phase (fraction of a period, units of 2^-64)
+    const double inv = 1.0 / t.period;
+    t.phase_inc = lbm::frac_to_u64(inv - std::floor(inv));
+    const double ph = t.phase * (0.5 / M_PI);
+    t.phase_off = lbm::frac_to_u64(ph - std::floor(ph));
+    t.rho_f = (float)t.rho;
+    t.drho_f = (float)(t.rho - 1.0);
+    t.u_mean_f = (float)t.u_mean;
+    t.u_amp_f = (float)t.u_amp;
+    for (int a = 0; a < 3; ++a) t.axis_f[a] = (float)t.axis[a];
   }
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
@@ -340,14 +353,20 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   chk(h2d(c, sm, L.slot_mask.data(), S));
   chk(h2d(c, sio, L.slot_io.data(), S));
   chk(h2d(c, sn, L.slot_nbr.data(), 18 * S));
-  chk(h2d(c, sp, L.slot_prof.data(), 3 * S));
+  std::vector<float> prof_f;
+  if (storage == LBM_F64) {
+    chk(h2d(c, reinterpret_cast<double*>(sp), L.slot_prof.data(), 3 * S));
+  } else {
+    prof_f.assign(L.slot_prof.begin(), L.slot_prof.end());  // rounded once, here
+    chk(h2d(c, reinterpret_cast<float*>(sp), prof_f.data(), 3 * S));
+  }
   chk(h2d(c, io, hio.data(), hio.size()));
   chk(h2d(c, c->iolet_off, L.iolet_off.data(), L.iolet_off.size()));
   chk(h2d(c, c->iolet_sites, L.iolet_sites.data(), L.iolet_sites.size()));
   if (mt) chk(h2d(c, mt, L.multi_tiles.data(), L.multi_tiles.size()));
   if (stab) chk(h2d(c, stab, L.seg_tab.data(), L.seg_tab.size()));
   if (S) {
-    chk(cudaMemsetAsync(sF, 0, S * sizeof(double), c->stream));
+    chk(cudaMemsetAsync(sF, 0, S * cb, c->stream));
     chk(cudaMemsetAsync(sK, 0, S * sizeof(double), c->stream));
     chk(cudaMemsetAsync(sdE, 0, S * sizeof(double), c->stream));
     chk(cudaMemsetAsync(sUw, 0, 3 * S * sizeof(double), c->stream));
@@ -413,7 +432,14 @@ int lbm_set_wall_params(lbm_ctx* c, int32_t wall_model, double rho0, const doubl
     hF[c->L.wall_slot[w]] = f;
     hK[c->L.wall_slot[w]] = k / 3.0;  // the kernel applies kappa c_s^2 to (rho - rho0)
   }
-  cudaError_t e = h2d(c, const_cast<double*>(c->d.slot_F), hF.data(), S);
+  cudaError_t e;
+  std::vector<float> hF_f;
+  if (c->storage == LBM_F64) {
+    e = h2d(c, static_cast<double*>(const_cast<void*>(c->d.slot_F)), hF.data(), S);
+  } else {
+    hF_f.assign(hF.begin(), hF.end());
+    e = h2d(c, static_cast<float*>(const_cast<void*>(c->d.slot_F)), hF_f.data(), S);
+  }
   if (e == cudaSuccess) e = h2d(c, const_cast<double*>(c->d.slot_kappa), hK.data(), S);
   if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_wall_params");
   int rc = sync(c, "lbm_set_wall_params");
@@ -444,9 +470,10 @@ int lbm_init_fields(lbm_ctx* c, const double* rho, const double* u) {
 int lbm_step(lbm_ctx* c, int64_t n_steps) {
   if (!c) return LBM_EINVAL;
   if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps must be >= 0");
-  lbm::StepParams p;
+  lbm::StepParams p{};
   p.rho0 = c->rho0;
   p.omega = 1.0 / c->tau;
+  p.omega_f = (float)p.omega;
   p.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
   p.prefetch = c->prefetch;
   p.step_dev = nullptr;
@@ -938,6 +965,7 @@ int ens_upload(lbm_ensemble* e) {
     md.d = c->d;
     md.d.chk = nullptr;  // store counting covers single-lattice steps only
     md.omega = 1.0 / c->tau;
+    md.omega_f = (float)md.omega;
     md.rho0 = c->rho0;
     md.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
   }

@@ -157,6 +157,60 @@ __device__ __forceinline__ double mul_pin(double a, double b) { return __dmul_rn
 __device__ __forceinline__ float fma_pin(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_pin(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// The relaxation rate 1/tau in the compute type: the FP32 paths take the copy
+// rounded on the host, so no step kernel converts from FP64 (GB300 issues one
+// FP64 warp instruction in the time of dozens of FP32 ones).
+template <class C>
+__device__ __forceinline__ C omega_as(double w, float wf);
+template <>
+__device__ __forceinline__ double omega_as<double>(double w, float) { return w; }
+template <>
+__device__ __forceinline__ float omega_as<float>(double, float wf) { return wf; }
+
+// Velocity inlet (Sec. 3) of a site with profile values (p0, ps, pc) at step
+// n: u_in = axis (u_mean p0 + u_amp (ps sin th + pc cos th)),
+// th = 2 pi n / T + phase.  FP64 paths take sin/cos of th in FP64, as the
+// oracle does.  FP32 paths take th from the iolet's 64-bit fixed-point phase
+// (frac(n / T + phase / 2 pi) in integer arithmetic, exact modulo one
+// period), keep its top 24 bits (a phase error below 2^-24 of a period,
+// ~4e-7 rad) and evaluate sinpi/cospi and the profile in FP32.
+__device__ __forceinline__ void inlet_velocity(const IoletDev& io, int64_t n, double p0, double ps,
+                                               double pc, double& ux, double& uy, double& uz) {
+  double g = mul_pin(io.u_mean, p0);
+  if (!io.steady) {
+    double sn, cs;
+    sincos(2.0 * M_PI * (double)n / io.period + io.phase, &sn, &cs);
+    g = fma_pin(io.u_amp, fma_pin(ps, sn, mul_pin(pc, cs)), g);
+  }
+  ux = mul_pin(g, io.axis[0]);
+  uy = mul_pin(g, io.axis[1]);
+  uz = mul_pin(g, io.axis[2]);
+}
+__device__ __forceinline__ void inlet_velocity(const IoletDev& io, int64_t n, float p0, float ps,
+                                               float pc, float& ux, float& uy, float& uz) {
+  float g = mul_pin(io.u_mean_f, p0);
+  if (!io.steady) {
+    const uint64_t ph = io.phase_off + (uint64_t)n * io.phase_inc;  // mod 2^64
+    const float t = (float)(uint32_t)(ph >> 40) * 0x1p-24f;           // [0, 1)
+    float sn, cs;
+    sincospif(2.0f * t, &sn, &cs);
+    g = fma_pin(io.u_amp_f, fma_pin(ps, sn, mul_pin(pc, cs)), g);
+  }
+  ux = mul_pin(g, io.axis_f[0]);
+  uy = mul_pin(g, io.axis_f[1]);
+  uz = mul_pin(g, io.axis_f[2]);
+}
+
+// Density outlet state rho_out and rho_out - 1 in the compute type.
+__device__ __forceinline__ void outlet_density(const IoletDev& io, double& r, double& dr) {
+  r = io.rho;
+  dr = io.rho - 1.0;
+}
+__device__ __forceinline__ void outlet_density(const IoletDev& io, float& r, float& dr) {
+  r = io.rho_f;
+  dr = io.drho_f;
+}
+
 template <class C>
 struct Mom {
   C drho, rho, ux, uy, uz, usq;
@@ -251,6 +305,14 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
                "l"(__cvta_generic_to_global(gmem))
                : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)),
+               "l"(__cvta_generic_to_global(gmem))
+               : "memory");
+}
+// one element of the compute type (4 or 8 bytes)
+__device__ __forceinline__ void cp_async_elem(float* smem, const float* gmem) { cp_async4(smem, gmem); }
+__device__ __forceinline__ void cp_async_elem(double* smem, const double* gmem) { cp_async8(smem, gmem); }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -330,7 +392,7 @@ __device__ __forceinline__ bool chk_site(int64_t y, int64_t n, int* err) {
 // Branch-free update of a site whose 18 links are fluid.
 template <class S, bool ODD>
 __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t* dsc,
-                                            double omega_t, int* err, int* chk) {
+                                            typename Codec<S>::C omega, int* err, int* chk) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
   C g[kQ];
@@ -342,7 +404,6 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
   });
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(err, kErrUnstable);
-  const C omega = C(omega_t);
   Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
   chk_count(chk, P, P + x, kQ * np, err);
   // Opposite directions a, b = opp(a) share c_b = -c_a, so their shifted
@@ -566,7 +627,7 @@ __device__ __forceinline__ void collide2(const F2 (&g)[kQ], F2 omega, int* err_l
 // sites, packed loads and stores where the offset is even.
 template <class S, bool ODD>
 __device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const int32_t* dsc,
-                                             double omega_t, int* err, int* chk) {
+                                             float omega, int* err, int* chk) {
   using Cd = Codec2<S>;
   F2 g[kQ];
   unroll<kQ>([&](auto J) {
@@ -581,7 +642,7 @@ __device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const 
     }
   });
   collide2(
-      g, bc2(float(omega_t)), err, err,
+      g, bc2(omega), err, err,
       [&](F2 s0) {
         Cd::st_al(P + x, s0);
         chk_count2(chk, P, P + x, kQ * np, err);
@@ -614,7 +675,7 @@ __device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const 
 // offset, no second address).
 template <class S, bool ODD, bool SAME>
 __device__ __forceinline__ void bulk_update2v(S* P, int64_t np, int64_t xa, int64_t xb,
-                                              const int32_t* da, const int32_t* db, double omega_t,
+                                              const int32_t* da, const int32_t* db, float omega,
                                               int* err, int* chk) {
   using Cd = Codec<S>;
   F2 g[kQ];
@@ -640,7 +701,7 @@ __device__ __forceinline__ void bulk_update2v(S* P, int64_t np, int64_t xa, int6
     chk_count(chk, P, pb, kQ * np, err);
   };
   collide2(
-      g, bc2(float(omega_t)), err, err,
+      g, bc2(omega), err, err,
       [&](F2 s0) { put(P + xa, SAME ? P + xa + kTile : P + xb, s0, 0); },
       [&](auto A, F2 sa, F2 sb) {
         constexpr int i = decltype(A)::value, k = i + 1;  // the pair (i, k = opp i)
@@ -722,7 +783,7 @@ constexpr int kAreaSite = 25;   // first row (compute-type units) of the per-sit
 // cp_async_wait_all); area: the warp's shared-memory area (BoundaryArea).
 template <class S, bool ODD>
 __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepParams& p,
-                                              double omega_t, S* P, int64_t x,
+                                              typename Codec<S>::C omega, S* P, int64_t x,
                                               const int32_t* offp, int ostride, uint32_t smask,
                                               uint32_t iom, const double* site,
                                               const int32_t* nbr_s, int lane, int64_t slot,
@@ -765,14 +826,15 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
   });
   auto gv = [&](int j) -> C { return static_cast<const volatile C*>(area)[j * kTile + lane]; };
   if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
-  const C omega = C(omega_t);
   const C keep = C(1) - omega;  // (1 - 1/tau)
   // Elastic wall (Sec. 2.3-2.4): dE in FP64, the ratio sw = U_w/u_f =
   // (F + dr - dx)/dr with dr = dx + dE in the compute type.
   C sw = C(0);
   if ((smask & kHasWall) && p.elastic) {
     cp_async_wait_all();
-    const double Fw = site[lane], Kw = site[kTile + lane];  // F, kappa c_s^2
+    // F (compute type), kappa c_s^2 (FP64)
+    const C Fw = reinterpret_cast<const C*>(site)[lane];
+    const double Kw = site[kTile + lane];
     const double dp = (double)m.rho - p.rho0;
     const double dE = Kw * (dp > 0.0 ? dp : 0.0);
     if constexpr (std::is_same<C, double>::value) {
@@ -780,7 +842,7 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
       sw = (Fw + dr - 1.0) / dr;
     } else {
       const float e = (float)dE;
-      sw = (float(Fw) + e) * recip(1.0f + e);
+      sw = (Fw + e) * recip(1.0f + e);
     }
     if (p.write_state) {
       const int64_t ss = d.slot_stride;
@@ -802,31 +864,15 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
     const IoletDev& io = d.iolets[k];
     if (io.kind == LBM_IOLET_VELOCITY) {
       cp_async_wait_all();
-      const double pr0 = site[2 * kTile + lane], pr1 = site[3 * kTile + lane];
-      const double pr2 = site[4 * kTile + lane];
-      double gval = io.u_mean * pr0;
-      if (!io.steady) {
-        double sn, cs;
-        const int64_t step = p.step + (p.step_dev ? *p.step_dev : 0);
-        if constexpr (std::is_same<C, double>::value) {
-          sincos(2.0 * M_PI * (double)step / io.period + io.phase, &sn, &cs);
-        } else {
-          double t = (double)step / io.period + io.phase * (0.5 / M_PI);
-          t -= floor(t);
-          float sf, cf;
-          sincospif(2.0f * (float)t, &sf, &cf);
-          sn = sf;
-          cs = cf;
-        }
-        gval = fma(io.u_amp, fma(pr1, sn, pr2 * cs), gval);
-      }
-      ubx = C(gval * io.axis[0]);
-      uby = C(gval * io.axis[1]);
-      ubz = C(gval * io.axis[2]);
+      // rows 2..4 of the per-site area: p0, ps, pc in the compute type
+      const C pr0 = reinterpret_cast<const C*>(site + 2 * kTile)[lane];
+      const C pr1 = reinterpret_cast<const C*>(site + 3 * kTile)[lane];
+      const C pr2 = reinterpret_cast<const C*>(site + 4 * kTile)[lane];
+      const int64_t step = p.step + (p.step_dev ? *p.step_dev : 0);
+      inlet_velocity(io, step, pr0, pr1, pr2, ubx, uby, ubz);
       usqb = C(1.5) * (ubx * ubx + uby * uby + ubz * ubz);
     } else {
-      rb = C(io.rho);
-      drb = C(io.rho - 1.0);
+      outlet_density(io, rb, drb);
     }
   }
   C* iost = area + kAreaIolet * kTile;
@@ -942,10 +988,12 @@ __device__ __forceinline__ C dir_weight(int i) {
 // [19][32] shared-memory area where g is parked for the boundary rule.
 template <class S, bool ODD>
 __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepParams& p,
-                                                double omega_t, S* P,
+                                                typename Codec<S>::C omega, S* P,
                                                 int64_t x, const int32_t* dsc, bool irr,
-                                                uint32_t smask, uint32_t iom, double Fw, double Kw,
-                                                double pr0, double pr1, double pr2,
+                                                uint32_t smask, uint32_t iom,
+                                                typename Codec<S>::C Fw, double Kw,
+                                                typename Codec<S>::C pr0, typename Codec<S>::C pr1,
+                                                typename Codec<S>::C pr2,
                                                 const int32_t* nbr_s, int lane, int64_t slot,
                                                 typename Codec<S>::C (&g)[kQ],
                                                 typename Codec<S>::C* gsm) {
@@ -954,7 +1002,6 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   const int64_t np = d.npad;
   const Mom<C> m = moments(g);
   if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
-  const C omega = C(omega_t);
   const C keep = C(1) - omega;  // (1 - 1/tau)
   // neighbour index of a fluid link i (odd steps)
   auto nb = [&](int i) -> int64_t {
@@ -995,7 +1042,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
       sw = (Fw + dr - 1.0) / dr;
     } else {
       const float e = (float)dE;
-      sw = mul_pin(float(Fw) + e, recip(1.0f + e));
+      sw = mul_pin(Fw + e, recip(1.0f + e));
     }
     if (p.write_state) {
       const int64_t ss = d.slot_stride;
@@ -1009,29 +1056,8 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   C uix = C(0), uiy = C(0), uiz = C(0);
   if (smask & kHasInlet) {
     const int k = (int)((iom & kIoletIdBits) >> kIoletShift);
-    const IoletDev& io = d.iolets[k];
-    double gval = mul_pin(io.u_mean, pr0);
-    if (!io.steady) {
-      // th = 2 pi n / T + phase.  FP64 paths take sin/cos in FP64 (as the
-      // oracle); FP32 paths reduce the phase to one period in FP64 and take
-      // sinpi/cospi in FP32 (error ~1e-7 of u_amp).
-      double sn, cs;
-      const int64_t step = p.step + (p.step_dev ? *p.step_dev : 0);
-      if constexpr (std::is_same<C, double>::value) {
-        sincos(2.0 * M_PI * (double)step / io.period + io.phase, &sn, &cs);
-      } else {
-        double t = (double)step / io.period + io.phase * (0.5 / M_PI);
-        t -= floor(t);
-        float sf, cf;
-        sincospif(2.0f * (float)t, &sf, &cf);
-        sn = sf;
-        cs = cf;
-      }
-      gval = fma_pin(io.u_amp, fma_pin(pr1, sn, mul_pin(pr2, cs)), gval);
-    }
-    uix = C(mul_pin(gval, io.axis[0]));
-    uiy = C(mul_pin(gval, io.axis[1]));
-    uiz = C(mul_pin(gval, io.axis[2]));
+    const int64_t step = p.step + (p.step_dev ? *p.step_dev : 0);
+    inlet_velocity(d.iolets[k], step, pr0, pr1, pr2, uix, uiy, uiz);
   }
   const C uisq = mul_pin(C(1.5), fma_pin(uiz, uiz, fma_pin(uiy, uiy, mul_pin(uix, uix))));
   // Links that leave the fluid: the population of direction j = opp(i) that
@@ -1068,7 +1094,9 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
         const C inner = fma_pin(mul_pin(C(4.5), ci), ci, fma_pin(C(3), ci, -uisq));
         e = mul_pin(wj, fma_pin(m.rho, inner, m.drho));
       } else {
-        e = mul_pin(wj, fma_pin(C(io.rho), fma_pin(C(3), cu, quad), C(io.rho - 1.0)));
+        C ro, dro;
+        outlet_density(io, ro, dro);
+        e = mul_pin(wj, fma_pin(ro, fma_pin(C(3), cu, quad), dro));
       }
     }
     return fma_pin(keep, fneq, e);
@@ -1119,13 +1147,15 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
 template <class S, bool ODD>
 __device__ __noinline__ void boundary_slow(const DevLattice& d, const StepParams& p, S* P,
                                            int64_t x, const int32_t* dsc, bool irr, uint32_t smask,
-                                           uint32_t iom, double Fw, double Kw, double pr0,
-                                           double pr1, double pr2, const int32_t* nbr_s, int lane,
+                                           uint32_t iom, typename Codec<S>::C Fw, double Kw,
+                                           typename Codec<S>::C pr0, typename Codec<S>::C pr1,
+                                           typename Codec<S>::C pr2, const int32_t* nbr_s, int lane,
                                            int64_t slot, typename Codec<S>::C* gsm) {
-  typename Codec<S>::C g[kQ];
+  using C = typename Codec<S>::C;
+  C g[kQ];
   boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g, d.n, d.err);
-  boundary_update<S, ODD>(d, p, p.omega, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s,
-                          lane, slot, g, gsm);
+  boundary_update<S, ODD>(d, p, omega_as<C>(p.omega, p.omega_f), P, x, dsc, irr, smask, iom, Fw,
+                          Kw, pr0, pr1, pr2, nbr_s, lane, slot, g, gsm);
 }
 
 #ifndef LBM_BULK_MINB
@@ -1184,7 +1214,8 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
     for (int o = 0; o < 18; ++o) ok = chk_site(x + dsc[o], d.n, d.err) && ok;
     if (!ok) return;
   }
-  bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc, p.omega, d.err, d.chk);
+  bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc,
+                      omega_as<typename Codec<S>::C>(p.omega, p.omega_f), d.err, d.chk);
 }
 
 
@@ -1213,8 +1244,8 @@ __device__ __forceinline__ BulkView bulk_view(const DevLattice& d) {
 //     same offsets).
 // A site without a partner takes the single-site update.
 template <class S, bool ODD, bool VERT>
-__device__ __forceinline__ void bulk_pair_warp(const BulkView& dA, int64_t kA, double omA,
-                                               const BulkView& dB, int64_t kB, double omB,
+__device__ __forceinline__ void bulk_pair_warp(const BulkView& dA, int64_t kA, float omA,
+                                               const BulkView& dB, int64_t kB, float omB,
                                                bool two, bool one_lattice, int64_t prefetch,
                                                int32_t (*dsc2)[20], int lane) {
   if (lane < 20) {
@@ -1298,7 +1329,7 @@ __global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::two)
   const int64_t k0 = d.n_boundary + 2 * ((int64_t)blockIdx.x * W + w);
   if (k0 >= d.n_tiles) return;  // warp-uniform
   const BulkView v = bulk_view(d);
-  bulk_pair_warp<S, ODD, VERT>(v, k0, p.omega, v, k0 + 1, p.omega, k0 + 1 < d.n_tiles, true,
+  bulk_pair_warp<S, ODD, VERT>(v, k0, p.omega_f, v, k0 + 1, p.omega_f, k0 + 1 < d.n_tiles, true,
                                p.prefetch, desc_s[w], lane);
 }
 
@@ -1367,15 +1398,19 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
   // per-site wall and inlet data (F, kappa/3, inlet profile p0, ps, pc) into
   // the warp's area (from row kAreaSite), copied asynchronously so that no register
   // holds them while the populations load
+  // Rows of 32 doubles: F (row 0) and p0, ps, pc (rows 2-4) in the compute
+  // type at the start of their rows, kappa c_s^2 (row 1) in FP64.
   double* site = reinterpret_cast<double*>(gsm + kAreaSite * kTile);  // [5][32]
+  auto site_row = [&](int r) { return reinterpret_cast<C*>(site + r * kTile); };
   if (valid && (smask & kHasWall)) {
-    cp_async8(site + lane, d.slot_F + slot);
+    cp_async_elem(site_row(0) + lane, static_cast<const C*>(d.slot_F) + slot);
     cp_async8(site + kTile + lane, d.slot_kappa + slot);
   }
   if (valid && (smask & kHasInlet)) {
-    cp_async8(site + 2 * kTile + lane, d.slot_prof + slot);
-    cp_async8(site + 3 * kTile + lane, d.slot_prof + d.slot_stride + slot);
-    cp_async8(site + 4 * kTile + lane, d.slot_prof + 2 * d.slot_stride + slot);
+    const C* prof = static_cast<const C*>(d.slot_prof);
+    cp_async_elem(site_row(2) + lane, prof + slot);
+    cp_async_elem(site_row(3) + lane, prof + d.slot_stride + slot);
+    cp_async_elem(site_row(4) + lane, prof + 2 * d.slot_stride + slot);
   }
   cp_async_commit();
   // warp-uniform: which boundary states the tile needs at all
@@ -1419,22 +1454,21 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
         offp = nbr_s + lane;
         ostride = kTile;
       }
-      boundary_fast<S, ODD>(d, p, p.omega, P, x, offp, ostride, smask, iom, site, nbr_s, lane,
-                            slot, warp_io, warp_wall, warp_nf, gsm);
+      boundary_fast<S, ODD>(d, p, omega_as<C>(p.omega, p.omega_f), P, x, offp, ostride, smask,
+                            iom, site, nbr_s, lane, slot, warp_io, warp_wall, warp_nf, gsm);
     }
     return true;
   }
   if constexpr (PART == 0) return true;
   cp_async_wait_all();
-  const double Fw = site[lane], Kw = site[kTile + lane];
-  const double pr0 = site[2 * kTile + lane], pr1 = site[3 * kTile + lane];
-  const double pr2 = site[4 * kTile + lane];
+  const C Fw = site_row(0)[lane];
+  const double Kw = site[kTile + lane];
+  const C pr0 = site_row(2)[lane], pr1 = site_row(3)[lane], pr2 = site_row(4)[lane];
   if constexpr (PART == 1) {
-    using C = typename Codec<S>::C;
     C g[kQ];
     boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g, d.n, d.err);
-    boundary_update<S, ODD>(d, p, p.omega, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2,
-                            nbr_s, lane, slot, g, gsm);
+    boundary_update<S, ODD>(d, p, omega_as<C>(p.omega, p.omega_f), P, x, dsc, irr, smask, iom,
+                            Fw, Kw, pr0, pr1, pr2, nbr_s, lane, slot, g, gsm);
   } else {
     boundary_slow<S, ODD>(d, p, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s, lane,
                           slot, gsm);
@@ -1495,6 +1529,7 @@ __global__ void __launch_bounds__(W * 32, EnsBulkMinBlocks<S, W>::one)
   const MemberDev& md = e.mem[t.member];
   StepParams pm = p;
   pm.omega = md.omega;
+  pm.omega_f = md.omega_f;
   bulk_tile<S, ODD>(md.d, pm, t.k, desc_s[w], lane);
 }
 
@@ -1523,8 +1558,8 @@ __global__ void __launch_bounds__(W * 32, EnsBulkMinBlocks<S, W>::two)
   const bool two = g0 + 1 < e.n_bulk_tiles;
   const TileRef ta = tile_ref(e.bulk_map, g0), tb = two ? tile_ref(e.bulk_map, g0 + 1) : ta;
   const BulkView A = member_view(e.mem + ta.member), B = member_view(e.mem + tb.member);
-  bulk_pair_warp<S, ODD, VERT>(A, ta.k, __ldg(&e.mem[ta.member].omega), B, tb.k,
-                               __ldg(&e.mem[tb.member].omega), two, ta.member == tb.member,
+  bulk_pair_warp<S, ODD, VERT>(A, ta.k, __ldg(&e.mem[ta.member].omega_f), B, tb.k,
+                               __ldg(&e.mem[tb.member].omega_f), two, ta.member == tb.member,
                                p.prefetch, desc_s[w], lane);
 }
 
@@ -1543,6 +1578,7 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
   const MemberDev& md = e.mem[t.member];
   StepParams pm = p;
   pm.omega = md.omega;
+  pm.omega_f = md.omega_f;
   pm.rho0 = md.rho0;
   pm.elastic = md.elastic;
   boundary_tile<S, ODD>(md.d, pm, t.k, desc_s[w], stage[w], &bars[w], gs[w], lane);
@@ -1648,6 +1684,7 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
           const MemberDev& md = e.mem[tr.member];
           StepParams pm = q;
           pm.omega = md.omega;
+          pm.omega_f = md.omega_f;
           pm.rho0 = md.rho0;
           pm.elastic = md.elastic;
           const int64_t k = tr.k;
@@ -1665,6 +1702,7 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
           const MemberDev& md = e.mem[tr.member];
           StepParams pm = q;
           pm.omega = md.omega;
+          pm.omega_f = md.omega_f;
           const int64_t k = tr.k;
           if (odd) persist_bulk<S, true>(md.d, pm, k, desc_s[w], lane);
           else persist_bulk<S, false>(md.d, pm, k, desc_s[w], lane);
@@ -2076,6 +2114,7 @@ int ensemble_step_t(const EnsembleLaunch& e, const StepParams& p, const StepStre
       const MemberDev& md = e.multi_host[q];
       StepParams pm = p;
       pm.omega = md.omega;
+      pm.omega_f = md.omega_f;
       pm.rho0 = md.rho0;
       pm.elastic = md.elastic;
       launch_multi<S>(md.d, pm, odd, side);

@@ -3,6 +3,7 @@
 // kernels use.  Not part of the public C ABI (see include/lbm.h).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <memory>
@@ -81,8 +82,24 @@ struct IoletDev {
   double u_mean, u_amp, period, phase;
   double axis[3];  // unit vector
   double pad;
+  // The same constants for the FP32 compute paths, rounded once on the host:
+  // the phase th = 2 pi n / T + phase as a 64-bit fixed-point fraction of a
+  // period, frac(n / T + phase / 2 pi) = (phase_off + n phase_inc) / 2^64
+  // (mod 1; integer arithmetic, no FP64 in the step kernels), and float
+  // copies of rho, rho - 1, u_mean, u_amp and the axis.
+  uint64_t phase_inc;
+  uint64_t phase_off;
+  float rho_f, drho_f, u_mean_f, u_amp_f;
+  float axis_f[3];
+  float pad_f;
 };
 static_assert(sizeof(IoletDev) % 16 == 0, "IoletDev alignment");
+
+// 2^64 x as an integer, for a fraction x in [0, 1) (anything else gives 0).
+inline uint64_t frac_to_u64(double x) {
+  if (!(x >= 0.0) || x >= 1.0) return 0;
+  return (uint64_t)std::ldexp(x, 64);
+}
 
 // Allocator whose resize() leaves new elements uninitialised, for the large
 // host arrays that the builder's threads write in full (first touch happens
@@ -154,9 +171,11 @@ struct DevLattice {
   const uint32_t* slot_mask = nullptr;
   const uint32_t* slot_io = nullptr;
   const int32_t* slot_nbr = nullptr;   // [18][slot_stride]
-  const double* slot_prof = nullptr;   // [3][slot_stride]
-  const double* slot_F = nullptr;
-  const double* slot_kappa = nullptr;  // kappa c_s^2 = kappa / 3 (per slot)
+  // per-slot inlet profile [3][slot_stride] (p0, ps, pc) and wall F, in the
+  // compute type (double for F64 storage, float otherwise)
+  const void* slot_prof = nullptr;
+  const void* slot_F = nullptr;
+  const double* slot_kappa = nullptr;  // kappa c_s^2 = kappa / 3 (per slot), FP64 (tube law)
   double* slot_dE = nullptr;
   double* slot_Uw = nullptr;           // [3][slot_stride]
   int64_t slot_stride = 0;
@@ -172,6 +191,8 @@ struct DevLattice {
 
 struct StepParams {
   double omega;      // 1 / tau
+  float omega_f;     // (float) omega, for the FP32 compute paths
+  int32_t pad0;
   double rho0;
   int32_t elastic;   // 1: elastic GZS wall, 0: bounce-back
   int32_t write_state;
@@ -188,7 +209,7 @@ struct MemberDev {
   double omega;
   double rho0;
   int32_t elastic;
-  int32_t pad;
+  float omega_f;  // (float) omega
 };
 
 
