@@ -781,6 +781,15 @@ constexpr int kAreaSite = 25;   // first row (compute-type units) of the per-sit
 // boundary values); site: the
 // warp's [5][32] per-site F, kappa/3, p0, ps, pc (copies in flight until
 // cp_async_wait_all); area: the warp's shared-memory area (BoundaryArea).
+// The odd-step slot deltas (opp(i) - i) np below stay within one row length
+// because opposite directions are numbered next to each other.
+constexpr bool opposites_adjacent() {
+  for (int i = 1; i < kQ; ++i)
+    if (dir_opp(i) - i != 1 && dir_opp(i) - i != -1) return false;
+  return true;
+}
+static_assert(opposites_adjacent(), "opposite directions must be adjacent");
+
 template <class S, bool ODD>
 __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepParams& p,
                                               typename Codec<S>::C omega, S* P, int64_t x,
@@ -802,6 +811,24 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
   // the same offset re-read at store time (volatile: not held in registers
   // from the loads to the stores)
   auto off_again = [&](int i) -> int32_t { return lds_volatile(offp + (i - 1) * ostride); };
+  // Odd steps: link i's slot is A_i = P + i np + x + delta_i, with delta_i =
+  // nbr(x, i) - x when the link is fluid and (opp(i) - i) np = +-np when it
+  // leaves the fluid (the site's own slot of direction opp(i)).  The load of
+  // g_opp(i) and the store of the post-collision value of direction i both
+  // use A_i.  In 32-bit parts (x < 2^32, |delta_i| < 2^31 since npad < 2^31)
+  // each address is two wide multiply-adds on the row base i np, which does
+  // not depend on the lane.
+  const int32_t np32 = (int32_t)np;
+  auto delta = [&](int i, int32_t off_i) -> int32_t {
+    const bool fluid = !((nf >> i) & 1u);
+    int32_t dl = fluid ? off_i : (dir_opp(i) - i) * np32;
+    // checked builds: a bad neighbour index is flagged and the own slot used
+    if (kChecked && fluid && !chk_site(x + off_i, d.n, d.err)) dl = (dir_opp(i) - i) * np32;
+    return dl;
+  };
+  auto slot_at = [&](int i, uint32_t xs, int32_t dl) -> S* {
+    return P + (int64_t)i * np + xs + dl;
+  };
   C g[kQ];
   unroll<kQ>([&](auto J) {
     constexpr int j = decltype(J)::value;
@@ -809,12 +836,7 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
     if constexpr (!ODD || j == 0) {
       g[j] = Cd::ld(P + j * np + x, j);
     } else {
-      const bool own = (nf >> o) & 1u;
-      int64_t y = own ? x : x + off(o);
-      if (!chk_site(y, d.n, d.err)) y = x;  // checked builds: flagged, read a safe slot
-      // one index from one base: the row offset is chosen between two
-      // products by compile-time rows, not multiplied at run time
-      g[j] = Cd::ld(P + ((own ? (int64_t)j * np : (int64_t)o * np) + y), j);
+      g[j] = Cd::ld(slot_at(o, (uint32_t)x, delta(o, off(o))), j);
     }
   });
   const Mom<C> m = moments(g);
@@ -890,13 +912,14 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
   }
   chk_count(d.chk, P, P + x, kQ * np, d.err);
   const bool bounce = !p.elastic;
-  // Store addresses from a base and a stride the compiler cannot identify
-  // with those of the loads (opaque copies): otherwise it keeps the 19 load
-  // addresses, or the rows' offsets, live until the stores that reuse them.
+  // Store addresses from a base and a stride (even steps) or a site index
+  // (odd steps) the compiler cannot identify with those of the loads (opaque
+  // copies): otherwise it keeps the 19 load addresses, or the rows' offsets,
+  // live until the stores that reuse them.
   S* Pst;
   asm volatile("mov.b64 %0, %1;" : "=l"(Pst) : "l"(P));
-  int64_t npst;
-  asm volatile("mov.b64 %0, %1;" : "=l"(npst) : "l"(np));
+  uint32_t xst;
+  asm volatile("mov.b32 %0, %1;" : "=r"(xst) : "r"((uint32_t)x));
   unroll<9>([&](auto Pi) {
     constexpr int a = 2 * decltype(Pi)::value + 1, b = a + 1;
     constexpr C w = a <= 6 ? C(1.0 / 18.0) : C(1.0 / 36.0);
@@ -939,11 +962,8 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
     S* pa;
     S* pb;
     if constexpr (ODD) {
-      int64_t ya = nfa ? x : x + off_again(a), yb = nfb ? x : x + off_again(b);
-      if (!chk_site(ya, d.n, d.err)) ya = x;
-      if (!chk_site(yb, d.n, d.err)) yb = x;
-      pa = Pst + ((nfa ? (int64_t)b * npst : (int64_t)a * npst) + ya);
-      pb = Pst + ((nfb ? (int64_t)a * npst : (int64_t)b * npst) + yb);
+      pa = slot_at(a, xst, delta(a, off_again(a)));
+      pb = slot_at(b, xst, delta(b, off_again(b)));
     } else {
       pa = Pst + b * np + x;
       pb = Pst + a * np + x;

@@ -160,7 +160,8 @@ int build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     run_base[c + 1] = run_base[c] + col_runs[c];
   }
   const int64_t n = col_base[C];
-  if (n >= std::numeric_limits<int32_t>::max() - 4 * kTile) {
+  // site ids are 32-bit, and so is the padded row length (n plus at most 191)
+  if (n >= std::numeric_limits<int32_t>::max() - 8 * kTile) {
     err = "too many fluid sites for 32-bit site ids";
     return LBM_EINVAL;
   }
