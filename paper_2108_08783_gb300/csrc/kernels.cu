@@ -509,8 +509,32 @@ struct Codec2<float> {
     p[1] = h;
   }
 };
+// 16-bit pairs also travel as packed words (low half: the first site): two
+// sites' values in one register from the load until the collision needs them.
+__device__ __forceinline__ uint32_t ld_word(const void* p) {
+  return *static_cast<const uint32_t*>(p);
+}
+__device__ __forceinline__ uint32_t ld_u16(const void* p) {
+  return *static_cast<const unsigned short*>(p);
+}
+__device__ __forceinline__ uint32_t pack_u16(uint32_t lo, uint32_t hi) {
+  return __byte_perm(lo, hi, 0x5410);
+}
+// An opaque copy: the compiler cannot tie the value read back after the
+// moments to the one unpacked for them, so it keeps the packed word, not
+// the two unpacked floats, live through the collision.
+__device__ __forceinline__ uint32_t opaque(uint32_t v) {
+  uint32_t r;
+  asm volatile("mov.b32 %0, %1;" : "=r"(r) : "r"(v));
+  return r;
+}
+
 template <>
 struct Codec2<__half> {
+  static __device__ __forceinline__ F2 unpack(uint32_t w) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+    return mk2(f.x, f.y);
+  }
   static __device__ __forceinline__ F2 ld_al(const __half* p) {
     const float2 f = __half22float2(*reinterpret_cast<const __half2*>(p));
     return mk2(f.x, f.y);
@@ -534,6 +558,9 @@ struct Codec2<__half> {
 };
 template <>
 struct Codec2<__nv_bfloat16> {
+  static __device__ __forceinline__ F2 unpack(uint32_t w) {
+    return mk2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+  }
   static __device__ __forceinline__ F2 ld_al(const __nv_bfloat16* p) {
     const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
     return mk2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
@@ -564,13 +591,20 @@ __device__ __forceinline__ void chk_count2(int* chk, const S* P0, const S* p, in
   chk_count(chk, P0, p + 1, lim, err);
 }
 
-// The collision of bulk_update for two sites at once, on packed pairs: g
-// holds the pre-collision values; store0(g*_0) receives the rest population
-// and store<a, b>(g*_a, g*_b) those of each opposite pair (a odd, b = a + 1).
-template <class St0, class St>
-__device__ __forceinline__ void collide2(const F2 (&g)[kQ], F2 omega, int* err_lo, int* err_hi,
-                                         St0&& store0, St&& store) {
+// The collision of bulk_update for two sites at once, on packed pairs: gm(j)
+// gives the pre-collision values for the moments, gp(j) the same values again
+// for the relaxation (the 16-bit paths unpack them twice from packed words
+// rather than hold 38 floats); store0(g*_0) receives the rest population and
+// store<a, b>(g*_a, g*_b) those of each opposite pair (a odd, b = a + 1).
+template <class GetM, class GetP, class St0, class St>
+__device__ __forceinline__ void collide2(GetM&& gm, GetP&& gp, F2 omega, int* err_lo,
+                                         int* err_hi, St0&& store0, St&& store) {
   // Eqs. (Density), (Momentum), grouped as in moments()
+  F2 g[kQ];
+  unroll<kQ>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    g[j] = gm(j);
+  });
   const F2 a1 = sub2(g[1], g[2]), a3 = sub2(g[3], g[4]), a5 = sub2(g[5], g[6]);
   const F2 a7 = sub2(g[7], g[8]), a9 = sub2(g[9], g[10]), a11 = sub2(g[11], g[12]);
   const F2 a13 = sub2(g[13], g[14]), a15 = sub2(g[15], g[16]), a17 = sub2(g[17], g[18]);
@@ -594,7 +628,10 @@ __device__ __forceinline__ void collide2(const F2 (&g)[kQ], F2 omega, int* err_l
   const F2 usq = mul2(bc2(1.5f), fma2(uz, uz, fma2(uy, uy, mul2(ux, ux))));
   // rest population: g*_0 = g_0 + omega (w_0 (drho - rho usq) - g_0)
   const F2 e0 = mul2(bc2(1.0f / 3.0f), sub2(drho, mul2(rho, usq)));
-  store0(fma2(omega, sub2(e0, g[0]), g[0]));
+  {
+    const F2 g0 = gp(0);
+    store0(fma2(omega, sub2(e0, g0), g0));
+  }
   // opposite pairs (a, b): g^eq = even +- odd (see bulk_update)
   const F2 wd1 = mul2(drho, bc2(1.0f / 18.0f)), wd2 = mul2(drho, bc2(1.0f / 36.0f));
   const F2 wr1 = mul2(rho, bc2(1.0f / 18.0f)), wr2 = mul2(rho, bc2(1.0f / 36.0f));
@@ -616,8 +653,9 @@ __device__ __forceinline__ void collide2(const F2 (&g)[kQ], F2 omega, int* err_l
     const F2 q = fma2(mul2(bc2(4.5f), cu), cu, nusq);
     const F2 even = (a <= 6) ? fma2(wr1, q, wd1) : fma2(wr2, q, wd2);
     const F2 odd = mul2((a <= 6) ? w3r1 : w3r2, cu);
-    const F2 sa = fma2(omega, sub2(add2(even, odd), g[a]), g[a]);
-    const F2 sb = fma2(omega, sub2(sub2(even, odd), g[a + 1]), g[a + 1]);
+    const F2 ga = gp(a), gb = gp(a + 1);
+    const F2 sa = fma2(omega, sub2(add2(even, odd), ga), ga);
+    const F2 sb = fma2(omega, sub2(sub2(even, odd), gb), gb);
     store(std::integral_constant<int, a>{}, sa, sb);
   });
 }
@@ -629,20 +667,34 @@ template <class S, bool ODD>
 __device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const int32_t* dsc,
                                              float omega, int* err, int* chk) {
   using Cd = Codec2<S>;
-  F2 g[kQ];
+  constexpr bool kPacked = sizeof(S) == 2;
+  F2 g[kPacked ? 1 : kQ];
+  uint32_t r[kPacked ? kQ : 1];
   unroll<kQ>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int o = dir_opp(j);
+    const S* q;
+    bool un = false;
     if constexpr (!ODD || j == 0) {
-      g[j] = Cd::ld_al(P + j * np + x);
+      q = P + j * np + x;
     } else {
       const int32_t dd = dsc[o - 1];
-      const S* q = P + o * np + x + dd;
-      g[j] = (dd & 1) ? Cd::ld_un(q) : Cd::ld_al(q);
+      q = P + o * np + x + dd;
+      un = dd & 1;
     }
+    if constexpr (kPacked) r[j] = un ? pack_u16(ld_u16(q), ld_u16(q + 1)) : ld_word(q);
+    else g[j] = un ? Cd::ld_un(q) : Cd::ld_al(q);
   });
+  auto gm = [&](int j) -> F2 {
+    if constexpr (kPacked) return Cd::unpack(r[j]);
+    else return g[j];
+  };
+  auto gp = [&](int j) -> F2 {
+    if constexpr (kPacked) return Cd::unpack(opaque(r[j]));
+    else return g[j];
+  };
   collide2(
-      g, bc2(omega), err, err,
+      gm, gp, bc2(omega), err, err,
       [&](F2 s0) {
         Cd::st_al(P + x, s0);
         chk_count2(chk, P, P + x, kQ * np, err);
@@ -678,7 +730,9 @@ __device__ __forceinline__ void bulk_update2v(S* P, int64_t np, int64_t xa, int6
                                               const int32_t* da, const int32_t* db, float omega,
                                               int* err, int* chk) {
   using Cd = Codec<S>;
-  F2 g[kQ];
+  constexpr bool kPacked = sizeof(S) == 2;
+  F2 g[kPacked ? 1 : kQ];
+  uint32_t r[kPacked ? kQ : 1];
   unroll<kQ>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int o = dir_opp(j);
@@ -690,8 +744,17 @@ __device__ __forceinline__ void bulk_update2v(S* P, int64_t np, int64_t xa, int6
       qa = P + o * np + xa + da[o - 1];
       qb = SAME ? qa + kTile : P + o * np + xb + db[o - 1];
     }
-    g[j] = mk2(Cd::ld(qa, j), Cd::ld(qb, j));
+    if constexpr (kPacked) r[j] = pack_u16(ld_u16(qa), ld_u16(qb));
+    else g[j] = mk2(Cd::ld(qa, j), Cd::ld(qb, j));
   });
+  auto gm = [&](int j) -> F2 {
+    if constexpr (kPacked) return Codec2<S>::unpack(r[j]);
+    else return g[j];
+  };
+  auto gp = [&](int j) -> F2 {
+    if constexpr (kPacked) return Codec2<S>::unpack(opaque(r[j]));
+    else return g[j];
+  };
   auto put = [&](S* pa, S* pb, F2 v, int i) {
     float lo, hi;
     split2(v, lo, hi);
@@ -701,7 +764,7 @@ __device__ __forceinline__ void bulk_update2v(S* P, int64_t np, int64_t xa, int6
     chk_count(chk, P, pb, kQ * np, err);
   };
   collide2(
-      g, bc2(omega), err, err,
+      gm, gp, bc2(omega), err, err,
       [&](F2 s0) { put(P + xa, SAME ? P + xa + kTile : P + xb, s0, 0); },
       [&](auto A, F2 sa, F2 sb) {
         constexpr int i = decltype(A)::value, k = i + 1;  // the pair (i, k = opp i)
@@ -1184,13 +1247,17 @@ __device__ __noinline__ void boundary_slow(const DevLattice& d, const StepParams
 #ifndef LBM_BULK2_MINB
 #define LBM_BULK2_MINB 6
 #endif
+#ifndef LBM_BULK2_MINB16
+#define LBM_BULK2_MINB16 8
+#endif
 // Resident CTAs per SM requested of the bulk kernels with W warps per CTA: the
 // same warps per SM whatever W (FP64: 16 warps; else LBM_BULK_MINB (one site
 // per lane) or LBM_BULK2_MINB (two sites per lane) CTAs of 4 warps).
 template <class S, int W>
 struct BulkMinBlocks {
   static constexpr int one = sizeof(S) == 8 ? 16 / W : LBM_BULK_MINB * 4 / W;
-  static constexpr int two = LBM_BULK2_MINB * 4 / W < 1 ? 1 : LBM_BULK2_MINB * 4 / W;
+  static constexpr int two_ctas = sizeof(S) == 2 ? LBM_BULK2_MINB16 : LBM_BULK2_MINB;
+  static constexpr int two = two_ctas * 4 / W < 1 ? 1 : two_ctas * 4 / W;
 };
 // The ensemble kernels hold each member's pointers and strides in registers
 // (a single lattice reads them from the kernel parameters), so they get their
@@ -1220,6 +1287,9 @@ constexpr int kBoundaryWarps = LBM_BOUNDARY_WARPS;  // k_boundary: tiles (warps)
 template <class S, bool ODD>
 __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams& p, int64_t k,
                                           int32_t* dsc, int lane) {
+  // a warp that updates tiles in a loop (persistent kernel): every lane is done
+  // with the previous tile's descriptor before it is overwritten
+  __syncwarp();
   if (lane < 20) dsc[lane] = __ldg(reinterpret_cast<const int32_t*>(d.launch + k) + lane);
   if (p.prefetch > 0 && k + p.prefetch < d.n_tiles && lane < kQ) {
     const int64_t tp = __ldg(&d.launch[k + p.prefetch].tile);
@@ -1379,6 +1449,10 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
                                               typename Codec<S>::C* gsm, int lane,
                                               uint32_t* bar_phase = nullptr) {
   using C = typename Codec<S>::C;
+  // a warp that updates tiles in a loop (persistent kernel): lanes that left
+  // the previous tile early (padding sites) wait here until every lane is done
+  // with its descriptor, segment table and staged rows
+  __syncwarp();
   const int64_t slot = k * kTile + lane;  // boundary tiles lead the launch order
   // per-site data and the descriptor, all in one round trip
   const uint32_t smask = __ldg(d.slot_mask + slot);
