@@ -1433,8 +1433,12 @@ __global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::one)
   bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
 }
 
+// Resident CTAs (4 warps) per SM requested of the boundary kernel: 7, i.e. 73
+// registers, measured on the long tube and the depth-6 tree against 6, 8 and
+// 10 (tree FP32 +8 %, tube FP32 +3 %, FP16S +1-3 % over 8, whose 64 registers
+// spill on odd steps).
 #ifndef LBM_BOUNDARY_MINB
-#define LBM_BOUNDARY_MINB 8
+#define LBM_BOUNDARY_MINB 7
 #endif
 // Boundary tile at launch position k (whole warp); nbr_s, bar: the warp's
 // staging area (18 rows of per-site neighbours) and mbarrier; dsc: its
