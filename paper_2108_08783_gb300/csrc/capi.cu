@@ -472,6 +472,8 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
   if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps must be >= 0");
   lbm::StepParams p{};
   p.rho0 = c->rho0;
+  p.rho0_f = (float)c->rho0;
+  p.rho0_exact = (double)p.rho0_f == c->rho0 ? 1 : 0;
   p.omega = 1.0 / c->tau;
   p.omega_f = (float)p.omega;
   p.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
@@ -967,6 +969,8 @@ int ens_upload(lbm_ensemble* e) {
     md.omega = 1.0 / c->tau;
     md.omega_f = (float)md.omega;
     md.rho0 = c->rho0;
+    md.rho0_f = (float)c->rho0;
+    md.rho0_exact = (double)md.rho0_f == c->rho0 ? 1 : 0;
     md.elastic = c->wall_model == LBM_WALL_ELASTIC_GZS ? 1 : 0;
   }
   cudaError_t r = cudaMemcpyAsync(e->mem_d, tab.data(), n * sizeof(lbm::MemberDev),

@@ -201,6 +201,24 @@ __device__ __forceinline__ void inlet_velocity(const IoletDev& io, int64_t n, fl
   uz = mul_pin(g, io.axis_f[2]);
 }
 
+// Tube law (Sec. 2.4): the wall expansion dE = kappa c_s^2 max(0, rho - rho0)
+// in FP64, Kw = kappa c_s^2 (Sec. 2.3 pressure p - P0 = c_s^2 (rho - rho0)).
+// FP64 compute: as written.  FP32 compute, with rho0 a float (p.rho0_exact)
+// and rho within [rho0/2, 2 rho0]: rho - rho0 is exact in FP32 (Sterbenz), so
+// the FP64 result is the same bits from one conversion and one FP64 multiply
+// instead of two conversions, an FP64 add and an FP64 compare; other lanes
+// take the FP64 difference.
+__device__ __forceinline__ double tube_law(double Kw, double rho, const StepParams& p) {
+  const double dp = rho - p.rho0;
+  return Kw * (dp > 0.0 ? dp : 0.0);
+}
+__device__ __forceinline__ double tube_law(double Kw, float rho, const StepParams& p) {
+  if (p.rho0_exact && rho >= 0.5f * p.rho0_f && rho <= 2.0f * p.rho0_f)
+    return Kw * (double)fmaxf(rho - p.rho0_f, 0.0f);
+  const double dp = (double)rho - p.rho0;
+  return Kw * (dp > 0.0 ? dp : 0.0);
+}
+
 // Density outlet state rho_out and rho_out - 1 in the compute type.
 __device__ __forceinline__ void outlet_density(const IoletDev& io, double& r, double& dr) {
   r = io.rho;
@@ -920,8 +938,7 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
     // F (compute type), kappa c_s^2 (FP64)
     const C Fw = reinterpret_cast<const C*>(site)[lane];
     const double Kw = site[kTile + lane];
-    const double dp = (double)m.rho - p.rho0;
-    const double dE = Kw * (dp > 0.0 ? dp : 0.0);
+    const double dE = tube_law(Kw, m.rho, p);
     if constexpr (std::is_same<C, double>::value) {
       const double dr = 1.0 + dE;
       sw = (Fw + dr - 1.0) / dr;
@@ -1118,8 +1135,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
   C sw = C(0);
   if ((smask & kHasWall) && p.elastic) {
     // Kw holds kappa c_s^2 = kappa / 3, so dE = Kw max(0, rho - rho0)
-    const double dp = (double)m.rho - p.rho0;
-    const double dE = Kw * (dp > 0.0 ? dp : 0.0);
+    const double dE = tube_law(Kw, m.rho, p);
     if constexpr (std::is_same<C, double>::value) {
       const double dr = 1.0 + dE;
       sw = (Fw + dr - 1.0) / dr;
@@ -1262,8 +1278,9 @@ struct BulkMinBlocks {
 // The ensemble kernels hold each member's pointers and strides in registers
 // (a single lattice reads them from the kernel parameters), so they get their
 // own register budgets, measured on the 256-tube ensemble: 80 registers for the
-// one-site bulk kernel and the boundary kernel (FP32 +14 % over 64, which
-// spill), 128 for the two-site bulk kernel (FP16S +11 % over 80).
+// one-site bulk kernel (FP32 +14 % over 64, which spill), 128 for the two-site
+// bulk kernel (FP16S +11 % over 80), 72 for the boundary kernel (FP16S +7 %
+// over 80, +2 % over 64).
 #ifndef LBM_ENS_BULK_MINB
 #define LBM_ENS_BULK_MINB 6
 #endif
@@ -1271,7 +1288,7 @@ struct BulkMinBlocks {
 #define LBM_ENS_BULK2_MINB 4
 #endif
 #ifndef LBM_ENS_BOUNDARY_MINB
-#define LBM_ENS_BOUNDARY_MINB 6
+#define LBM_ENS_BOUNDARY_MINB 7
 #endif
 template <class S, int W>
 struct EnsBulkMinBlocks {
@@ -1678,6 +1695,8 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
   pm.omega = md.omega;
   pm.omega_f = md.omega_f;
   pm.rho0 = md.rho0;
+  pm.rho0_f = md.rho0_f;
+  pm.rho0_exact = md.rho0_exact;
   pm.elastic = md.elastic;
   boundary_tile<S, ODD>(md.d, pm, t.k, desc_s[w], stage[w], &bars[w], gs[w], lane);
 }
@@ -1784,6 +1803,8 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
           pm.omega = md.omega;
           pm.omega_f = md.omega_f;
           pm.rho0 = md.rho0;
+          pm.rho0_f = md.rho0_f;
+          pm.rho0_exact = md.rho0_exact;
           pm.elastic = md.elastic;
           const int64_t k = tr.k;
           const bool ok = odd ? persist_boundary<S, true>(md.d, pm, k, desc_s[w], stage[w],
@@ -2214,6 +2235,8 @@ int ensemble_step_t(const EnsembleLaunch& e, const StepParams& p, const StepStre
       pm.omega = md.omega;
       pm.omega_f = md.omega_f;
       pm.rho0 = md.rho0;
+      pm.rho0_f = md.rho0_f;
+      pm.rho0_exact = md.rho0_exact;
       pm.elastic = md.elastic;
       launch_multi<S>(md.d, pm, odd, side);
     }

@@ -194,6 +194,8 @@ struct StepParams {
   float omega_f;     // (float) omega, for the FP32 compute paths
   int32_t pad0;
   double rho0;
+  float rho0_f;        // (float) rho0
+  int32_t rho0_exact;  // rho0 == (double) rho0_f
   int32_t elastic;   // 1: elastic GZS wall, 0: bounce-back
   int32_t write_state;
   int64_t step;      // step index (plus *step_dev when step_dev is set)
@@ -210,6 +212,8 @@ struct MemberDev {
   double rho0;
   int32_t elastic;
   float omega_f;  // (float) omega
+  float rho0_f;   // (float) rho0
+  int32_t rho0_exact;
 };
 
 
