@@ -137,6 +137,22 @@ int lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *u);
  * return without waiting.  Step n evaluates the inlet time factor at n. */
 int lbm_step(lbm_ctx *ctx, int64_t n_steps);
 
+/* lbm_step_diag - lbm_step of n_steps >= 1 timesteps whose last step also
+ * reduces the diagnostics of the state it reads (the state after n_steps - 1
+ * steps), as lbm_reduce defines them: out[0] total mass sum_x rho_x,
+ * out[1 + k] the flux of rho u along iolet k's axis over the sites with a
+ * link into it.  The step kernels add each tile's rho - 1 in FP32 (one value
+ * per 32 sites) and write the momenta of the iolet sites; one more kernel adds
+ * those in FP64 in a fixed order, so no extra pass over the populations is
+ * made (Sec. 2.1 moments; the mass and flux sums of the benchmark contract).
+ * out is a host array [1 + n_iolets]; the copy into it is queued on the
+ * context's stream and complete after the next synchronizing call
+ * (lbm_sync); page-locked memory keeps the call from waiting.  The first call
+ * allocates the device tables (a double per tile, three doubles per lane
+ * of the tiles with iolet sites).  Errors: LBM_EINVAL (n_steps < 1, NULL
+ * arguments), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_step_diag(lbm_ctx *ctx, int64_t n_steps, double *out);
+
 /* lbm_moments - rho [n_sites] and u [n_sites][3] (FP64, canonical order) of
  * the current pre-collision state (Eqs. Density, Momentum).  Either pointer may
  * be NULL.  dst_is_device != 0: device pointers, written asynchronously on the

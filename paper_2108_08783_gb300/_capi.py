@@ -21,7 +21,8 @@ LBM_PROFILE_PARABOLIC, LBM_PROFILE_WOMERSLEY, LBM_PROFILE_PLUG = 0, 1, 2
 
 # Every symbol include/lbm.h and include/lbm_mlp.h declare.
 EXPORTS = (
-    "lbm_build_lattice", "lbm_set_wall_params", "lbm_init_fields", "lbm_step", "lbm_moments",
+    "lbm_build_lattice", "lbm_set_wall_params", "lbm_init_fields", "lbm_step", "lbm_step_diag",
+    "lbm_moments",
     "lbm_sync", "lbm_info", "lbm_export_lattice", "lbm_wall_state", "lbm_reduce",
     "lbm_get_populations", "lbm_set_populations", "lbm_checkpoint_bytes", "lbm_checkpoint_save",
     "lbm_checkpoint_load", "lbm_wss", "lbm_set_stream", "lbm_last_error", "lbm_status_string",
@@ -91,6 +92,7 @@ def lib():
         "lbm_set_wall_params": ([P, i32, dbl, P, P, i64], C.c_int),
         "lbm_init_fields": ([P, P, P], C.c_int),
         "lbm_step": ([P, i64], C.c_int),
+        "lbm_step_diag": ([P, i64, P], C.c_int),
         "lbm_moments": ([P, P, P, i32], C.c_int),
         "lbm_sync": ([P], C.c_int),
         "lbm_info": ([P, P], C.c_int),

@@ -78,6 +78,13 @@ struct lbm_ctx {
   cudaEvent_t fork = nullptr, join = nullptr;
   size_t ev_used = 0;
   int32_t* coords_dev = nullptr;  // [n][3] voxel coordinates, uploaded on first use (warm start)
+  // fused diagnostics (lbm_step_diag), set up on first use
+  bool diag_ready = false;
+  double* diag_part = nullptr;
+  unsigned* diag_done = nullptr;
+  double* diag_out = nullptr;
+  int64_t* diag_io_off = nullptr;
+  int64_t* diag_io_q = nullptr;
 };
 
 namespace {
@@ -467,9 +474,11 @@ int lbm_init_fields(lbm_ctx* c, const double* rho, const double* u) {
   return rc;
 }
 
-int lbm_step(lbm_ctx* c, int64_t n_steps) {
-  if (!c) return LBM_EINVAL;
-  if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps must be >= 0");
+namespace {
+
+// n_steps timesteps; with diag_last the last one also writes the fused
+// diagnostics of the state it reads.
+int run_steps(lbm_ctx* c, int64_t n_steps, bool diag_last) {
   lbm::StepParams p{};
   p.rho0 = c->rho0;
   p.rho0_f = (float)c->rho0;
@@ -484,6 +493,7 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
   for (int64_t s = 0; s < n_steps; ++s) {
     p.step = c->step;
     p.write_state = s == n_steps - 1 ? 1 : 0;
+    p.diag = diag_last && s == n_steps - 1 ? 1 : 0;
     void* ev[3] = {nullptr, nullptr, nullptr};
     if (c->prof) {
       while (c->ev.size() < c->ev_used + 3) {
@@ -504,6 +514,93 @@ int lbm_step(lbm_ctx* c, int64_t n_steps) {
 #endif
     ++c->step;
   }
+  return LBM_OK;
+}
+
+// Device tables of the fused diagnostics: the boundary tiles with sites
+// linked to iolets numbered in launch order, and per iolet the places of its
+// sites among those tiles' lanes.
+int diag_setup(lbm_ctx* c) {
+  if (c->diag_ready) return LBM_OK;
+  const HostLattice& L = c->L;
+  const int64_t nb = c->d.n_boundary;
+  const int nio = (int)c->iolets.size();
+  std::vector<int32_t> iotile((size_t)nb, -1);
+  int32_t n_io = 0;
+  for (int64_t k = 0; k < nb; ++k) {
+    bool any = false;
+    for (int l = 0; l < lbm::kTile; ++l) {
+      const size_t sl = (size_t)k * lbm::kTile + l;
+      if ((L.slot_io[sl] & lbm::kDirBits) || (L.slot_mask[sl] & lbm::kMultiIolet)) any = true;
+    }
+    if (any) iotile[(size_t)k] = n_io++;
+  }
+  std::vector<int64_t> ioff((size_t)nio + 1, 0), q;
+  for (int k = 0; k < nio; ++k) {
+    for (int64_t i = L.iolet_off[k]; i < L.iolet_off[k + 1]; ++i) {
+      const int64_t x = L.iolet_sites[(size_t)i];
+      const int32_t slot0 = L.tiles[(size_t)(x / lbm::kTile)].slot;
+      const int32_t it = slot0 >= 0 ? iotile[(size_t)(slot0 / lbm::kTile)] : -1;
+      if (it < 0) return fail(c, LBM_ESTATE, "diagnostics: an iolet site outside the iolet tiles");
+      q.push_back((int64_t)it * lbm::kTile + x % lbm::kTile);
+    }
+    ioff[(size_t)k + 1] = (int64_t)q.size();
+  }
+  const int64_t js = (int64_t)(n_io > 0 ? n_io : 1) * lbm::kTile;
+  double* mass = dev_alloc<double>(c, (size_t)c->d.n_tiles);
+  double* j = dev_alloc<double>(c, 3 * (size_t)js);
+  int32_t* it_d = dev_alloc<int32_t>(c, nb > 0 ? (size_t)nb : 1);
+  c->diag_io_off = dev_alloc<int64_t>(c, ioff.size());
+  c->diag_io_q = dev_alloc<int64_t>(c, q.empty() ? 1 : q.size());
+  c->diag_part = dev_alloc<double>(c, (size_t)lbm::diag_blocks());
+  c->diag_done = dev_alloc<unsigned>(c, 1);
+  c->diag_out = dev_alloc<double>(c, 1 + (size_t)nio);
+  if (!mass || !j || !it_d || !c->diag_io_off || !c->diag_io_q || !c->diag_part || !c->diag_done ||
+      !c->diag_out)
+    return fail(c, LBM_ENOMEM, "diagnostics: device allocation");
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  chk(h2d(c, it_d, iotile.data(), iotile.size()));
+  chk(h2d(c, c->diag_io_off, ioff.data(), ioff.size()));
+  chk(h2d(c, c->diag_io_q, q.data(), q.size()));
+  chk(cudaMemsetAsync(c->diag_done, 0, sizeof(unsigned), c->stream));
+  chk(cudaMemsetAsync(mass, 0, (size_t)c->d.n_tiles * sizeof(double), c->stream));
+  chk(cudaMemsetAsync(j, 0, 3 * (size_t)js * sizeof(double), c->stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics setup");
+  int rc = sync(c, "diagnostics setup");  // the host tables are temporaries
+  if (rc != LBM_OK) return rc;
+  c->d.diag_mass = mass;
+  c->d.diag_j = j;
+  c->d.diag_iotile = it_d;
+  c->d.diag_jstride = js;
+  c->diag_ready = true;
+  return LBM_OK;
+}
+
+}  // namespace
+
+int lbm_step(lbm_ctx* c, int64_t n_steps) {
+  if (!c) return LBM_EINVAL;
+  if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps must be >= 0");
+  return run_steps(c, n_steps, false);
+}
+
+int lbm_step_diag(lbm_ctx* c, int64_t n_steps, double* out) {
+  if (!c || !out) return LBM_EINVAL;
+  c->err.clear();
+  if (n_steps < 1) return fail(c, LBM_EINVAL, "n_steps must be >= 1");
+  int rc = diag_setup(c);
+  if (rc != LBM_OK) return rc;
+  rc = run_steps(c, n_steps, true);
+  if (rc != LBM_OK) return rc;
+  rc = check_launch(c, lbm::launch_diag_final(c->d, c->diag_io_off, c->diag_io_q, c->diag_part,
+                                              c->diag_done, c->diag_out, c->stream),
+                    "diagnostics kernel");
+  if (rc != LBM_OK) return rc;
+  const int k = (int)c->iolets.size();
+  cudaError_t e = cudaMemcpyAsync(out, c->diag_out, (1 + k) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_diag copy");
   return LBM_OK;
 }
 

@@ -145,6 +145,13 @@ struct Codec<__nv_bfloat16> {
 
 // ------------------------------------------------------------------ collision
 
+// Sum over the warp's 32 lanes in a fixed butterfly order (every lane gets it).
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
 __device__ __forceinline__ double recip(double v) { return __drcp_rn(v); }
 
@@ -408,9 +415,12 @@ __device__ __forceinline__ bool chk_site(int64_t y, int64_t n, int* err) {
 }
 
 // Branch-free update of a site whose 18 links are fluid.
+// Returns the site's rho - 1 (for the fused mass diagnostic).
 template <class S, bool ODD>
-__device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const int32_t* dsc,
-                                            typename Codec<S>::C omega, int* err, int* chk) {
+__device__ __forceinline__ typename Codec<S>::C bulk_update(S* P, int64_t np, int64_t x,
+                                                            const int32_t* dsc,
+                                                            typename Codec<S>::C omega, int* err,
+                                                            int* chk) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
   C g[kQ];
@@ -455,6 +465,7 @@ __device__ __forceinline__ void bulk_update(S* P, int64_t np, int64_t x, const i
       chk_count(chk, P, P + a * np + x, kQ * np, err);
     }
   });
+  return m.drho;
 }
 
 // --------------------------------------------------- two sites per lane
@@ -615,8 +626,8 @@ __device__ __forceinline__ void chk_count2(int* chk, const S* P0, const S* p, in
 // rather than hold 38 floats); store0(g*_0) receives the rest population and
 // store<a, b>(g*_a, g*_b) those of each opposite pair (a odd, b = a + 1).
 template <class GetM, class GetP, class St0, class St>
-__device__ __forceinline__ void collide2(GetM&& gm, GetP&& gp, F2 omega, int* err_lo,
-                                         int* err_hi, St0&& store0, St&& store) {
+__device__ __forceinline__ F2 collide2(GetM&& gm, GetP&& gp, F2 omega, int* err_lo,
+                                       int* err_hi, St0&& store0, St&& store) {
   // Eqs. (Density), (Momentum), grouped as in moments()
   F2 g[kQ];
   unroll<kQ>([&](auto J) {
@@ -676,14 +687,22 @@ __device__ __forceinline__ void collide2(GetM&& gm, GetP&& gp, F2 omega, int* er
     const F2 sb = fma2(omega, sub2(sub2(even, odd), gb), gb);
     store(std::integral_constant<int, a>{}, sa, sb);
   });
+  return drho;
+}
+
+// The sum of a packed pair's two halves.
+__device__ __forceinline__ float sum2(F2 a) {
+  float lo, hi;
+  split2(a, lo, hi);
+  return lo + hi;
 }
 
 // Branch-free update of the sites x, x + 1 (x even) whose 18 links are fluid,
 // both with the neighbour offsets dsc: one address per direction for both
 // sites, packed loads and stores where the offset is even.
 template <class S, bool ODD>
-__device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const int32_t* dsc,
-                                             float omega, int* err, int* chk) {
+__device__ __forceinline__ float bulk_update2(S* P, int64_t np, int64_t x, const int32_t* dsc,
+                                              float omega, int* err, int* chk) {
   using Cd = Codec2<S>;
   constexpr bool kPacked = sizeof(S) == 2;
   F2 g[kPacked ? 1 : kQ];
@@ -711,7 +730,7 @@ __device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const 
     if constexpr (kPacked) return Cd::unpack(opaque(r[j]));
     else return g[j];
   };
-  collide2(
+  return sum2(collide2(
       gm, gp, bc2(omega), err, err,
       [&](F2 s0) {
         Cd::st_al(P + x, s0);
@@ -735,7 +754,7 @@ __device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const 
           chk_count2(chk, P, P + b * np + x, kQ * np, err);
           chk_count2(chk, P, P + a * np + x, kQ * np, err);
         }
-      });
+      }));
 }
 
 // Branch-free update of site xa of one bulk tile and site xb of another tile of
@@ -744,7 +763,7 @@ __device__ __forceinline__ void bulk_update2(S* P, int64_t np, int64_t x, const 
 // each of its addresses is the first tile's plus one tile (an immediate
 // offset, no second address).
 template <class S, bool ODD, bool SAME>
-__device__ __forceinline__ void bulk_update2v(S* P, int64_t np, int64_t xa, int64_t xb,
+__device__ __forceinline__ float bulk_update2v(S* P, int64_t np, int64_t xa, int64_t xb,
                                               const int32_t* da, const int32_t* db, float omega,
                                               int* err, int* chk) {
   using Cd = Codec<S>;
@@ -781,7 +800,7 @@ __device__ __forceinline__ void bulk_update2v(S* P, int64_t np, int64_t xa, int6
     chk_count(chk, P, pa, kQ * np, err);
     chk_count(chk, P, pb, kQ * np, err);
   };
-  collide2(
+  return sum2(collide2(
       gm, gp, bc2(omega), err, err,
       [&](F2 s0) { put(P + xa, SAME ? P + xa + kTile : P + xb, s0, 0); },
       [&](auto A, F2 sa, F2 sb) {
@@ -799,7 +818,7 @@ __device__ __forceinline__ void bulk_update2v(S* P, int64_t np, int64_t xa, int6
           put(pk, SAME ? pk + kTile : P + k * np + xb, sa, i);
           put(pi, SAME ? pi + kTile : P + i * np + xb, sb, k);
         }
-      });
+      }));
 }
 
 // Update of a site of a boundary tile.  `code[i]` holds the tile's uniform
@@ -838,6 +857,17 @@ struct BoundaryArea {
   static constexpr int size = 25 * kTile + 5 * kTile * (int)(sizeof(double) / sizeof(C));
 };
 constexpr int kAreaIolet = 19;  // first row of the iolet states
+
+// Fused diagnostics: the momentum rho u of a site with iolet links, at its
+// place among the lanes of the tiles that have such sites, for the fluxes.
+template <class C>
+__device__ __forceinline__ void diag_momentum(const DevLattice& d, int64_t slot, const Mom<C>& m) {
+  const int64_t q = (int64_t)__ldg(d.diag_iotile + (slot >> 5)) * kTile + (slot & (kTile - 1));
+  const int64_t js = d.diag_jstride;
+  d.diag_j[q] = (double)(m.rho * m.ux);
+  d.diag_j[js + q] = (double)(m.rho * m.uy);
+  d.diag_j[2 * js + q] = (double)(m.rho * m.uz);
+}
 constexpr int kAreaSite = 25;   // first row (compute-type units) of the per-site doubles
 
 // Update of a boundary site whose iolet links (if any) all lead to one iolet,
@@ -872,7 +902,8 @@ constexpr bool opposites_adjacent() {
 static_assert(opposites_adjacent(), "opposite directions must be adjacent");
 
 template <class S, bool ODD>
-__device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepParams& p,
+__device__ __forceinline__ typename Codec<S>::C boundary_fast(const DevLattice& d,
+                                                              const StepParams& p,
                                               typename Codec<S>::C omega, S* P, int64_t x,
                                               const int32_t* offp, int ostride, uint32_t smask,
                                               uint32_t iom, const double* site,
@@ -1053,6 +1084,8 @@ __device__ __forceinline__ void boundary_fast(const DevLattice& d, const StepPar
     chk_count(d.chk, P, pa, kQ * np, d.err);
     chk_count(d.chk, P, pb, kQ * np, d.err);
   });
+  if (p.diag && (iom & kDirBits)) diag_momentum(d, slot, m);
+  return m.drho;
 }
 
 // D3Q19 vectors and weights for directions known only at run time (the
@@ -1087,7 +1120,8 @@ __device__ __forceinline__ C dir_weight(int i) {
 // per-site neighbour rows (irregular tiles on odd steps); gsm: the warp's
 // [19][32] shared-memory area where g is parked for the boundary rule.
 template <class S, bool ODD>
-__device__ __forceinline__ void boundary_update(const DevLattice& d, const StepParams& p,
+__device__ __forceinline__ typename Codec<S>::C boundary_update(const DevLattice& d,
+                                                                const StepParams& p,
                                                 typename Codec<S>::C omega, S* P,
                                                 int64_t x, const int32_t* dsc, bool irr,
                                                 uint32_t smask, uint32_t iom,
@@ -1126,8 +1160,9 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
       chk_count(d.chk, P, pi, kQ * np, d.err);
     }
   });
+  if (p.diag && ((iom & kDirBits) || (smask & kMultiIolet))) diag_momentum(d, slot, m);
   uint32_t nf = smask & kDirBits;
-  if (!nf) return;
+  if (!nf) return m.drho;
   // Elastic wall (Sec. 2.3-2.4): the tube-law expansion dE in FP64, and the
   // ratio sw = U_w/u_f = (F + dr - dx)/dr with dr = dx + dE in the compute
   // type (FP64 throughput is low on this GPU and the ratio only scales an FP32
@@ -1238,6 +1273,7 @@ __device__ __forceinline__ void boundary_update(const DevLattice& d, const StepP
       chk_count(d.chk, P, P + j * np + x, kQ * np, d.err);
     }
   }
+  return m.drho;
 }
 
 // Sites linked to two or more iolets (each non-fluid link takes its own code
@@ -1301,9 +1337,12 @@ struct EnsBulkMinBlocks {
 constexpr int kBoundaryWarps = LBM_BOUNDARY_WARPS;  // k_boundary: tiles (warps) per CTA
 
 // Bulk tile at launch position k (whole warp); dsc: the warp's 20-word area.
+// Returns the lane's rho - 1 (0 for a lane without a site).
 template <class S, bool ODD>
-__device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams& p, int64_t k,
-                                          int32_t* dsc, int lane) {
+__device__ __forceinline__ typename Codec<S>::C bulk_tile(const DevLattice& d,
+                                                          const StepParams& p, int64_t k,
+                                                          int32_t* dsc, int lane) {
+  using C = typename Codec<S>::C;
   // a warp that updates tiles in a loop (persistent kernel): every lane is done
   // with the previous tile's descriptor before it is overwritten
   __syncwarp();
@@ -1315,14 +1354,14 @@ __device__ __forceinline__ void bulk_tile(const DevLattice& d, const StepParams&
   }
   __syncwarp();
   const int64_t x = (int64_t)dsc[19] * kTile + lane;
-  if (x >= d.n) return;
+  if (x >= d.n) return C(0);
   if constexpr (kChecked && ODD) {
     bool ok = true;
     for (int o = 0; o < 18; ++o) ok = chk_site(x + dsc[o], d.n, d.err) && ok;
-    if (!ok) return;
+    if (!ok) return C(0);
   }
-  bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc,
-                      omega_as<typename Codec<S>::C>(p.omega, p.omega_f), d.err, d.chk);
+  return bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc,
+                             omega_as<C>(p.omega, p.omega_f), d.err, d.chk);
 }
 
 
@@ -1351,7 +1390,7 @@ __device__ __forceinline__ BulkView bulk_view(const DevLattice& d) {
 //     same offsets).
 // A site without a partner takes the single-site update.
 template <class S, bool ODD, bool VERT>
-__device__ __forceinline__ void bulk_pair_warp(const BulkView& dA, int64_t kA, float omA,
+__device__ __forceinline__ float bulk_pair_warp(const BulkView& dA, int64_t kA, float omA,
                                                const BulkView& dB, int64_t kB, float omB,
                                                bool two, bool one_lattice, int64_t prefetch,
                                                int32_t (*dsc2)[20], int lane) {
@@ -1374,7 +1413,7 @@ __device__ __forceinline__ void bulk_pair_warp(const BulkView& dA, int64_t kA, f
   __syncwarp();
   if constexpr (!VERT) {
     const int half = lane >> 4;
-    if (half && !two) return;
+    if (half && !two) return 0.0f;
     // this half's lattice, field by field (no reference chosen at run time)
     S* P = static_cast<S*>(half ? dB.pop : dA.pop);
     const int64_t np = half ? dB.npad : dA.npad, n = half ? dB.n : dA.n;
@@ -1382,25 +1421,25 @@ __device__ __forceinline__ void bulk_pair_warp(const BulkView& dA, int64_t kA, f
     int* chk = half ? dB.chk : dA.chk;
     const int32_t* dsc = dsc2[half];
     const int64_t x = (int64_t)dsc[19] * kTile + 2 * (lane & 15);
-    if (x >= n) return;
+    if (x >= n) return 0.0f;
     if constexpr (kChecked && ODD) {
       bool ok = true;
       for (int o = 0; o < 18; ++o) ok = chk_site(x + dsc[o], n, err) && ok;
       if (x + 1 < n)
         for (int o = 0; o < 18; ++o) ok = chk_site(x + 1 + dsc[o], n, err) && ok;
-      if (!ok) return;
+      if (!ok) return 0.0f;
     }
     // a bulk tile is never the ragged last tile (its last site has a +x link
     // out of the fluid), so x + 1 < n; the guard keeps the update in bounds
-    if (x + 1 < n) bulk_update2<S, ODD>(P, np, x, dsc, half ? omB : omA, err, chk);
-    else bulk_update<S, ODD>(P, np, x, dsc, half ? omB : omA, err, chk);
+    if (x + 1 < n) return bulk_update2<S, ODD>(P, np, x, dsc, half ? omB : omA, err, chk);
+    return bulk_update<S, ODD>(P, np, x, dsc, half ? omB : omA, err, chk);
   } else {
     const int32_t* da = dsc2[0];
     const int64_t xa = (int64_t)da[19] * kTile + lane;
     S* PA = static_cast<S*>(dA.pop);
     if (!two) {
-      if (xa < dA.n) bulk_update<S, ODD>(PA, dA.npad, xa, da, omA, dA.err, dA.chk);
-      return;
+      if (xa < dA.n) return bulk_update<S, ODD>(PA, dA.npad, xa, da, omA, dA.err, dA.chk);
+      return 0.0f;
     }
     const int32_t* db = dsc2[1];
     const int64_t xb = (int64_t)db[19] * kTile + lane;
@@ -1408,9 +1447,10 @@ __device__ __forceinline__ void bulk_pair_warp(const BulkView& dA, int64_t kA, f
       // the two tiles belong to different members of an ensemble (or a site
       // has no partner, not reached for bulk tiles): one site at a time
       S* PB = static_cast<S*>(dB.pop);
-      if (xa < dA.n) bulk_update<S, ODD>(PA, dA.npad, xa, da, omA, dA.err, dA.chk);
-      if (xb < dB.n) bulk_update<S, ODD>(PB, dB.npad, xb, db, omB, dB.err, dB.chk);
-      return;
+      float r = 0.0f;
+      if (xa < dA.n) r += bulk_update<S, ODD>(PA, dA.npad, xa, da, omA, dA.err, dA.chk);
+      if (xb < dB.n) r += bulk_update<S, ODD>(PB, dB.npad, xb, db, omB, dB.err, dB.chk);
+      return r;
     }
     // B directly follows A with the same offsets (warp-uniform)
     const bool same = __all_sync(
@@ -1419,16 +1459,18 @@ __device__ __forceinline__ void bulk_pair_warp(const BulkView& dA, int64_t kA, f
       bool ok = true;
       for (int o = 0; o < 18; ++o)
         ok = chk_site(xa + da[o], dA.n, dA.err) && chk_site(xb + db[o], dA.n, dA.err) && ok;
-      if (!ok) return;
+      if (!ok) return 0.0f;
     }
-    if (same) bulk_update2v<S, ODD, true>(PA, dA.npad, xa, xb, da, db, omA, dA.err, dA.chk);
-    else bulk_update2v<S, ODD, false>(PA, dA.npad, xa, xb, da, db, omA, dA.err, dA.chk);
+    if (same) return bulk_update2v<S, ODD, true>(PA, dA.npad, xa, xb, da, db, omA, dA.err, dA.chk);
+    return bulk_update2v<S, ODD, false>(PA, dA.npad, xa, xb, da, db, omA, dA.err, dA.chk);
   }
 }
 
 // Bulk tiles of one lattice, two per warp (warp w of block b: the bulk tiles
 // at launch positions n_boundary + 2 (b W + w) and the one after it).
-template <class S, bool ODD, bool VERT, int W>
+// DIAG: also write the tiles' sums of rho - 1 (fused diagnostics), a separate
+// instantiation so that ordinary steps keep their registers.
+template <class S, bool ODD, bool VERT, int W, bool DIAG = false>
 __global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::two)
     k_bulk2(const DevLattice d, const StepParams p) {
   __shared__ __align__(16) int32_t desc_s[W][2][20];
@@ -1436,18 +1478,29 @@ __global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::two)
   const int64_t k0 = d.n_boundary + 2 * ((int64_t)blockIdx.x * W + w);
   if (k0 >= d.n_tiles) return;  // warp-uniform
   const BulkView v = bulk_view(d);
-  bulk_pair_warp<S, ODD, VERT>(v, k0, p.omega_f, v, k0 + 1, p.omega_f, k0 + 1 < d.n_tiles, true,
-                               p.prefetch, desc_s[w], lane);
+  const bool two = k0 + 1 < d.n_tiles;
+  const float dr = bulk_pair_warp<S, ODD, VERT>(v, k0, p.omega_f, v, k0 + 1, p.omega_f, two, true,
+                                                p.prefetch, desc_s[w], lane);
+  if constexpr (DIAG) {
+    // the two tiles' mass under the first one's launch position
+    const float m = warp_sum(dr);
+    if (lane == 0) d.diag_mass[k0] = (double)m;
+    if (lane == 1 && two) d.diag_mass[k0 + 1] = 0.0;
+  }
 }
 
-template <class S, bool ODD, int W>
+template <class S, bool ODD, int W, bool DIAG = false>
 __global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::one)
     k_bulk(const DevLattice d, const StepParams p) {
   __shared__ __align__(16) int32_t desc_s[W][20];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k = d.n_boundary + (int64_t)blockIdx.x * W + w;
   if (k >= d.n_tiles) return;  // warp-uniform
-  bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
+  const auto dr = bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
+  if constexpr (DIAG) {
+    const auto m = warp_sum(dr);
+    if (lane == 0) d.diag_mass[k] = (double)m;
+  }
 }
 
 // Resident CTAs (4 warps) per SM requested of the boundary kernel: 7, i.e. 73
@@ -1468,7 +1521,8 @@ template <class S, bool ODD, int PART = 0>
 __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepParams& p, int64_t k,
                                               int32_t* dsc, int32_t* nbr_s, uint64_t* bar,
                                               typename Codec<S>::C* gsm, int lane,
-                                              uint32_t* bar_phase = nullptr) {
+                                              uint32_t* bar_phase = nullptr,
+                                              typename Codec<S>::C* dr = nullptr) {
   using C = typename Codec<S>::C;
   // a warp that updates tiles in a loop (persistent kernel): lanes that left
   // the previous tile early (padding sites) wait here until every lane is done
@@ -1569,8 +1623,10 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
         offp = nbr_s + lane;
         ostride = kTile;
       }
-      boundary_fast<S, ODD>(d, p, omega_as<C>(p.omega, p.omega_f), P, x, offp, ostride, smask,
-                            iom, site, nbr_s, lane, slot, warp_io, warp_wall, warp_nf, gsm);
+      const C r = boundary_fast<S, ODD>(d, p, omega_as<C>(p.omega, p.omega_f), P, x, offp,
+                                        ostride, smask, iom, site, nbr_s, lane, slot, warp_io,
+                                        warp_wall, warp_nf, gsm);
+      if (dr) *dr = r;
     }
     return true;
   }
@@ -1582,8 +1638,10 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
   if constexpr (PART == 1) {
     C g[kQ];
     boundary_load<S, ODD>(P, d.npad, x, smask & kDirBits, dsc, irr, nbr_s, lane, g, d.n, d.err);
-    boundary_update<S, ODD>(d, p, omega_as<C>(p.omega, p.omega_f), P, x, dsc, irr, smask, iom,
-                            Fw, Kw, pr0, pr1, pr2, nbr_s, lane, slot, g, gsm);
+    const C r = boundary_update<S, ODD>(d, p, omega_as<C>(p.omega, p.omega_f), P, x, dsc, irr,
+                                        smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s, lane, slot, g,
+                                        gsm);
+    if (dr) *dr = r;
   } else {
     boundary_slow<S, ODD>(d, p, P, x, dsc, irr, smask, iom, Fw, Kw, pr0, pr1, pr2, nbr_s, lane,
                           slot, gsm);
@@ -1591,9 +1649,11 @@ __device__ __forceinline__ bool boundary_tile(const DevLattice& d, const StepPar
   return true;
 }
 
-template <class S, bool ODD>
+template <class S, bool ODD, bool DIAG = false>
 __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_BOUNDARY_MINB)
-    k_boundary(const DevLattice d, const StepParams p) {
+    k_boundary(const DevLattice d, const StepParams p0) {
+  StepParams p = p0;
+  p.diag = DIAG;  // a compile-time constant for the tile code
   using C = typename Codec<S>::C;
   __shared__ __align__(128) int32_t stage[kBoundaryWarps][18 * kTile];
   __shared__ __align__(16) C gs[kBoundaryWarps][BoundaryArea<C>::size];
@@ -1602,15 +1662,22 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k = (int64_t)blockIdx.x * kBoundaryWarps + w;
   if (k >= d.n_boundary) return;  // warp-uniform
-  boundary_tile<S, ODD>(d, p, k, desc_s[w], stage[w], &bars[w], gs[w], lane);
+  C dr = C(0);
+  boundary_tile<S, ODD>(d, p, k, desc_s[w], stage[w], &bars[w], gs[w], lane, nullptr, &dr);
+  if constexpr (DIAG) {
+    const C m = warp_sum(dr);
+    if (lane == 0) d.diag_mass[k] = (double)m;
+  }
 }
 
 // The sites linked to two or more iolets, over the boundary tiles that have
 // such sites (d.multi_tiles); every other site of those tiles is left to
 // k_boundary.
-template <class S, bool ODD>
+template <class S, bool ODD, bool DIAG = false>
 __global__ void __launch_bounds__(kBoundaryWarps * 32)
-    k_boundary_multi(const DevLattice d, const StepParams p) {
+    k_boundary_multi(const DevLattice d, const StepParams p0) {
+  StepParams p = p0;
+  p.diag = DIAG;
   using C = typename Codec<S>::C;
   __shared__ __align__(128) int32_t stage[kBoundaryWarps][18 * kTile];
   __shared__ __align__(16) C gs[kBoundaryWarps][BoundaryArea<C>::size];
@@ -1619,8 +1686,14 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32)
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t q = (int64_t)blockIdx.x * kBoundaryWarps + w;
   if (q >= d.n_multi) return;  // warp-uniform
-  boundary_tile<S, ODD, 1>(d, p, __ldg(d.multi_tiles + q), desc_s[w], stage[w], &bars[w], gs[w],
-                           lane);
+  const int64_t k = __ldg(d.multi_tiles + q);
+  C dr = C(0);
+  boundary_tile<S, ODD, 1>(d, p, k, desc_s[w], stage[w], &bars[w], gs[w], lane, nullptr, &dr);
+  if constexpr (DIAG) {
+    // after k_boundary (same stream) wrote the tile's other sites
+    const C m = warp_sum(dr);
+    if (lane == 0) d.diag_mass[k] += (double)m;
+  }
 }
 
 // -------------------------------------------------------------- ensembles
@@ -1697,6 +1770,7 @@ __global__ void __launch_bounds__(kBoundaryWarps * 32, sizeof(S) == 8 ? 2 : LBM_
   pm.rho0 = md.rho0;
   pm.rho0_f = md.rho0_f;
   pm.rho0_exact = md.rho0_exact;
+  pm.diag = 0;  // ensembles: no fused diagnostics
   pm.elastic = md.elastic;
   boundary_tile<S, ODD>(md.d, pm, t.k, desc_s[w], stage[w], &bars[w], gs[w], lane);
 }
@@ -1805,6 +1879,7 @@ __global__ void __launch_bounds__(kPersistWarps * 32, sizeof(S) == 8 ? 1 : 4)
           pm.rho0 = md.rho0;
           pm.rho0_f = md.rho0_f;
           pm.rho0_exact = md.rho0_exact;
+          pm.diag = 0;  // ensembles: no fused diagnostics
           pm.elastic = md.elastic;
           const int64_t k = tr.k;
           const bool ok = odd ? persist_boundary<S, true>(md.d, pm, k, desc_s[w], stage[w],
@@ -2048,6 +2123,56 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
+// Fused diagnostics, the final sums in a fixed order: blocks [0, kDiagBlocks)
+// add contiguous ranges of the per-tile partials of rho - 1 and the last of
+// them to finish adds the block sums in block order (total mass = n plus
+// that sum); block kDiagBlocks + k adds iolet k's flux, (rho u) . axis over
+// the sites with a link into it (io_q: their places in diag_j).
+constexpr int kDiagBlocks = 128;
+__global__ void __launch_bounds__(kRedThreads)
+    k_diag_final(const DevLattice d, const int64_t* io_off, const int64_t* io_q, double* part,
+                 unsigned* done, double* out) {
+  __shared__ double sh[kRedThreads];
+  __shared__ int last;
+  const int b = blockIdx.x;
+  if (b < kDiagBlocks) {
+    const int64_t per = (d.n_tiles + kDiagBlocks - 1) / kDiagBlocks;
+    const int64_t lo = (int64_t)b * per;
+    const int64_t hi = lo + per < d.n_tiles ? lo + per : d.n_tiles;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) acc += d.diag_mass[i];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+      part[b] = s;
+      __threadfence();
+      last = atomicAdd(done, 1u) == kDiagBlocks - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last) return;  // block-uniform
+    __threadfence();
+    double a = 0.0;
+    for (int i = threadIdx.x; i < kDiagBlocks; i += kRedThreads) a += __ldcg(part + i);
+    const double t = block_sum(a, sh);
+    if (threadIdx.x == 0) {
+      out[0] = (double)d.n + t;
+      if (!isfinite(t)) atomicOr(d.err, kErrUnstable);
+      *done = 0;  // for the next diagnostic step (stream order)
+    }
+  } else {
+    const int k = b - kDiagBlocks;
+    const IoletDev& io = d.iolets[k];
+    const int64_t js = d.diag_jstride;
+    double acc = 0.0;
+    for (int64_t q = io_off[k] + threadIdx.x; q < io_off[k + 1]; q += kRedThreads) {
+      const int64_t j = io_q[q];
+      acc += d.diag_j[j] * io.axis[0] + d.diag_j[js + j] * io.axis[1] +
+             d.diag_j[2 * js + j] * io.axis[2];
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[1 + k] = s;
+  }
+}
+
 __global__ void k_flux_final(const double* part, int bpi, double* out) {
   if (threadIdx.x != 0) return;
   double s = 0.0;
@@ -2096,8 +2221,13 @@ template <class S>
 void launch_multi(const DevLattice& d, const StepParams& p, bool odd, cudaStream_t s) {
   if (d.n_multi <= 0) return;
   const unsigned nb = (unsigned)((d.n_multi + kBoundaryWarps - 1) / kBoundaryWarps);
-  if (odd) k_boundary_multi<S, true><<<nb, kBoundaryWarps * 32, 0, s>>>(d, p);
-  else k_boundary_multi<S, false><<<nb, kBoundaryWarps * 32, 0, s>>>(d, p);
+  if (p.diag) {
+    if (odd) k_boundary_multi<S, true, true><<<nb, kBoundaryWarps * 32, 0, s>>>(d, p);
+    else k_boundary_multi<S, false, true><<<nb, kBoundaryWarps * 32, 0, s>>>(d, p);
+  } else {
+    if (odd) k_boundary_multi<S, true><<<nb, kBoundaryWarps * 32, 0, s>>>(d, p);
+    else k_boundary_multi<S, false><<<nb, kBoundaryWarps * 32, 0, s>>>(d, p);
+  }
 }
 
 // Pairing of the bulk kernel's two sites per lane for this step's parity
@@ -2113,24 +2243,24 @@ inline int bulk_pairing(int32_t bulk_sites, bool odd) {
 }
 
 // The bulk kernel of one step with W warps per CTA (pairing: bulk_pairing).
-template <class S, int W>
+template <class S, int W, bool DIAG = false>
 void launch_bulk(const DevLattice& d, const StepParams& p, bool odd, int pairing, int64_t tiles,
                  cudaStream_t m) {
   if (pairing) {
     const unsigned nb = (unsigned)((tiles + 2 * W - 1) / (2 * W));
     if constexpr (sizeof(S) < 8) {
       if (pairing == 1) {
-        if (odd) k_bulk2<S, true, false, W><<<nb, W * 32, 0, m>>>(d, p);
-        else k_bulk2<S, false, false, W><<<nb, W * 32, 0, m>>>(d, p);
+        if (odd) k_bulk2<S, true, false, W, DIAG><<<nb, W * 32, 0, m>>>(d, p);
+        else k_bulk2<S, false, false, W, DIAG><<<nb, W * 32, 0, m>>>(d, p);
       } else {
-        if (odd) k_bulk2<S, true, true, W><<<nb, W * 32, 0, m>>>(d, p);
-        else k_bulk2<S, false, true, W><<<nb, W * 32, 0, m>>>(d, p);
+        if (odd) k_bulk2<S, true, true, W, DIAG><<<nb, W * 32, 0, m>>>(d, p);
+        else k_bulk2<S, false, true, W, DIAG><<<nb, W * 32, 0, m>>>(d, p);
       }
     }
   } else {
     const unsigned nb = (unsigned)((tiles + W - 1) / W);
-    if (odd) k_bulk<S, true, W><<<nb, W * 32, 0, m>>>(d, p);
-    else k_bulk<S, false, W><<<nb, W * 32, 0, m>>>(d, p);
+    if (odd) k_bulk<S, true, W, DIAG><<<nb, W * 32, 0, m>>>(d, p);
+    else k_bulk<S, false, W, DIAG><<<nb, W * 32, 0, m>>>(d, p);
   }
 }
 template <class S, int W>
@@ -2168,13 +2298,20 @@ int step_t(const DevLattice& d, const StepParams& p, const StepStreams& ss, void
   if (nbnd) {
     cudaEventRecord((cudaEvent_t)ss.fork, m);
     cudaStreamWaitEvent(side, (cudaEvent_t)ss.fork, 0);
-    if (odd) k_boundary<S, true><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
-    else k_boundary<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
+    if (p.diag) {
+      if (odd) k_boundary<S, true, true><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
+      else k_boundary<S, false, true><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
+    } else {
+      if (odd) k_boundary<S, true><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
+      else k_boundary<S, false><<<nbnd, kBoundaryWarps * 32, 0, side>>>(d, p);
+    }
     launch_multi<S>(d, p, odd, side);
   }
   if (nbulk_tiles > 0) {
     const int pairing = sizeof(S) < 8 ? bulk_pairing(p.bulk_sites, odd) : 0;
-    if (p.bulk_warps == 8) launch_bulk<S, 8>(d, p, odd, pairing, nbulk_tiles, m);
+    // diagnostic steps take CTAs of 4 warps whatever the knob (same results)
+    if (p.diag) launch_bulk<S, 4, true>(d, p, odd, pairing, nbulk_tiles, m);
+    else if (p.bulk_warps == 8) launch_bulk<S, 8>(d, p, odd, pairing, nbulk_tiles, m);
     else launch_bulk<S, 4>(d, p, odd, pairing, nbulk_tiles, m);
   }
   if (ev) cudaEventRecord((cudaEvent_t)ev[1], m);
@@ -2237,6 +2374,7 @@ int ensemble_step_t(const EnsembleLaunch& e, const StepParams& p, const StepStre
       pm.rho0 = md.rho0;
       pm.rho0_f = md.rho0_f;
       pm.rho0_exact = md.rho0_exact;
+      pm.diag = 0;  // ensembles: no fused diagnostics
       pm.elastic = md.elastic;
       launch_multi<S>(md.d, pm, odd, side);
     }
@@ -2340,6 +2478,14 @@ int launch_reduce(int storage, const DevLattice& d, int odd, const int64_t* off,
     return (int)cudaGetLastError();
   });
 }
+
+int launch_diag_final(const DevLattice& d, const int64_t* io_off, const int64_t* io_q,
+                      double* part, unsigned* done, double* out, void* stream) {
+  k_diag_final<<<kDiagBlocks + d.n_iolets, kRedThreads, 0, (cudaStream_t)stream>>>(
+      d, io_off, io_q, part, done, out);
+  return (int)cudaGetLastError();
+}
+int diag_blocks() { return kDiagBlocks; }
 
 int launch_wss(int storage, const DevLattice& d, int odd, double tau, const int64_t* sites,
                const double* normals, int64_t m, double* out, void* stream) {

@@ -187,6 +187,14 @@ struct DevLattice {
   const int32_t* seg_tab = nullptr;      // [n_boundary][kSegWords] (segmented irregular tiles)
   const int32_t* multi_tiles = nullptr;  // boundary tiles with multi-iolet sites
   int64_t n_multi = 0;
+  // fused diagnostics (steps with StepParams::diag): per launch position the
+  // tile's sum of rho - 1 over its sites; the momentum rho u of every lane of
+  // the boundary tiles that have sites with iolet links, [3][diag_jstride],
+  // the tile at boundary position k at lanes 32 diag_iotile[k] + (0..31)
+  double* diag_mass = nullptr;
+  double* diag_j = nullptr;
+  const int32_t* diag_iotile = nullptr;  // [n_boundary], -1: no iolet links
+  int64_t diag_jstride = 0;
 };
 
 struct StepParams {
@@ -203,6 +211,8 @@ struct StepParams {
   const int64_t* step_dev;  // device step counter (captured graphs), or NULL
   int32_t bulk_sites;       // bulk kernel mode (LBM_TUNE_BULK_SITES)
   int32_t bulk_warps;       // warps per CTA of the bulk kernel: 4 or 8
+  int32_t diag;             // 1: the step kernels also write the fused diagnostics
+  int32_t pad1;
 };
 
 // One member of an ensemble: its device view and its wall constants.
@@ -285,6 +295,11 @@ int launch_wss(int storage, const DevLattice& d, int odd_layout, double tau,
                const int64_t* sites, const double* normals, int64_t m, double* out,
                void* stream);
 size_t storage_bytes(int storage);
+// Fused diagnostics: the final sums of a step run with StepParams::diag into
+// out[1 + n_iolets] (part: diag_blocks() doubles; done: a zeroed counter).
+int launch_diag_final(const DevLattice& d, const int64_t* io_off, const int64_t* io_q,
+                      double* part, unsigned* done, double* out, void* stream);
+int diag_blocks();
 // Checked builds: flag every population slot not stored exactly once since the
 // last call (padding slots: never), then clear the counts.
 int launch_check_counts(const DevLattice& d, void* stream);

@@ -150,6 +150,15 @@ class Lattice:
     def step(self, n=1):
         self._check(self._lib.lbm_step(self.h, int(n)))
 
+    def step_diag(self, n=1, out=None):
+        """``lbm_step_diag``: n steps, the last of which also reduces the mass and
+        iolet fluxes of the state it reads into ``out`` (float64 [1 + n_iolets],
+        complete after the next sync)."""
+        if out is None:
+            out = np.zeros(1 + self.n_iolets)
+        self._check(self._lib.lbm_step_diag(self.h, int(n), _ptr(out)))
+        return out
+
     def sync(self):
         self._check(self._lib.lbm_sync(self.h))
 
