@@ -145,9 +145,12 @@ int lbm_step(lbm_ctx *ctx, int64_t n_steps);
  * per 32 sites) and write the momenta of the iolet sites; one more kernel adds
  * those in FP64 in a fixed order, so no extra pass over the populations is
  * made (Sec. 2.1 moments; the mass and flux sums of the benchmark contract).
- * out is a host array [1 + n_iolets]; the copy into it is queued on the
- * context's stream and complete after the next synchronizing call
- * (lbm_sync); page-locked memory keeps the call from waiting.  The first call
+ * out is a host array [1 + n_iolets].  The final sums and the copy into out
+ * run on a stream of the library's own, ordered after this step and beside
+ * the steps queued after it (two buffer sets used in turn); they are
+ * complete after the next call that waits (lbm_sync, lbm_reduce,
+ * lbm_moments to host memory, ...); page-locked memory keeps the copy
+ * asynchronous.  The first call
  * allocates the device tables (a double per tile, three doubles per lane
  * of the tiles with iolet sites).  Errors: LBM_EINVAL (n_steps < 1, NULL
  * arguments), LBM_ENOMEM, LBM_ECUDA. */

@@ -78,13 +78,24 @@ struct lbm_ctx {
   cudaEvent_t fork = nullptr, join = nullptr;
   size_t ev_used = 0;
   int32_t* coords_dev = nullptr;  // [n][3] voxel coordinates, uploaded on first use (warm start)
-  // fused diagnostics (lbm_step_diag), set up on first use
+  // fused diagnostics (lbm_step_diag), set up on first use: kDiagSets sets
+  // of buffers used in turn, so that the final sums and the copy to the host
+  // of one diagnostic step run on their own (high-priority) stream beside the
+  // next steps
+  static constexpr int kDiagSets = 4;
   bool diag_ready = false;
-  double* diag_part = nullptr;
-  unsigned* diag_done = nullptr;
-  double* diag_out = nullptr;
+  double* diag_mass[kDiagSets] = {};
+  double* diag_j[kDiagSets] = {};
+  double* diag_part[kDiagSets] = {};
+  unsigned* diag_done[kDiagSets] = {};
+  double* diag_out[kDiagSets] = {};
   int64_t* diag_io_off = nullptr;
   int64_t* diag_io_q = nullptr;
+  cudaStream_t diag_stream = nullptr;
+  cudaEvent_t diag_filled[kDiagSets] = {};  // main stream: the step kernels wrote set b
+  cudaEvent_t diag_free[kDiagSets] = {};    // diagnostic stream: set b copied out
+  bool diag_used[kDiagSets] = {};
+  int64_t diag_seq = 0;
 };
 
 namespace {
@@ -156,6 +167,7 @@ int check_launch(lbm_ctx* c, int rc, const char* what) {
 
 int sync(lbm_ctx* c, const char* what) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && c->diag_stream) e = cudaStreamSynchronize(c->diag_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, what);
   return LBM_OK;
 }
@@ -186,11 +198,17 @@ void lbm_destroy(lbm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   if (c->side) cudaStreamSynchronize(c->side);
+  if (c->diag_stream) cudaStreamSynchronize(c->diag_stream);
   for (void* p : c->owned) dev_free_raw(c, p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
   if (c->side) cudaStreamDestroy(c->side);
+  for (int b = 0; b < lbm_ctx::kDiagSets; ++b) {
+    if (c->diag_filled[b]) cudaEventDestroy(c->diag_filled[b]);
+    if (c->diag_free[b]) cudaEventDestroy(c->diag_free[b]);
+  }
+  if (c->diag_stream) cudaStreamDestroy(c->diag_stream);
   delete c;
 }
 
@@ -547,30 +565,45 @@ int diag_setup(lbm_ctx* c) {
     ioff[(size_t)k + 1] = (int64_t)q.size();
   }
   const int64_t js = (int64_t)(n_io > 0 ? n_io : 1) * lbm::kTile;
-  double* mass = dev_alloc<double>(c, (size_t)c->d.n_tiles);
-  double* j = dev_alloc<double>(c, 3 * (size_t)js);
   int32_t* it_d = dev_alloc<int32_t>(c, nb > 0 ? (size_t)nb : 1);
   c->diag_io_off = dev_alloc<int64_t>(c, ioff.size());
   c->diag_io_q = dev_alloc<int64_t>(c, q.empty() ? 1 : q.size());
-  c->diag_part = dev_alloc<double>(c, (size_t)lbm::diag_blocks());
-  c->diag_done = dev_alloc<unsigned>(c, 1);
-  c->diag_out = dev_alloc<double>(c, 1 + (size_t)nio);
-  if (!mass || !j || !it_d || !c->diag_io_off || !c->diag_io_q || !c->diag_part || !c->diag_done ||
-      !c->diag_out)
-    return fail(c, LBM_ENOMEM, "diagnostics: device allocation");
+  bool ok = it_d && c->diag_io_off && c->diag_io_q;
+  for (int b = 0; b < lbm_ctx::kDiagSets; ++b) {
+    c->diag_mass[b] = dev_alloc<double>(c, (size_t)c->d.n_tiles);
+    c->diag_j[b] = dev_alloc<double>(c, 3 * (size_t)js);
+    c->diag_part[b] = dev_alloc<double>(c, (size_t)lbm::diag_blocks());
+    c->diag_done[b] = dev_alloc<unsigned>(c, 1);
+    c->diag_out[b] = dev_alloc<double>(c, 1 + (size_t)nio);
+    ok = ok && c->diag_mass[b] && c->diag_j[b] && c->diag_part[b] && c->diag_done[b] &&
+         c->diag_out[b];
+  }
+  if (!ok) return fail(c, LBM_ENOMEM, "diagnostics: device allocation");
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   chk(h2d(c, it_d, iotile.data(), iotile.size()));
   chk(h2d(c, c->diag_io_off, ioff.data(), ioff.size()));
   chk(h2d(c, c->diag_io_q, q.data(), q.size()));
-  chk(cudaMemsetAsync(c->diag_done, 0, sizeof(unsigned), c->stream));
-  chk(cudaMemsetAsync(mass, 0, (size_t)c->d.n_tiles * sizeof(double), c->stream));
-  chk(cudaMemsetAsync(j, 0, 3 * (size_t)js * sizeof(double), c->stream));
+  for (int b = 0; b < lbm_ctx::kDiagSets; ++b) {
+    chk(cudaMemsetAsync(c->diag_done[b], 0, sizeof(unsigned), c->stream));
+    chk(cudaMemsetAsync(c->diag_mass[b], 0, (size_t)c->d.n_tiles * sizeof(double), c->stream));
+    chk(cudaMemsetAsync(c->diag_j[b], 0, 3 * (size_t)js * sizeof(double), c->stream));
+  }
+  if (e == cudaSuccess && !c->diag_stream) {
+    // highest priority: its few blocks start ahead of the next bulk kernel's
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess)
+      e = cudaStreamCreateWithPriority(&c->diag_stream, cudaStreamNonBlocking, hi);
+  }
+  for (int b = 0; b < lbm_ctx::kDiagSets && e == cudaSuccess; ++b) {
+    if (!c->diag_filled[b]) e = cudaEventCreateWithFlags(&c->diag_filled[b], cudaEventDisableTiming);
+    if (e == cudaSuccess && !c->diag_free[b])
+      e = cudaEventCreateWithFlags(&c->diag_free[b], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics setup");
   int rc = sync(c, "diagnostics setup");  // the host tables are temporaries
   if (rc != LBM_OK) return rc;
-  c->d.diag_mass = mass;
-  c->d.diag_j = j;
   c->d.diag_iotile = it_d;
   c->d.diag_jstride = js;
   c->diag_ready = true;
@@ -591,16 +624,31 @@ int lbm_step_diag(lbm_ctx* c, int64_t n_steps, double* out) {
   if (n_steps < 1) return fail(c, LBM_EINVAL, "n_steps must be >= 1");
   int rc = diag_setup(c);
   if (rc != LBM_OK) return rc;
+  // buffer set b: its previous final sums and copy are done before the step
+  // kernels write it again (normally long since)
+  const int b = (int)(c->diag_seq % lbm_ctx::kDiagSets);
+  cudaError_t e = cudaSuccess;
+  if (c->diag_used[b]) e = cudaStreamWaitEvent(c->stream, c->diag_free[b], 0);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_diag order");
+  c->d.diag_mass = c->diag_mass[b];
+  c->d.diag_j = c->diag_j[b];
   rc = run_steps(c, n_steps, true);
   if (rc != LBM_OK) return rc;
-  rc = check_launch(c, lbm::launch_diag_final(c->d, c->diag_io_off, c->diag_io_q, c->diag_part,
-                                              c->diag_done, c->diag_out, c->stream),
+  // final sums and the copy out on the diagnostic stream, beside later steps
+  e = cudaEventRecord(c->diag_filled[b], c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->diag_stream, c->diag_filled[b], 0);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_diag order");
+  rc = check_launch(c, lbm::launch_diag_final(c->d, c->diag_io_off, c->diag_io_q, c->diag_part[b],
+                                              c->diag_done[b], c->diag_out[b], c->diag_stream),
                     "diagnostics kernel");
   if (rc != LBM_OK) return rc;
   const int k = (int)c->iolets.size();
-  cudaError_t e = cudaMemcpyAsync(out, c->diag_out, (1 + k) * sizeof(double),
-                                  cudaMemcpyDeviceToHost, c->stream);
+  e = cudaMemcpyAsync(out, c->diag_out[b], (1 + k) * sizeof(double), cudaMemcpyDeviceToHost,
+                      c->diag_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(c->diag_free[b], c->diag_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_diag copy");
+  c->diag_used[b] = true;
+  ++c->diag_seq;
   return LBM_OK;
 }
 
