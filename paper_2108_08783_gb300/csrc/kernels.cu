@@ -1961,18 +1961,23 @@ __device__ __forceinline__ int64_t slot_of(const DevLattice& d, int64_t x, int j
   return o * d.npad + nb[o];
 }
 
+// f = f^eq(rho, u) (Eq. feq) at every site, stored as g^eq = f^eq - w in
+// the compute type (FP64 storage: FP64; else FP32, which the FP32 collision
+// would round to anyway, and no FP64 arithmetic on the slow FP64 pipe).
 template <class S>
 __global__ void k_init(const DevLattice d, const double* rho, const double* u) {
+  using C = typename Codec<S>::C;
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= d.n) return;
   const double r = rho ? rho[x] : 1.0;
-  const double ux = u ? u[3 * x] : 0.0, uy = u ? u[3 * x + 1] : 0.0, uz = u ? u[3 * x + 2] : 0.0;
-  const double usq = 1.5 * (ux * ux + uy * uy + uz * uz);
+  const C dr = C(r - 1.0), rc = C(r);
+  const C ux = u ? C(u[3 * x]) : C(0), uy = u ? C(u[3 * x + 1]) : C(0);
+  const C uz = u ? C(u[3 * x + 2]) : C(0);
+  const C usq = C(1.5) * (ux * ux + uy * uy + uz * uz);
   S* P = static_cast<S*>(d.pop);
   unroll<kQ>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    // f^eq (Eq. feq) = w_i + g^eq_i; the shifted part is stored directly
-    Codec<S>::st_init(P + i * d.npad + x, geq<i, double>(r - 1.0, r, ux, uy, uz, usq));
+    Codec<S>::st(P + i * d.npad + x, i, geq<i, C>(dr, rc, ux, uy, uz, usq));
   });
 }
 
@@ -2017,18 +2022,38 @@ __device__ void f_moments(const double (&f)[kQ], double& rho, double& jx, double
   }
 }
 
+// rho, u of every site (Eqs. Density, Momentum), canonical order.  FP64
+// storage: in FP64 from f; the other storages: from the stored g in the
+// compute type, as the step kernels form them (rho = 1 + sum g in FP64).
 template <class S>
 __global__ void k_moments(const DevLattice d, int odd, double* rho, double* u) {
+  using C = typename Codec<S>::C;
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= d.n) return;
-  double f[kQ], r, jx, jy, jz;
-  site_f<S>(d, x, odd, f);
-  f_moments(f, r, jx, jy, jz);
-  if (rho) rho[x] = r;
-  if (u) {
-    u[3 * x] = jx / r;
-    u[3 * x + 1] = jy / r;
-    u[3 * x + 2] = jz / r;
+  if constexpr (std::is_same<C, double>::value) {
+    double f[kQ], r, jx, jy, jz;
+    site_f<S>(d, x, odd, f);
+    f_moments(f, r, jx, jy, jz);
+    if (rho) rho[x] = r;
+    if (u) {
+      u[3 * x] = jx / r;
+      u[3 * x + 1] = jy / r;
+      u[3 * x + 2] = jz / r;
+    }
+  } else {
+    uint32_t nf;
+    int64_t nb[kQ];
+    site_links(d, x, nf, nb);
+    const S* P = static_cast<const S*>(d.pop);
+    C g[kQ];
+    for (int j = 0; j < kQ; ++j) g[j] = Codec<S>::ld(P + slot_of(d, x, j, odd, nf, nb), j);
+    const Mom<C> m = moments(g);
+    if (rho) rho[x] = 1.0 + (double)m.drho;
+    if (u) {
+      u[3 * x] = m.ux;
+      u[3 * x + 1] = m.uy;
+      u[3 * x + 2] = m.uz;
+    }
   }
 }
 
