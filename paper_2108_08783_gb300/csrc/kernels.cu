@@ -952,13 +952,22 @@ __device__ __forceinline__ typename Codec<S>::C boundary_fast(const DevLattice& 
     }
   });
   const Mom<C> m = moments(g);
-  // Park g in the warp's area; the pairs below read it back (volatile, so the
-  // 19 values are not held in registers through the boundary rule).
-  unroll<kQ>([&](auto J) {
-    constexpr int j = decltype(J)::value;
-    area[j * kTile + lane] = g[j];
-  });
-  auto gv = [&](int j) -> C { return static_cast<const volatile C*>(area)[j * kTile + lane]; };
+  // FP32 compute: g stays in registers through the boundary rule (at 72
+  // registers no spills; parking it in shared memory and reading it back
+  // pair by pair, needed at 64, measured 1.5-3 % slower).  FP64: g is parked
+  // in the warp's area and read back pair by pair (volatile, so the 19
+  // doubles are not held in registers through the rule).
+  constexpr bool kPark = std::is_same<C, double>::value;
+  if constexpr (kPark) {
+    unroll<kQ>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      area[j * kTile + lane] = g[j];
+    });
+  }
+  auto gv = [&](int j) -> C {
+    if constexpr (kPark) return static_cast<const volatile C*>(area)[j * kTile + lane];
+    else return g[j];
+  };
   if (unstable(m.rho)) atomicOr(d.err, kErrUnstable);
   const C keep = C(1) - omega;  // (1 - 1/tau)
   // Elastic wall (Sec. 2.3-2.4): dE in FP64, the ratio sw = U_w/u_f =
