@@ -91,6 +91,7 @@ struct lbm_ctx {
   double* diag_out[kDiagSets] = {};
   int64_t* diag_io_off = nullptr;
   int64_t* diag_io_q = nullptr;
+  int diag_fpi = 1;  // final-sum blocks per iolet
   cudaStream_t diag_stream = nullptr;
   cudaEvent_t diag_filled[kDiagSets] = {};  // main stream: the step kernels wrote set b
   cudaEvent_t diag_free[kDiagSets] = {};    // diagnostic stream: set b copied out
@@ -565,6 +566,9 @@ int diag_setup(lbm_ctx* c) {
     ioff[(size_t)k + 1] = (int64_t)q.size();
   }
   const int64_t js = (int64_t)(n_io > 0 ? n_io : 1) * lbm::kTile;
+  int64_t max_sites = 0;
+  for (int k = 0; k < nio; ++k) max_sites = std::max(max_sites, ioff[(size_t)k + 1] - ioff[(size_t)k]);
+  c->diag_fpi = lbm::diag_flux_blocks(max_sites);
   int32_t* it_d = dev_alloc<int32_t>(c, nb > 0 ? (size_t)nb : 1);
   c->diag_io_off = dev_alloc<int64_t>(c, ioff.size());
   c->diag_io_q = dev_alloc<int64_t>(c, q.empty() ? 1 : q.size());
@@ -572,7 +576,7 @@ int diag_setup(lbm_ctx* c) {
   for (int b = 0; b < lbm_ctx::kDiagSets; ++b) {
     c->diag_mass[b] = dev_alloc<double>(c, (size_t)c->d.n_tiles);
     c->diag_j[b] = dev_alloc<double>(c, 3 * (size_t)js);
-    c->diag_part[b] = dev_alloc<double>(c, (size_t)lbm::diag_blocks());
+    c->diag_part[b] = dev_alloc<double>(c, (size_t)lbm::diag_blocks(nio, c->diag_fpi));
     c->diag_done[b] = dev_alloc<unsigned>(c, 1);
     c->diag_out[b] = dev_alloc<double>(c, 1 + (size_t)nio);
     ok = ok && c->diag_mass[b] && c->diag_j[b] && c->diag_part[b] && c->diag_done[b] &&
@@ -638,8 +642,9 @@ int lbm_step_diag(lbm_ctx* c, int64_t n_steps, double* out) {
   e = cudaEventRecord(c->diag_filled[b], c->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->diag_stream, c->diag_filled[b], 0);
   if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_diag order");
-  rc = check_launch(c, lbm::launch_diag_final(c->d, c->diag_io_off, c->diag_io_q, c->diag_part[b],
-                                              c->diag_done[b], c->diag_out[b], c->diag_stream),
+  rc = check_launch(c, lbm::launch_diag_final(c->d, c->diag_io_off, c->diag_io_q, c->diag_fpi,
+                                              c->diag_part[b], c->diag_done[b], c->diag_out[b],
+                                              c->diag_stream),
                     "diagnostics kernel");
   if (rc != LBM_OK) return rc;
   const int k = (int)c->iolets.size();

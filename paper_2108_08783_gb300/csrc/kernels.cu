@@ -415,12 +415,15 @@ __device__ __forceinline__ bool chk_site(int64_t y, int64_t n, int* err) {
 }
 
 // Branch-free update of a site whose 18 links are fluid.
-// Returns the site's rho - 1 (for the fused mass diagnostic).
-template <class S, bool ODD>
+// Returns the site's rho - 1 (for the fused mass diagnostic).  With SLOT the
+// whole warp (every lane updating a site) adds the lanes' rho - 1 as soon as
+// the moments are formed and lane 0 writes the sum to *slot, so nothing of it
+// stays live through the stores.
+template <class S, bool ODD, bool SLOT = false>
 __device__ __forceinline__ typename Codec<S>::C bulk_update(S* P, int64_t np, int64_t x,
                                                             const int32_t* dsc,
                                                             typename Codec<S>::C omega, int* err,
-                                                            int* chk) {
+                                                            int* chk, double* slot = nullptr) {
   using Cd = Codec<S>;
   using C = typename Cd::C;
   C g[kQ];
@@ -431,6 +434,10 @@ __device__ __forceinline__ typename Codec<S>::C bulk_update(S* P, int64_t np, in
     else g[j] = Cd::ld(P + o * np + x + dsc[o - 1], j);
   });
   const Mom<C> m = moments(g);
+  if constexpr (SLOT) {
+    const C sum = warp_sum(m.drho);
+    if ((threadIdx.x & 31) == 0) *slot = (double)sum;
+  }
   if (unstable(m.rho)) atomicOr(err, kErrUnstable);
   Cd::st(P + x, 0, g[0] + omega * (geq<0, C>(m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - g[0]));
   chk_count(chk, P, P + x, kQ * np, err);
@@ -1346,11 +1353,14 @@ struct EnsBulkMinBlocks {
 constexpr int kBoundaryWarps = LBM_BOUNDARY_WARPS;  // k_boundary: tiles (warps) per CTA
 
 // Bulk tile at launch position k (whole warp); dsc: the warp's 20-word area.
-// Returns the lane's rho - 1 (0 for a lane without a site).
-template <class S, bool ODD>
+// Returns the lane's rho - 1 (0 for a lane without a site).  With SLOT the
+// tile's sum goes to *slot instead (fused diagnostics): from inside the update
+// when every lane has a site (bulk tiles always do), else after it.
+template <class S, bool ODD, bool SLOT = false>
 __device__ __forceinline__ typename Codec<S>::C bulk_tile(const DevLattice& d,
                                                           const StepParams& p, int64_t k,
-                                                          int32_t* dsc, int lane) {
+                                                          int32_t* dsc, int lane,
+                                                          double* slot = nullptr) {
   using C = typename Codec<S>::C;
   // a warp that updates tiles in a loop (persistent kernel): every lane is done
   // with the previous tile's descriptor before it is overwritten
@@ -1363,6 +1373,22 @@ __device__ __forceinline__ typename Codec<S>::C bulk_tile(const DevLattice& d,
   }
   __syncwarp();
   const int64_t x = (int64_t)dsc[19] * kTile + lane;
+  if constexpr (SLOT) {
+    bool ok = x < d.n;
+    if constexpr (kChecked && ODD)
+      for (int o = 0; o < 18; ++o) ok = ok && chk_site(x + dsc[o], d.n, d.err);
+    if (__all_sync(0xffffffffu, ok)) {
+      bulk_update<S, ODD, true>(static_cast<S*>(d.pop), d.npad, x, dsc,
+                                omega_as<C>(p.omega, p.omega_f), d.err, d.chk, slot);
+      return C(0);
+    }
+    const C dr = ok ? bulk_update<S, ODD>(static_cast<S*>(d.pop), d.npad, x, dsc,
+                                          omega_as<C>(p.omega, p.omega_f), d.err, d.chk)
+                    : C(0);
+    const C sum = warp_sum(dr);
+    if (lane == 0) *slot = (double)sum;
+    return C(0);
+  }
   if (x >= d.n) return C(0);
   if constexpr (kChecked && ODD) {
     bool ok = true;
@@ -1505,11 +1531,8 @@ __global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::one)
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k = d.n_boundary + (int64_t)blockIdx.x * W + w;
   if (k >= d.n_tiles) return;  // warp-uniform
-  const auto dr = bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
-  if constexpr (DIAG) {
-    const auto m = warp_sum(dr);
-    if (lane == 0) d.diag_mass[k] = (double)m;
-  }
+  if constexpr (DIAG) bulk_tile<S, ODD, true>(d, p, k, desc_s[w], lane, d.diag_mass + k);
+  else bulk_tile<S, ODD>(d, p, k, desc_s[w], lane);
 }
 
 // Resident CTAs (4 warps) per SM requested of the boundary kernel: 7, i.e. 73
@@ -2157,53 +2180,62 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
-// Fused diagnostics, the final sums in a fixed order: blocks [0, kDiagBlocks)
-// add contiguous ranges of the per-tile partials of rho - 1 and the last of
-// them to finish adds the block sums in block order (total mass = n plus
-// that sum); block kDiagBlocks + k adds iolet k's flux, (rho u) . axis over
-// the sites with a link into it (io_q: their places in diag_j).
+// Fused diagnostics, the final sums in a fixed order.  Blocks [0, kDiagBlocks)
+// add contiguous ranges of the per-tile partials of rho - 1; then fpi blocks
+// per iolet k add (rho u) . axis_k over consecutive runs of kRedThreads of its
+// sites (io_q: their places in diag_j; one site per thread, so no block waits
+// on a chain of dependent loads).  Every block writes one partial; the last
+// block to finish adds them in block order: out[0] = n + the mass partials,
+// out[1 + k] = iolet k's fpi partials.
 constexpr int kDiagBlocks = 128;
 __global__ void __launch_bounds__(kRedThreads)
-    k_diag_final(const DevLattice d, const int64_t* io_off, const int64_t* io_q, double* part,
-                 unsigned* done, double* out) {
+    k_diag_final(const DevLattice d, const int64_t* io_off, const int64_t* io_q, int fpi,
+                 double* part, unsigned* done, double* out) {
   __shared__ double sh[kRedThreads];
   __shared__ int last;
   const int b = blockIdx.x;
+  double acc = 0.0;
   if (b < kDiagBlocks) {
     const int64_t per = (d.n_tiles + kDiagBlocks - 1) / kDiagBlocks;
     const int64_t lo = (int64_t)b * per;
     const int64_t hi = lo + per < d.n_tiles ? lo + per : d.n_tiles;
-    double acc = 0.0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) acc += d.diag_mass[i];
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) {
-      part[b] = s;
-      __threadfence();
-      last = atomicAdd(done, 1u) == kDiagBlocks - 1 ? 1 : 0;
-    }
-    __syncthreads();
-    if (!last) return;  // block-uniform
-    __threadfence();
-    double a = 0.0;
-    for (int i = threadIdx.x; i < kDiagBlocks; i += kRedThreads) a += __ldcg(part + i);
-    const double t = block_sum(a, sh);
-    if (threadIdx.x == 0) {
-      out[0] = (double)d.n + t;
-      if (!isfinite(t)) atomicOr(d.err, kErrUnstable);
-      *done = 0;  // for the next diagnostic step (stream order)
-    }
   } else {
-    const int k = b - kDiagBlocks;
-    const IoletDev& io = d.iolets[k];
-    const int64_t js = d.diag_jstride;
-    double acc = 0.0;
-    for (int64_t q = io_off[k] + threadIdx.x; q < io_off[k + 1]; q += kRedThreads) {
-      const int64_t j = io_q[q];
-      acc += d.diag_j[j] * io.axis[0] + d.diag_j[js + j] * io.axis[1] +
-             d.diag_j[2 * js + j] * io.axis[2];
+    const int k = (b - kDiagBlocks) / fpi, f = (b - kDiagBlocks) % fpi;
+    const int64_t q = io_off[k] + (int64_t)f * kRedThreads + threadIdx.x;
+    if (q < io_off[k + 1]) {
+      const IoletDev& io = d.iolets[k];
+      const int64_t js = d.diag_jstride, j = io_q[q];
+      acc = d.diag_j[j] * io.axis[0] + d.diag_j[js + j] * io.axis[1] +
+            d.diag_j[2 * js + j] * io.axis[2];
     }
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) out[1 + k] = s;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    part[b] = s;
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1 ? 1 : 0;
+  }
+  __syncthreads();
+  if (!last) return;  // block-uniform
+  __threadfence();
+  // mass: the kDiagBlocks partials in block order
+  double a = 0.0;
+  for (int i = threadIdx.x; i < kDiagBlocks; i += kRedThreads) a += __ldcg(part + i);
+  const double t = block_sum(a, sh);
+  if (threadIdx.x == 0) {
+    out[0] = (double)d.n + t;
+    if (!isfinite(t)) atomicOr(d.err, kErrUnstable);
+    *done = 0;  // for the next diagnostic step (stream order)
+  }
+  // fluxes: one warp per iolet at a time, its fpi partials in order
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = w; k < d.n_iolets; k += kRedThreads / 32) {
+    const double* pk = part + kDiagBlocks + (int64_t)k * fpi;
+    double v = 0.0;
+    for (int f = lane; f < fpi; f += 32) v += __ldcg(pk + f);
+    v = warp_sum(v);
+    if (lane == 0) out[1 + k] = v;
   }
 }
 
@@ -2513,13 +2545,17 @@ int launch_reduce(int storage, const DevLattice& d, int odd, const int64_t* off,
   });
 }
 
-int launch_diag_final(const DevLattice& d, const int64_t* io_off, const int64_t* io_q,
+int launch_diag_final(const DevLattice& d, const int64_t* io_off, const int64_t* io_q, int fpi,
                       double* part, unsigned* done, double* out, void* stream) {
-  k_diag_final<<<kDiagBlocks + d.n_iolets, kRedThreads, 0, (cudaStream_t)stream>>>(
-      d, io_off, io_q, part, done, out);
+  k_diag_final<<<kDiagBlocks + d.n_iolets * fpi, kRedThreads, 0, (cudaStream_t)stream>>>(
+      d, io_off, io_q, fpi, part, done, out);
   return (int)cudaGetLastError();
 }
-int diag_blocks() { return kDiagBlocks; }
+int diag_blocks(int n_iolets, int fpi) { return kDiagBlocks + n_iolets * fpi; }
+int diag_flux_blocks(int64_t max_sites) {
+  const int64_t f = (max_sites + kRedThreads - 1) / kRedThreads;
+  return f > 0 ? (int)f : 1;
+}
 
 int launch_wss(int storage, const DevLattice& d, int odd, double tau, const int64_t* sites,
                const double* normals, int64_t m, double* out, void* stream) {

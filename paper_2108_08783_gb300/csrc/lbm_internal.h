@@ -296,10 +296,12 @@ int launch_wss(int storage, const DevLattice& d, int odd_layout, double tau,
                void* stream);
 size_t storage_bytes(int storage);
 // Fused diagnostics: the final sums of a step run with StepParams::diag into
-// out[1 + n_iolets] (part: diag_blocks() doubles; done: a zeroed counter).
-int launch_diag_final(const DevLattice& d, const int64_t* io_off, const int64_t* io_q,
+// out[1 + n_iolets]; fpi = diag_flux_blocks(largest iolet site count) blocks
+// per iolet, part: diag_blocks(n_iolets, fpi) doubles, done: a zeroed counter.
+int launch_diag_final(const DevLattice& d, const int64_t* io_off, const int64_t* io_q, int fpi,
                       double* part, unsigned* done, double* out, void* stream);
-int diag_blocks();
+int diag_blocks(int n_iolets, int fpi);
+int diag_flux_blocks(int64_t max_sites);
 // Checked builds: flag every population slot not stored exactly once since the
 // last call (padding slots: never), then clear the counts.
 int launch_check_counts(const DevLattice& d, void* stream);
