@@ -219,11 +219,16 @@ __device__ __forceinline__ double tube_law(double Kw, double rho, const StepPara
   const double dp = rho - p.rho0;
   return Kw * (dp > 0.0 ? dp : 0.0);
 }
+// (the FP64 difference out of line, so that the compiler branches around it
+// instead of issuing it predicated off on every lane)
+__device__ __noinline__ double tube_law_fp64(double Kw, float rho, double rho0) {
+  const double dp = (double)rho - rho0;
+  return Kw * (dp > 0.0 ? dp : 0.0);
+}
 __device__ __forceinline__ double tube_law(double Kw, float rho, const StepParams& p) {
   if (p.rho0_exact && rho >= 0.5f * p.rho0_f && rho <= 2.0f * p.rho0_f)
     return Kw * (double)fmaxf(rho - p.rho0_f, 0.0f);
-  const double dp = (double)rho - p.rho0;
-  return Kw * (dp > 0.0 ? dp : 0.0);
+  return tube_law_fp64(Kw, rho, p.rho0);
 }
 
 // Density outlet state rho_out and rho_out - 1 in the compute type.
