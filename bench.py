@@ -651,7 +651,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES))
     ap.add_argument("--config", default="tube40", choices=["tube40", "tree", "tube8", "ensemble"])
-    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--e2e-steps", type=int, default=4000,
+                    help="steps of the end-to-end run (the workload's usual length)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

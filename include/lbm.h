@@ -341,8 +341,13 @@ int lbm_fmap(const double *alpha, int64_t n_alpha, const double *dr_over_R, int6
  * distance of the bulk kernel, tiles, >= 0), LBM_TUNE_BULK_SITES (1 to 4:
  * one or two sites per lane of the bulk kernel and their pairing) and
  * LBM_TUNE_BULK_WARPS (4 or 8 warps per CTA of the bulk kernel), as for
- * lbm_ensemble_tune.  Defaults are
- * chosen per storage at build time.  LBM_EINVAL for another knob or value. */
+ * lbm_ensemble_tune; for a lattice with 16-bit storage LBM_TUNE_BULK_SITES
+ * also takes 5: as 2, but on even steps a fixed grid of warps whose rows
+ * arrive by TMA tensor copies into a two-stage shared-memory ring per warp
+ * (the first use builds the tensor map of the population array; the same
+ * results as 2, bit for bit).  Defaults are chosen per storage at build
+ * time.  LBM_EINVAL for another knob or value, LBM_ECUDA when the tensor map
+ * cannot be made. */
 int lbm_tune(lbm_ctx *ctx, int32_t knob, int64_t value);
 
 /* lbm_set_stream - run subsequent work on another cudaStream_t. */

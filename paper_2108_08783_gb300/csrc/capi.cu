@@ -1,6 +1,8 @@
 // C ABI of the library (declared in include/lbm.h): context lifetime, device
 // memory, host<->device copies and kernel launches.  Every step of the method
 // runs in the kernels of kernels.cu; this file only marshals.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -70,6 +72,11 @@ struct lbm_ctx {
   int64_t prefetch = 0;  // L2 prefetch distance (tiles), set from the storage at build
   int32_t bulk_sites = 1;  // bulk kernel mode, set from the storage at build
   int32_t bulk_warps = 4;  // warps per CTA of the bulk kernel
+  int32_t n_sms = 0;       // SMs of the context's device
+  // tensor map of the populations as a [19][npad] array of 16-bit elements,
+  // boxes of 32 x 19 (staged-row bulk kernel), made on first use
+  alignas(64) CUtensorMap tmap;
+  bool tmap_ready = false;
   // optional per-kernel timing (lbm_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;  // 3 per profiled step
@@ -398,6 +405,13 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
     chk(cudaMemsetAsync(sUw, 0, 3 * S * sizeof(double), c->stream));
   }
   chk(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      c->n_sms = sms;
+    cudaGetLastError();
+  }
   chk(cudaMemsetAsync(d.pop, 0, (size_t)lbm::kQ * d.npad * sz, c->stream));
   if (e != cudaSuccess) {
     rc = cuda_fail(c, e, "lbm_build_lattice upload");
@@ -495,6 +509,28 @@ int lbm_init_fields(lbm_ctx* c, const double* rho, const double* u) {
 
 namespace {
 
+// The populations as a 2-D tensor for TMA copies: [19 rows][npad] 16-bit
+// elements (row stride npad elements), boxes of one tile (32) x 19 rows.
+int make_tmap(lbm_ctx* c) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q);
+  if (e != cudaSuccess || !fn || q != cudaDriverEntryPointSuccess)
+    return fail(c, LBM_ECUDA, "staged rows: no cuTensorMapEncodeTiled");
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const cuuint64_t dims[2] = {(cuuint64_t)c->d.npad, (cuuint64_t)lbm::kQ};
+  const cuuint64_t strides[1] = {(cuuint64_t)c->d.npad * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)lbm::kTile, (cuuint32_t)lbm::kQ};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, c->d.pop, dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, LBM_ECUDA, "staged rows: tensor map encoding failed");
+  c->tmap_ready = true;
+  return LBM_OK;
+}
+
 // n_steps timesteps; with diag_last the last one also writes the fused
 // diagnostics of the state it reads.
 int run_steps(lbm_ctx* c, int64_t n_steps, bool diag_last) {
@@ -509,6 +545,8 @@ int run_steps(lbm_ctx* c, int64_t n_steps, bool diag_last) {
   p.step_dev = nullptr;
   p.bulk_sites = c->bulk_sites;
   p.bulk_warps = c->bulk_warps;
+  p.n_sms = c->n_sms;
+  p.tmap = c->tmap_ready ? &c->tmap : nullptr;
   for (int64_t s = 0; s < n_steps; ++s) {
     p.step = c->step;
     p.write_state = s == n_steps - 1 ? 1 : 0;
@@ -666,7 +704,11 @@ int lbm_tune(lbm_ctx* c, int32_t knob, int64_t value) {
       c->prefetch = value;
       return LBM_OK;
     case LBM_TUNE_BULK_SITES:
-      if (value < 1 || value > 4) return fail(c, LBM_EINVAL, "bulk sites mode must be 1 to 4");
+      if (value < 1 || value > 5) return fail(c, LBM_EINVAL, "bulk sites mode must be 1 to 5");
+      if (value == 5 && lbm::storage_bytes(c->storage) == 2 && !c->tmap_ready) {
+        int rc = make_tmap(c);
+        if (rc != LBM_OK) return rc;
+      }
       c->bulk_sites = (int32_t)value;
       return LBM_OK;
     case LBM_TUNE_BULK_WARPS:

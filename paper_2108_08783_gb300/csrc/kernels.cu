@@ -30,6 +30,7 @@
 // memory with cp.async.bulk copies completing on an mbarrier.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -1529,6 +1530,112 @@ __global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::two)
   }
 }
 
+// Even steps of the 16-bit bulk tiles with staged rows (LBM_TUNE_BULK_SITES 5):
+// a fixed grid of warps walks the bulk tile pairs.  While a warp updates one
+// pair from shared memory, two TMA copies (one per tile, 19 rows x 32 sites
+// of the row-major population array, described by the tensor map tm) bring
+// the next pair into the other stage of its two-stage ring, each stage
+// completing on its own mbarrier; even steps read each site's own slots, so
+// every copy starts on a tile boundary.  No register holds a population in
+// flight.  Lane l takes the adjacent sites 2 (l mod 16), 2 (l mod 16) + 1 of
+// the first (l < 16) or second tile, as k_bulk2 does; a lone last tile takes
+// bulk_tile.
+constexpr int kStageWarps = 4;
+constexpr int kStageTileWords = 20 * kTile / 2;  // 19 rows of 64 bytes, padded to 1280 bytes
+__device__ __forceinline__ uint32_t lds_volatile_u32(const uint32_t* p) {
+  return *static_cast<const volatile uint32_t*>(p);
+}
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* tm, int32_t x, int32_t y,
+                                       uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+#ifndef LBM_STAGES
+#define LBM_STAGES 2
+#endif
+constexpr int kStages = LBM_STAGES;  // ring depth per warp: pairs in flight + 1
+template <class S>
+__global__ void __launch_bounds__(kStageWarps * 32, kStages <= 2 ? 8 : (kStages == 3 ? 6 : 5))
+    k_bulk2s(const DevLattice d, const StepParams p, const __grid_constant__ CUtensorMap tm) {
+  static_assert(sizeof(S) == 2, "staged rows: 16-bit storage");
+  __shared__ __align__(128) uint32_t buf[kStageWarps][kStages][2][kStageTileWords];
+  __shared__ __align__(8) uint64_t bars[kStageWarps][kStages];
+  __shared__ __align__(16) int32_t desc_s[kStageWarps][20];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nb = d.n_boundary, n_pairs = (d.n_tiles - nb) / 2;
+  const int64_t stride = (int64_t)gridDim.x * kStageWarps;
+  S* P = static_cast<S*>(d.pop);
+  const int64_t np = d.npad;
+  if (lane == 0)
+    for (int i = 0; i < kStages; ++i) mbar_init(&bars[w][i], 1);
+  __syncwarp();
+  // tile ids of pair qq (every lane loads the same two words)
+  auto tile_of = [&](int64_t qq, int h) -> int32_t {
+    return qq < n_pairs ? __ldg(&d.launch[nb + 2 * qq + h].tile) : 0;
+  };
+  auto issue = [&](int st, int32_t ta, int32_t tb) {
+    if (lane == 0) {
+      // the lanes' reads of this stage (two iterations back) come before the
+      // copies that overwrite it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bars[w][st], 2u * kQ * kTile * (uint32_t)sizeof(S));
+      tma_2d(&buf[w][st][0][0], &tm, ta * kTile, 0, &bars[w][st]);
+      tma_2d(&buf[w][st][1][0], &tm, tb * kTile, 0, &bars[w][st]);
+    }
+  };
+  // ring: pair q + i stride sits in stage (it + i) mod kStages; the ids of
+  // a pair are loaded an iteration before its copies are issued
+  int64_t q = (int64_t)blockIdx.x * kStageWarps + w;
+  int32_t ta[kStages + 1], tb[kStages + 1];  // ids of pairs q, q + stride, ...
+  for (int i = 0; i <= kStages; ++i) {
+    ta[i] = tile_of(q + i * stride, 0);
+    tb[i] = tile_of(q + i * stride, 1);
+  }
+  for (int i = 0; i + 1 < kStages; ++i)
+    if (q + i * stride < n_pairs) issue(i, ta[i], tb[i]);
+  uint32_t phases = 0;  // bit i: parity of stage i
+  const F2 om = bc2(p.omega_f);
+  int st = 0;
+  for (; q < n_pairs; q += stride, st = st + 1 == kStages ? 0 : st + 1) {
+    const int last = st == 0 ? kStages - 1 : st - 1;  // the stage read two iterations back
+    if (q + (kStages - 1) * stride < n_pairs) issue(last, ta[kStages - 1], tb[kStages - 1]);
+    const uint32_t ph = (phases >> st) & 1u;
+    if (!__all_sync(0xFFFFFFFFu, mbar_wait_bounded(&bars[w][st], ph))) {
+      // the copies did not complete: flag the step and stop (one more bounded
+      // wait on each stage gives copies in flight a chance to land)
+      if (lane == 0) atomicOr(d.err, kErrTimeout);
+      for (int i = 0; i < kStages; ++i) mbar_wait_bounded(&bars[w][i], (phases >> i) & 1u);
+      return;
+    }
+    phases ^= 1u << st;
+    const int64_t x = (int64_t)(lane < 16 ? ta[0] : tb[0]) * kTile + 2 * (lane & 15);
+    const uint32_t* row = &buf[w][st][lane >> 4][lane & 15];  // row j at + j * 16 words
+    using Cd = Codec2<S>;
+    collide2(
+        [&](int j) -> F2 { return Cd::unpack(row[j * (kTile / 2)]); },
+        [&](int j) -> F2 { return Cd::unpack(lds_volatile_u32(row + j * (kTile / 2))); }, om,
+        d.err, d.err, [&](F2 s0) { Cd::st_al(P + x, s0); },
+        [&](auto A, F2 sa, F2 sb) {
+          constexpr int a = decltype(A)::value, b = a + 1;
+          Cd::st_al(P + b * np + x, sa);
+          Cd::st_al(P + a * np + x, sb);
+        });
+    __syncwarp();
+    for (int i = 0; i < kStages; ++i) {
+      ta[i] = ta[i + 1];
+      tb[i] = tb[i + 1];
+    }
+    ta[kStages] = tile_of(q + (kStages + 1) * stride, 0);
+    tb[kStages] = tile_of(q + (kStages + 1) * stride, 1);
+  }
+  // a lone last bulk tile
+  if ((d.n_tiles - nb) % 2 && blockIdx.x == 0 && w == 0)
+    bulk_tile<S, false>(d, p, d.n_tiles - 1, desc_s[w], lane);
+}
+
 template <class S, bool ODD, int W, bool DIAG = false>
 __global__ void __launch_bounds__(W * 32, BulkMinBlocks<S, W>::one)
     k_bulk(const DevLattice d, const StepParams p) {
@@ -2309,6 +2416,7 @@ inline int bulk_pairing(int32_t bulk_sites, bool odd) {
     case 2: return odd ? 2 : 1;
     case 3: return 1;
     case 4: return 2;
+    case 5: return odd ? 2 : 3;  // 3: staged rows (k_bulk2s, 16-bit even steps)
   }
   return 0;
 }
@@ -2317,6 +2425,20 @@ inline int bulk_pairing(int32_t bulk_sites, bool odd) {
 template <class S, int W, bool DIAG = false>
 void launch_bulk(const DevLattice& d, const StepParams& p, bool odd, int pairing, int64_t tiles,
                  cudaStream_t m) {
+  if constexpr (sizeof(S) == 2 && !DIAG) {
+    if (pairing == 3 && !odd && p.n_sms > 0) {
+      const int64_t pairs = tiles / 2;
+      int64_t g = (int64_t)p.n_sms * (kStages <= 2 ? 8 : (kStages == 3 ? 6 : 5));
+      const int64_t gmax = (pairs + kStageWarps - 1) / kStageWarps;
+      if (g > gmax) g = gmax > 0 ? gmax : 1;
+      if (p.tmap) {
+        k_bulk2s<S><<<(unsigned)g, kStageWarps * 32, 0, m>>>(
+            d, p, *static_cast<const CUtensorMap*>(p.tmap));
+        return;
+      }
+    }
+  }
+  if (pairing == 3) pairing = 1;  // other storages and diagnostic steps: adjacent pairs
   if (pairing) {
     const unsigned nb = (unsigned)((tiles + 2 * W - 1) / (2 * W));
     if constexpr (sizeof(S) < 8) {
@@ -2337,6 +2459,7 @@ void launch_bulk(const DevLattice& d, const StepParams& p, bool odd, int pairing
 template <class S, int W>
 void launch_bulk_ens(const EnsembleLaunch& e, const StepParams& p, bool odd, int pairing,
                      cudaStream_t m) {
+  if (pairing == 3) pairing = 1;  // staged rows: single lattices only
   if (pairing) {
     const unsigned nb = (unsigned)((e.n_bulk_tiles + 2 * W - 1) / (2 * W));
     if constexpr (sizeof(S) < 8) {

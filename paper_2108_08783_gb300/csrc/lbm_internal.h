@@ -212,7 +212,8 @@ struct StepParams {
   int32_t bulk_sites;       // bulk kernel mode (LBM_TUNE_BULK_SITES)
   int32_t bulk_warps;       // warps per CTA of the bulk kernel: 4 or 8
   int32_t diag;             // 1: the step kernels also write the fused diagnostics
-  int32_t pad1;
+  int32_t n_sms;            // SMs of the device (fixed-grid kernels)
+  const void* tmap;         // host CUtensorMap of the populations (staged rows), or NULL
 };
 
 // One member of an ensemble: its device view and its wall constants.

@@ -268,6 +268,8 @@ class Lattice:
         equal)."""
         if self.storage == "f64":
             bulk_sites = (1,)
+        elif self.storage in ("f16s", "bf16s") and 5 not in bulk_sites:
+            bulk_sites = tuple(bulk_sites) + (5,)  # TMA-staged even steps
         best = dict(bulk_sites=bulk_sites[0], bulk_warps=bulk_warps[0], prefetch=prefetch[0])
         results = []
         for knob, cands in (("bulk_sites", bulk_sites), ("bulk_warps", bulk_warps),

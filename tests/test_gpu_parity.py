@@ -248,15 +248,17 @@ def test_long_tube_full_size_short_run(storage, tol, bulk_sites):
 @pytest.mark.parametrize("storage", ["f32", "f16s"])
 def test_every_bulk_kernel_variant_against_the_oracle(storage):
     """The bulk kernel in each launch configuration the autotuner chooses from
-    (one or two sites per lane with either pairing, 4 or 8 warps per CTA) on the
-    R = 12, L = 159 tube, 301 steps from a smooth random state: FP32 within the
-    1e-5 tolerance; FP16S within its storage bound at that step count; and for
-    FP32 the variants agree with one another to 1e-6."""
+    (one or two sites per lane with either pairing, 4 or 8 warps per CTA, and
+    for 16-bit storage the TMA-staged even steps) on the R = 12, L = 159 tube,
+    301 steps from a smooth random state: FP32 within the 1e-5 tolerance; FP16S
+    within its storage bound at that step count; and for FP32 the variants
+    agree with one another to 1e-6.  The staged variant updates from the same
+    values as two-site mode 2, so the two must agree bit for bit."""
     geo = _bulk_tube()
     fields = I.random_fields(13, geo.shape, drho=1e-3, umax=0.02)
     orc = None
     res = {}
-    for bulk_sites in (1, 2, 3, 4):
+    for bulk_sites in ((1, 2, 3, 4) if storage == "f32" else (1, 2, 3, 4, 5)):
         for warps in (4, 8):
             lat, o = make_pair(geo, storage, tau=0.8, wall_model=1, F=0.85, kappa=BULK_KAPPA,
                                fields=fields, bulk_sites=bulk_sites)
@@ -283,6 +285,10 @@ def test_every_bulk_kernel_variant_against_the_oracle(storage):
         assert er < bound_r and rel_l2(ul, uo) < bound_u, (key, er, rel_l2(ul, uo))
         if storage == "f32":
             assert rel_l2(ul, u0) < 1e-6, key
+    if storage != "f32":
+        for warps in (4, 8):
+            np.testing.assert_array_equal(res[(5, warps)][0], res[(2, warps)][0])
+            np.testing.assert_array_equal(res[(5, warps)][1], res[(2, warps)][1])
 
 
 # ------------------------------------------------------------------ reduced precision
