@@ -511,7 +511,11 @@ def run_ours(args):
     n = lat.n
     stream = lat.stream
     # ---------------------------------------------------------------- device timing
-    lat.step(args.warmup)
+    # warm-up: at least W steps, and two blocks of the library's captured step
+    # graph (lbm_step replays 20-step graphs), so that the graph is captured
+    # before the timed region and the timed region starts on an even step
+    warm = max(args.warmup, 40)
+    lat.step(warm + (warm & 1))
     lat.sync()
     clocks = Clocks(local)
     if rank == 0:

@@ -341,7 +341,13 @@ int lbm_fmap(const double *alpha, int64_t n_alpha, const double *dr_over_R, int6
  * distance of the bulk kernel, tiles, >= 0), LBM_TUNE_BULK_SITES (1 to 4:
  * one or two sites per lane of the bulk kernel and their pairing) and
  * LBM_TUNE_BULK_WARPS (4 or 8 warps per CTA of the bulk kernel), as for
- * lbm_ensemble_tune; for a lattice with 16-bit storage LBM_TUNE_BULK_SITES
+ * lbm_ensemble_tune, and LBM_TUNE_GRAPH_STEPS: G > 0 (even) replays whole
+ * blocks of G steps of lbm_step as one CUDA graph, captured on first use on a
+ * stream of the library's own that is ordered with the context's stream by
+ * events (the inlet time reads a device step counter; any later lbm_tune or
+ * lbm_set_wall_params captures again; not used by lbm_step_diag, while
+ * lbm_profile is on, or in checked builds; default 20, 0 for direct
+ * launches); for a lattice with 16-bit storage LBM_TUNE_BULK_SITES
  * also takes 5: as 2, but on even steps a fixed grid of warps whose rows
  * arrive by TMA tensor copies into a two-stage shared-memory ring per warp
  * (the first use builds the tensor map of the population array; the same

@@ -73,6 +73,16 @@ struct lbm_ctx {
   int32_t bulk_sites = 1;  // bulk kernel mode, set from the storage at build
   int32_t bulk_warps = 4;  // warps per CTA of the bulk kernel
   int32_t n_sms = 0;       // SMs of the context's device
+  // captured steps (LBM_TUNE_GRAPH_STEPS): G steps replayed as one CUDA graph
+  // on a private stream, ordered with the context's stream by events; the
+  // inlet phase reads a device step counter that the graph advances
+  int64_t graph_steps = 0;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t g_in = nullptr, g_out = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int gexec_parity = -1;
+  int64_t gexec_steps = 0;
+  int64_t* step_d = nullptr;
   // tensor map of the populations as a [19][npad] array of 16-bit elements,
   // boxes of 32 x 19 (staged-row bulk kernel), made on first use
   alignas(64) CUtensorMap tmap;
@@ -107,6 +117,10 @@ struct lbm_ctx {
 };
 
 namespace {
+
+// Steps per captured graph of a lattice by default: +3 % on the long tube
+// against direct launches (100 gains another 0.1-0.4 %).
+constexpr int64_t kDefaultGraphSteps = 20;
 
 constexpr uint64_t kCkptMagic = 0x314b43504d424cULL;  // "LBMPCK1"
 
@@ -207,6 +221,11 @@ void lbm_destroy(lbm_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->side) cudaStreamSynchronize(c->side);
   if (c->diag_stream) cudaStreamSynchronize(c->diag_stream);
+  if (c->gstream) cudaStreamSynchronize(c->gstream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->g_in) cudaEventDestroy(c->g_in);
+  if (c->g_out) cudaEventDestroy(c->g_out);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
   for (void* p : c->owned) dev_free_raw(c, p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->fork) cudaEventDestroy(c->fork);
@@ -266,6 +285,7 @@ int lbm_build_lattice(const uint8_t* labels, int32_t nx, int32_t ny, int32_t nz,
   c->storage = storage;
   c->prefetch = default_prefetch(storage);
   c->bulk_sites = default_bulk_sites(storage);
+  c->graph_steps = kDefaultGraphSteps;
   c->tau = tau;
   c->stream = (cudaStream_t)cuda_stream;
   if (alloc) {
@@ -486,6 +506,7 @@ int lbm_set_wall_params(lbm_ctx* c, int32_t wall_model, double rho0, const doubl
   if (rc != LBM_OK) return rc;
   c->wall_model = wall_model;
   c->rho0 = rho0;
+  c->gexec_steps = 0;  // a captured step graph holds the old wall constants
   return LBM_OK;
 }
 
@@ -533,6 +554,13 @@ int make_tmap(lbm_ctx* c) {
 
 // n_steps timesteps; with diag_last the last one also writes the fused
 // diagnostics of the state it reads.
+void drop_graph(lbm_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->gexec_parity = -1;
+  c->gexec_steps = 0;
+}
+
 int run_steps(lbm_ctx* c, int64_t n_steps, bool diag_last) {
   lbm::StepParams p{};
   p.rho0 = c->rho0;
@@ -547,6 +575,67 @@ int run_steps(lbm_ctx* c, int64_t n_steps, bool diag_last) {
   p.bulk_warps = c->bulk_warps;
   p.n_sms = c->n_sms;
   p.tmap = c->tmap_ready ? &c->tmap : nullptr;
+#ifndef LBM_CHECKED
+  const int64_t G = c->graph_steps;
+  if (G > 0 && n_steps >= G && !diag_last && !c->prof) {
+    // whole blocks of G steps as graph replays on the private stream
+    cudaError_t r = cudaSuccess;
+    if (!c->gstream) r = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking);
+    if (r == cudaSuccess && !c->g_in) r = cudaEventCreateWithFlags(&c->g_in, cudaEventDisableTiming);
+    if (r == cudaSuccess && !c->g_out) r = cudaEventCreateWithFlags(&c->g_out, cudaEventDisableTiming);
+    if (r != cudaSuccess) return cuda_fail(c, r, "graph stream");
+    if (!c->step_d) {
+      c->step_d = dev_alloc<int64_t>(c, 1);
+      if (!c->step_d) return fail(c, LBM_ENOMEM, "graph step counter");
+    }
+    r = cudaEventRecord(c->g_in, c->stream);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(c->gstream, c->g_in, 0);
+    if (r != cudaSuccess) return cuda_fail(c, r, "graph ordering");
+    const lbm::StepStreams gs{c->gstream, c->side, c->fork, c->join};
+    const int parity = (int)(c->step & 1);
+    if (!c->gexec || c->gexec_parity != parity || c->gexec_steps != G) {
+      drop_graph(c);
+      cudaGraph_t graph = nullptr;
+      r = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+      for (int64_t s = 0; s < G && r == cudaSuccess; ++s) {
+        p.step = parity + s;  // the kernels add *step_d = step - parity
+        p.step_dev = c->step_d;
+        p.write_state = s == G - 1 ? 1 : 0;
+        const int lr = lbm::launch_step(c->storage, c->d, p, gs, nullptr);
+        if (lr != 0) r = (cudaError_t)lr;
+      }
+      if (r == cudaSuccess) r = (cudaError_t)lbm::launch_advance(c->step_d, G, c->gstream);
+      cudaError_t r2 = cudaStreamEndCapture(c->gstream, &graph);
+      if (r == cudaSuccess) r = r2;
+      if (r == cudaSuccess) r = cudaGraphInstantiate(&c->gexec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (r != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail(c, r, "step graph capture");
+      }
+      c->gexec_parity = parity;
+      c->gexec_steps = G;
+    }
+    r = (cudaError_t)lbm::launch_set_step(c->step_d, c->step - parity, c->gstream);
+    int64_t done = 0;
+    for (; r == cudaSuccess && n_steps - done >= G; done += G) r = cudaGraphLaunch(c->gexec, c->gstream);
+    if (r != cudaSuccess) return cuda_fail(c, r, "step graph launch");
+    c->step += done;
+    p.step_dev = nullptr;
+    for (int64_t s = done; s < n_steps; ++s) {
+      p.step = c->step;
+      p.write_state = s == n_steps - 1 ? 1 : 0;
+      p.diag = 0;
+      const int lr = lbm::launch_step(c->storage, c->d, p, gs, nullptr);
+      if (lr != 0) return cuda_fail(c, (cudaError_t)lr, "step kernels");
+      ++c->step;
+    }
+    r = cudaEventRecord(c->g_out, c->gstream);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(c->stream, c->g_out, 0);
+    if (r != cudaSuccess) return cuda_fail(c, r, "graph ordering");
+    return LBM_OK;
+  }
+#endif
   for (int64_t s = 0; s < n_steps; ++s) {
     p.step = c->step;
     p.write_state = s == n_steps - 1 ? 1 : 0;
@@ -698,7 +787,12 @@ int lbm_step_diag(lbm_ctx* c, int64_t n_steps, double* out) {
 int lbm_tune(lbm_ctx* c, int32_t knob, int64_t value) {
   if (!c) return LBM_EINVAL;
   c->err.clear();
+  c->gexec_steps = 0;  // a captured step graph holds the old settings: capture again
   switch (knob) {
+    case LBM_TUNE_GRAPH_STEPS:
+      if (value < 0 || (value & 1)) return fail(c, LBM_EINVAL, "graph steps must be even and >= 0");
+      c->graph_steps = value;
+      return LBM_OK;
     case LBM_TUNE_PREFETCH:
       if (value < 0) return fail(c, LBM_EINVAL, "prefetch distance must be >= 0");
       c->prefetch = value;

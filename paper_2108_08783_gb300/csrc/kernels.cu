@@ -2077,6 +2077,7 @@ int ensemble_persistent_t(const EnsembleLaunch& e, const StepParams& p, int64_t 
 }
 
 __global__ void k_advance(int64_t* step, int64_t by) { *step += by; }
+__global__ void k_set_step(int64_t* step, int64_t value) { *step = value; }
 
 // ------------------------------------------------ state conversion kernels
 
@@ -2602,6 +2603,10 @@ int launch_ensemble_persistent(int storage, const EnsembleLaunch& e, const StepP
   });
 }
 
+int launch_set_step(int64_t* step_dev, int64_t value, void* stream) {
+  k_set_step<<<1, 1, 0, (cudaStream_t)stream>>>(step_dev, value);
+  return (int)cudaGetLastError();
+}
 int launch_advance(int64_t* step_dev, int64_t by, void* stream) {
   k_advance<<<1, 1, 0, (cudaStream_t)stream>>>(step_dev, by);
   return (int)cudaGetLastError();

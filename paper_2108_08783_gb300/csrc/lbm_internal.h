@@ -282,6 +282,7 @@ int launch_ensemble_persistent(int storage, const EnsembleLaunch& e, const StepP
                                int64_t n_steps, GridSync* sync, int extra_arrivals,
                                void* stream);
 int launch_advance(int64_t* step_dev, int64_t by, void* stream);
+int launch_set_step(int64_t* step_dev, int64_t value, void* stream);
 int launch_init(int storage, const DevLattice& d, const double* rho, const double* u,
                 void* stream);
 int launch_gather(int storage, const DevLattice& d, int odd_layout, double* f_out, void* stream);

@@ -235,7 +235,7 @@ class Lattice:
     def profile(self, enable=True):
         self._check(self._lib.lbm_profile(self.h, 1 if enable else 0))
 
-    def tune(self, prefetch=None, bulk_sites=None, bulk_warps=None):
+    def tune(self, prefetch=None, bulk_sites=None, bulk_warps=None, graph_steps=None):
         """Launch knobs (``lbm_tune``): L2 prefetch distance of the bulk kernel in
         tiles, the bulk kernel's sites per lane and their pairing (1 to 4), and
         its warps per CTA (4 or 8)."""
@@ -245,6 +245,8 @@ class Lattice:
             self._check(self._lib.lbm_tune(self.h, A.LBM_TUNE_BULK_SITES, int(bulk_sites)))
         if bulk_warps is not None:
             self._check(self._lib.lbm_tune(self.h, A.LBM_TUNE_BULK_WARPS, int(bulk_warps)))
+        if graph_steps is not None:
+            self._check(self._lib.lbm_tune(self.h, A.LBM_TUNE_GRAPH_STEPS, int(graph_steps)))
 
     def time_steps(self, n):
         """Device ms of n steps (CUDA events on the lattice's stream)."""
@@ -259,7 +261,7 @@ class Lattice:
         return e0.elapsed_time(e1)
 
     def autotune(self, bulk_sites=(1, 2, 3, 4), bulk_warps=(4, 8), prefetch=(0, 2048, 4096),
-                 trial_steps=40):
+                 graph_steps=(20, 0), trial_steps=40):
         """Choose the bulk kernel's site tile (one site per lane, a 32-site tile per
         warp; or two per lane, 64 sites per warp, paired as adjacent sites or as
         two tiles), its CTA size and its L2 prefetch distance by timing each
@@ -270,10 +272,11 @@ class Lattice:
             bulk_sites = (1,)
         elif self.storage in ("f16s", "bf16s") and 5 not in bulk_sites:
             bulk_sites = tuple(bulk_sites) + (5,)  # TMA-staged even steps
-        best = dict(bulk_sites=bulk_sites[0], bulk_warps=bulk_warps[0], prefetch=prefetch[0])
+        best = dict(bulk_sites=bulk_sites[0], bulk_warps=bulk_warps[0], prefetch=prefetch[0],
+                    graph_steps=graph_steps[0])
         results = []
         for knob, cands in (("bulk_sites", bulk_sites), ("bulk_warps", bulk_warps),
-                            ("prefetch", prefetch)):
+                            ("prefetch", prefetch), ("graph_steps", graph_steps)):
             times = {}
             for v in cands:
                 cfg = dict(best)
