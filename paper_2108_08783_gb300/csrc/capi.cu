@@ -82,7 +82,11 @@ struct lbm_ctx {
   cudaGraphExec_t gexec = nullptr;
   int gexec_parity = -1;
   int64_t gexec_steps = 0;
+  // device step counter: holds the even floor of the step it was last made
+  // right for (step_d_for; -1: unknown); the captured kernels add it to their
+  // compile-time offset (the parity plus the step within the block)
   int64_t* step_d = nullptr;
+  int64_t step_d_for = -1;
   // tensor map of the populations as a [19][npad] array of 16-bit elements,
   // boxes of 32 x 19 (staged-row bulk kernel), made on first use
   alignas(64) CUtensorMap tmap;
@@ -561,7 +565,8 @@ void drop_graph(lbm_ctx* c) {
   c->gexec_steps = 0;
 }
 
-int run_steps(lbm_ctx* c, int64_t n_steps, bool diag_last) {
+// The launch parameters of the context's steps (the step index set per step).
+lbm::StepParams step_params(const lbm_ctx* c) {
   lbm::StepParams p{};
   p.rho0 = c->rho0;
   p.rho0_f = (float)c->rho0;
@@ -575,6 +580,11 @@ int run_steps(lbm_ctx* c, int64_t n_steps, bool diag_last) {
   p.bulk_warps = c->bulk_warps;
   p.n_sms = c->n_sms;
   p.tmap = c->tmap_ready ? &c->tmap : nullptr;
+  return p;
+}
+
+int run_steps(lbm_ctx* c, int64_t n_steps, bool diag_last) {
+  lbm::StepParams p = step_params(c);
 #ifndef LBM_CHECKED
   const int64_t G = c->graph_steps;
   if (G > 0 && n_steps >= G && !diag_last && !c->prof) {
@@ -616,11 +626,13 @@ int run_steps(lbm_ctx* c, int64_t n_steps, bool diag_last) {
       c->gexec_parity = parity;
       c->gexec_steps = G;
     }
-    r = (cudaError_t)lbm::launch_set_step(c->step_d, c->step - parity, c->gstream);
+    if (c->step_d_for != c->step)
+      r = (cudaError_t)lbm::launch_set_step(c->step_d, c->step - parity, c->gstream);
     int64_t done = 0;
     for (; r == cudaSuccess && n_steps - done >= G; done += G) r = cudaGraphLaunch(c->gexec, c->gstream);
     if (r != cudaSuccess) return cuda_fail(c, r, "step graph launch");
     c->step += done;
+    c->step_d_for = c->step;  // each replay advanced the counter by G
     p.step_dev = nullptr;
     for (int64_t s = done; s < n_steps; ++s) {
       p.step = c->step;
@@ -759,15 +771,22 @@ int lbm_step_diag(lbm_ctx* c, int64_t n_steps, double* out) {
   // kernels write it again (normally long since)
   const int b = (int)(c->diag_seq % lbm_ctx::kDiagSets);
   cudaError_t e = cudaSuccess;
-  if (c->diag_used[b]) e = cudaStreamWaitEvent(c->stream, c->diag_free[b], 0);
-  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_diag order");
   c->d.diag_mass = c->diag_mass[b];
   c->d.diag_j = c->diag_j[b];
-  rc = run_steps(c, n_steps, true);
+  // (a captured graph per diagnostic step measured no faster: the stream
+  // hops around it cost what the launches save)
+  if (n_steps > 1) {
+    rc = run_steps(c, n_steps - 1, false);  // captured graphs where they apply
+    if (rc != LBM_OK) return rc;
+  }
+  if (c->diag_used[b]) e = cudaStreamWaitEvent(c->stream, c->diag_free[b], 0);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_diag order");
+  rc = run_steps(c, 1, true);
   if (rc != LBM_OK) return rc;
-  // final sums and the copy out on the diagnostic stream, beside later steps
   e = cudaEventRecord(c->diag_filled[b], c->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->diag_stream, c->diag_filled[b], 0);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_diag order");
+  // final sums and the copy out on the diagnostic stream, beside later steps
+  e = cudaStreamWaitEvent(c->diag_stream, c->diag_filled[b], 0);
   if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_diag order");
   rc = check_launch(c, lbm::launch_diag_final(c->d, c->diag_io_off, c->diag_io_q, c->diag_fpi,
                                               c->diag_part[b], c->diag_done[b], c->diag_out[b],

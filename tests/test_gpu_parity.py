@@ -375,3 +375,30 @@ def test_murray_tree_parity(storage, tol, steps):
     orc.run(steps)
     _compare(lat, orc, tol, "tree")
     np.testing.assert_allclose(lat.reduce(), orc.reduce(), rtol=10 * tol, atol=1e-9)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_captured_step_graphs_equal_direct_launches(storage):
+    """lbm_step replays captured graphs of G steps (the inlet phase from a device
+    step counter, odd and even starting steps, a remainder of direct steps,
+    recapture after a knob or wall change, diagnostic steps in between): the
+    populations and the wall state equal those of direct launches bit for bit."""
+    geo = I.tube(12, 159, u_mean=0.025, u_amp=0.01, period=37.0)
+    fields = I.random_fields(21, geo.shape, drho=1e-3, umax=0.02)
+    runs = []
+    for g in (0, 10):
+        lat, _ = make_pair(geo, storage, tau=0.8, wall_model=1, F=0.85, kappa=BULK_KAPPA,
+                           fields=fields)
+        lat.tune(graph_steps=g)
+        lat.step(3)
+        lat.step(45)              # odd start: 4 replays and 5 direct steps
+        lat.tune(prefetch=1024)   # recapture
+        lat.step(20)
+        lat.step_diag(1)
+        lat.set_wall("elastic", rho0=1.0, F=0.8, kappa=BULK_KAPPA)  # recapture
+        lat.step(31)
+        lat.sync()
+        runs.append((lat.populations(), lat.wall_state()[0], lat.wall_state()[1]))
+        lat.close()
+    for a, b in zip(runs[0], runs[1]):
+        np.testing.assert_array_equal(a, b)
