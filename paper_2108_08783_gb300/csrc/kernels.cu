@@ -90,6 +90,23 @@ __device__ __forceinline__ C geq(C drho, C rho, C ux, C uy, C uz, C usq) {
 }
 
 // ------------------------------------------------------------- storage codecs
+// Loads of 16-bit populations (one site's value, or a packed pair) with an
+// L2 prefetch-size hint: the L2 fetches the aligned 256-byte block around the
+// requested sectors from DRAM in one request. On the long tube this makes the
+// FP16S step 2.3 % faster than plain loads (the inline loads also leave the
+// paired bulk kernels fewer spills); FP32 populations measured 1 % slower with
+// the same loads and keep plain ones.
+__device__ __forceinline__ uint32_t ld_pop_b32(const void* p) {
+  uint32_t v;
+  asm volatile("ld.global.L2::256B.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned short ld_pop_u16(const void* p) {
+  unsigned short v;
+  asm volatile("ld.global.L2::256B.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return v;
+}
+
 // Every storage type holds g = f - w (the deviation from the rest
 // equilibrium).  ld/st convert between the stored value and g in the compute
 // type C; get/put convert between the stored value and f in double.
@@ -120,7 +137,9 @@ struct Codec<float> {
 template <>
 struct Codec<__half> {
   using C = float;
-  static __device__ __forceinline__ C ld(const __half* p, int) { return __half2float(*p); }
+  static __device__ __forceinline__ C ld(const __half* p, int) {
+    return __half2float(__ushort_as_half(ld_pop_u16(p)));
+  }
   static __device__ __forceinline__ void st(__half* p, int, C g) { *p = __float2half_rn(g); }
   static __device__ __forceinline__ double get(const __half* p, int i) {
     return (double)__half2float(*p) + weight<double>(i);
@@ -133,7 +152,9 @@ struct Codec<__half> {
 template <>
 struct Codec<__nv_bfloat16> {
   using C = float;
-  static __device__ __forceinline__ C ld(const __nv_bfloat16* p, int) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ C ld(const __nv_bfloat16* p, int) {
+    return __uint_as_float((uint32_t)ld_pop_u16(p) << 16);
+  }
   static __device__ __forceinline__ void st(__nv_bfloat16* p, int, C g) { *p = __float2bfloat16_rn(g); }
   static __device__ __forceinline__ double get(const __nv_bfloat16* p, int i) {
     return (double)__bfloat162float(*p) + weight<double>(i);
@@ -553,12 +574,8 @@ struct Codec2<float> {
 };
 // 16-bit pairs also travel as packed words (low half: the first site): two
 // sites' values in one register from the load until the collision needs them.
-__device__ __forceinline__ uint32_t ld_word(const void* p) {
-  return *static_cast<const uint32_t*>(p);
-}
-__device__ __forceinline__ uint32_t ld_u16(const void* p) {
-  return *static_cast<const unsigned short*>(p);
-}
+__device__ __forceinline__ uint32_t ld_word(const void* p) { return ld_pop_b32(p); }
+__device__ __forceinline__ uint32_t ld_u16(const void* p) { return ld_pop_u16(p); }
 __device__ __forceinline__ uint32_t pack_u16(uint32_t lo, uint32_t hi) {
   return __byte_perm(lo, hi, 0x5410);
 }
@@ -577,12 +594,9 @@ struct Codec2<__half> {
     const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
     return mk2(f.x, f.y);
   }
-  static __device__ __forceinline__ F2 ld_al(const __half* p) {
-    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(p));
-    return mk2(f.x, f.y);
-  }
+  static __device__ __forceinline__ F2 ld_al(const __half* p) { return unpack(ld_pop_b32(p)); }
   static __device__ __forceinline__ F2 ld_un(const __half* p) {
-    return mk2(__half2float(p[0]), __half2float(p[1]));
+    return unpack(pack_u16(ld_pop_u16(p), ld_pop_u16(p + 1)));
   }
   static __device__ __forceinline__ void st_al(__half* p, F2 g) {
     float l, h;
@@ -603,12 +617,9 @@ struct Codec2<__nv_bfloat16> {
   static __device__ __forceinline__ F2 unpack(uint32_t w) {
     return mk2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
   }
-  static __device__ __forceinline__ F2 ld_al(const __nv_bfloat16* p) {
-    const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
-    return mk2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
-  }
+  static __device__ __forceinline__ F2 ld_al(const __nv_bfloat16* p) { return unpack(ld_pop_b32(p)); }
   static __device__ __forceinline__ F2 ld_un(const __nv_bfloat16* p) {
-    const uint32_t a = __bfloat16_as_ushort(p[0]), b = __bfloat16_as_ushort(p[1]);
+    const uint32_t a = ld_pop_u16(p), b = ld_pop_u16(p + 1);
     return mk2(__uint_as_float(a << 16), __uint_as_float(b << 16));
   }
   static __device__ __forceinline__ void st_al(__nv_bfloat16* p, F2 g) {
