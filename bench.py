@@ -407,6 +407,7 @@ def ensemble_study(args, steps, warmup):
     members, autotuned schedule; FP16S and FP32 storage batched, FP32 stepped one
     lattice at a time, and the storages' errors on a subset."""
     from paper_2108_08783_gb300 import Ensemble
+    from paper_2108_08783_gb300._capi import LBM_EUNSTABLE, LbmError
     members = ensemble_members()
     out = {}
     peak, _ = measured_peaks()
@@ -414,11 +415,27 @@ def ensemble_study(args, steps, warmup):
         lats = _ensemble_lattices(members, storage)
         n = sum(l.n for l in lats)
         ens = Ensemble(lats)
-        best, trials = ens.autotune(trial_steps=20)
+        # one timed trial per candidate and at most two sweeps: 28 candidates of
+        # 2 x 20 steps each, at most 2,240 steps; then every member starts again
+        # from rest, so the timed run is the same 2,000-odd steps from rest
+        # whatever the search took (the family's least stable member diverges
+        # after ~3,750 steps)
+        best, trials = ens.autotune(trial_steps=20, trials=1, sweeps=2)
+        trial_unstable = 0
+        for l in lats:
+            l.init_fields()
+            try:
+                l.sync()  # reads (and clears) a density flag raised during the search
+            except LbmError as err:
+                if err.status != LBM_EUNSTABLE:
+                    raise
+                trial_unstable += 1
         ens.step(warmup)
         ms = _timed(lambda: ens.step(steps), ens.stream)
         ens.sync()
         out[storage] = {"batched_mlups": n * steps / ms / 1e3, "autotuned": best,
+                        "autotune_trials": len(trials),
+                        "members_unstable_during_autotune": trial_unstable,
                         "ms_per_step": ms / steps,
                         "roofline_frac": n * 2 * 19 * BYTES[storage] / (ms / steps * 1e-3) / 1e9
                         / peak}

@@ -6,6 +6,7 @@ allocator, passed to the library as an allocator callback) and the CUDA
 stream.
 """
 import ctypes as C
+import itertools
 
 import numpy as np
 
@@ -17,6 +18,61 @@ WALL = {"bounceback": A.LBM_WALL_BOUNCEBACK, "elastic": A.LBM_WALL_ELASTIC_GZS}
 
 def _ptr(a):
     return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def default_knobs(storage):
+    """The launch knobs a new lattice or ensemble starts with (``lbm_tune``): two
+    sites per lane for 16-bit storage, one otherwise; an L2 prefetch distance of
+    4096 tiles for FP32 storage, none otherwise; CTAs of 4 warps."""
+    sixteen = storage in ("f16s", "bf16s")
+    return dict(bulk_sites=2 if sixteen else 1, bulk_warps=4,
+                prefetch=4096 if storage == "f32" else 0)
+
+
+def coordinate_search(apply, timer, knobs, start, trials=2, sweeps=3, margin=0.005):
+    """Tune launch knobs by coordinate search from ``start``.
+
+    ``knobs`` lists (name, candidates); a name may be a tuple of knob names
+    whose candidates are tuples of values, searched jointly (knobs whose best
+    values depend on each other, such as the bulk kernel's sites per lane and
+    its prefetch distance, where a search one knob at a time can stop at
+    either of two local optima).  Each entry in turn takes every candidate with
+    the others held; ``apply(cfg)`` sets a configuration and ``timer()``
+    returns the ms of a trial (the first call after ``apply`` only warms up,
+    e.g. captures a graph; the best of ``trials`` more is kept).  A candidate
+    replaces the current value only when it is faster by more than ``margin``
+    (relative), so timing noise does not walk away from the start.  The sweeps
+    repeat until one changes nothing, at most ``sweeps`` times.  Returns
+    (best, [(cfg, ms)])."""
+    best = dict(start)
+    results = []
+
+    def measure(cfg):
+        apply(cfg)
+        timer()
+        ms = min(timer() for _ in range(trials))
+        results.append((dict(cfg), ms))
+        return ms
+
+    for _ in range(sweeps):
+        changed = False
+        for name, cands in knobs:
+            names = name if isinstance(name, tuple) else (name,)
+            values = (lambda v: v) if isinstance(name, tuple) else (lambda v: (v,))
+            cur = tuple(best[n] for n in names)
+            times = {cur: measure(best)}
+            for v in cands:
+                v = values(v)
+                if v not in times:
+                    times[v] = measure(dict(best, **dict(zip(names, v))))
+            v = min(times, key=times.get)
+            if v != cur and times[v] < times[cur] * (1.0 - margin):
+                best.update(zip(names, v))
+                changed = True
+        if not changed:
+            break
+    apply(best)
+    return best, results
 
 
 def iolet_struct(io):
@@ -261,33 +317,25 @@ class Lattice:
         return e0.elapsed_time(e1)
 
     def autotune(self, bulk_sites=(1, 2, 3, 4), bulk_warps=(4, 8), prefetch=(0, 2048, 4096),
-                 graph_steps=(20, 0), trial_steps=40):
+                 graph_steps=(20, 0), trial_steps=40, trials=2, sweeps=3):
         """Choose the bulk kernel's site tile (one site per lane, a 32-site tile per
         warp; or two per lane, 64 sites per warp, paired as adjacent sites or as
-        two tiles), its CTA size and its L2 prefetch distance by timing each
-        candidate on this lattice (coordinate search).  Every trial advances the
-        lattice by ``trial_steps`` steps (an even number keeps both parities
-        equal)."""
+        two tiles), its CTA size, its L2 prefetch distance and graph replay by
+        timing each candidate on this lattice (``coordinate_search`` from the
+        library's defaults, sites per lane and prefetch distance jointly;
+        ``trials`` and ``sweeps`` as there).  Every trial, and the warm-up run
+        before each candidate's trials, advances the lattice by ``trial_steps``
+        steps (an even number keeps both parities equal)."""
         if self.storage == "f64":
             bulk_sites = (1,)
         elif self.storage in ("f16s", "bf16s") and 5 not in bulk_sites:
             bulk_sites = tuple(bulk_sites) + (5,)  # TMA-staged even steps
-        best = dict(bulk_sites=bulk_sites[0], bulk_warps=bulk_warps[0], prefetch=prefetch[0],
-                    graph_steps=graph_steps[0])
-        results = []
-        for knob, cands in (("bulk_sites", bulk_sites), ("bulk_warps", bulk_warps),
-                            ("prefetch", prefetch), ("graph_steps", graph_steps)):
-            times = {}
-            for v in cands:
-                cfg = dict(best)
-                cfg[knob] = v
-                self.tune(**cfg)
-                self.time_steps(trial_steps)
-                times[v] = self.time_steps(trial_steps)
-                results.append((dict(cfg), times[v]))
-            best[knob] = min(times, key=times.get)
-        self.tune(**best)
-        return best, results
+        start = dict(default_knobs(self.storage), graph_steps=20)
+        knobs = ((("bulk_sites", "prefetch"), list(itertools.product(bulk_sites, prefetch))),
+                 ("bulk_warps", bulk_warps), ("graph_steps", graph_steps))
+        return coordinate_search(lambda cfg: self.tune(**cfg),
+                                 lambda: self.time_steps(trial_steps), knobs, start,
+                                 trials=trials, sweeps=sweeps)
 
     def profile_read(self):
         """Since profile(True): ((step ms, bulk-kernel ms), (bulk launches, boundary launches))."""
@@ -376,32 +424,26 @@ class Ensemble:
 
     def autotune(self, prefetch=(0, 1024, 2048, 4096, 8192), schedule=(0, 1),
                  graph_steps=(0, 20), persistent=(0, 1), bulk_sites=(1, 2, 3, 4),
-                 bulk_warps=(4, 8), trial_steps=40):
+                 bulk_warps=(4, 8), trial_steps=40, trials=2, sweeps=3):
         """Choose the schedule knobs by timing each candidate on this ensemble
-        (coordinate search, one knob at a time): member order, the bulk kernel's
-        site tile (one site per lane, 32 sites per warp; or two per lane, 64 per
-        warp, paired as adjacent sites or as two tiles), its L2 prefetch distance,
-        graph replay and the persistent kernel.  Every trial advances the members
-        by ``trial_steps`` steps."""
-        results = []
-        if self.members[0].storage == "f64":
+        (``coordinate_search`` from the library's defaults, sites per lane and
+        prefetch distance jointly): member order, the bulk kernel's site tile
+        (one site per lane, 32 sites per warp; or two per lane, 64 per warp,
+        paired as adjacent sites or as two tiles), its CTA size and L2 prefetch
+        distance, graph replay and the persistent kernel (``trials`` and
+        ``sweeps`` as there).  Every trial, and the warm-up run before each
+        candidate's trials, advances the members by ``trial_steps`` steps."""
+        storage = self.members[0].storage
+        if storage == "f64":
             bulk_sites = (1,)
-        best = dict(prefetch=prefetch[0], schedule=schedule[0], graph_steps=graph_steps[0],
-                    persistent=persistent[0], bulk_sites=bulk_sites[0], bulk_warps=bulk_warps[0])
-        for knob, cands in (("schedule", schedule), ("bulk_sites", bulk_sites),
-                            ("bulk_warps", bulk_warps), ("prefetch", prefetch),
-                            ("graph_steps", graph_steps), ("persistent", persistent)):
-            times = {}
-            for v in cands:
-                cfg = dict(best)
-                cfg[knob] = v
-                self.tune(**cfg)
-                self.time_steps(trial_steps)  # warm (and capture a graph if any)
-                times[v] = self.time_steps(trial_steps)
-                results.append((dict(cfg), times[v]))
-            best[knob] = min(times, key=times.get)
-        self.tune(**best)
-        return best, results
+        start = dict(default_knobs(storage), schedule=0, graph_steps=0, persistent=0)
+        knobs = (("schedule", schedule),
+                 (("bulk_sites", "prefetch"), list(itertools.product(bulk_sites, prefetch))),
+                 ("bulk_warps", bulk_warps), ("graph_steps", graph_steps),
+                 ("persistent", persistent))
+        return coordinate_search(lambda cfg: self.tune(**cfg),
+                                 lambda: self.time_steps(trial_steps), knobs, start,
+                                 trials=trials, sweeps=sweeps)
 
     def close(self):
         h = getattr(self, "h", None)
