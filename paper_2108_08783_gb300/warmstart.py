@@ -7,8 +7,8 @@ by the method itself (batched lattices, ``Ensemble``); the network
 (tube parameters, axial and radial position) -> (rho, u_r, u_z) from those
 converged fields with the library's own forward/backward/Adam kernels; a run
 then starts from the network's proposal (``Lattice.warm_start``) instead of
-from rest.  The zero-velocity start stays the fallback and the converged
-solution of the method is the judge of the network's error.
+from rest.  The zero-velocity start stays the fallback, and the network's
+error is measured against the method's own converged solution.
 
 Convergence: the relative change of u per step, measured over a window of
 ``window`` steps, ||u(t) - u(t - window)|| / (window ||u(t)||), falls below
