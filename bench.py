@@ -56,6 +56,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+# lbm_step's default graph block (LBM_TUNE_GRAPH_STEPS): whole blocks of 20 steps
+# replay a captured graph that also launches one k_advance (the device step
+# counter) after its steps
+GRAPH_STEPS = 20
 DTYPE = {"f64": "f64", "f32": "f32", "f16s": "f32", "bf16s": "f32"}
 METRIC = "elastic-wall D3Q19 MLUPS & % HBM roofline; mixed-prec vs FP32 at fixed error"
 
@@ -562,6 +566,11 @@ def run_ours(args):
     lat.profile(False)
     lat.sync()
     launches_per_step = (n_bulk_l + n_bnd_l) / pk
+    # the timed region's graph bookkeeping: one k_advance per replayed block, and
+    # one k_set_step when the warm-up ended on direct steps (the counter is stale)
+    graph_launches = 0
+    if args.steps >= GRAPH_STEPS:
+        graph_launches = args.steps // GRAPH_STEPS + (1 if warm % GRAPH_STEPS else 0)
     # ---------------------------------------------------------------- roofline
     peak, peak_kind = measured_peaks()
     s = BYTES[args.storage]
@@ -651,7 +660,7 @@ def run_ours(args):
             "config": run_config(args, name, n, ws),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": prec,
             "wall_cost": walls, "tree": tree, "ensemble": ens,
-            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "gpu_launches": int(round(launches_per_step * args.steps)) + graph_launches,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
