@@ -93,8 +93,9 @@ def measured_peaks():
 
 
 def kernel_traffic(storage, config):
-    """DRAM bytes per bulk-kernel launch from the committed ncu summary, or None
-    if the kernel source changed since the counters were taken."""
+    """DRAM bytes of one step (its bulk and boundary launches, mean of an odd and
+    an even step) from the committed ncu summary, or None if the kernel source
+    changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
